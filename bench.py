@@ -1,0 +1,300 @@
+"""Benchmark of the SU(2) two-site H.psi (Eq. 2) on GB300.
+
+One step = one full H.psi (every operator-table row, every task) of the
+seeded synthetic workload, inputs resident in HBM.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME]
+                  [--prec split|fp64] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank runs an independent replica of the
+workload (the path needs no exchange on one node), value = total flops of
+all ranks / max time over ranks ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "H·ψ TFLOPS/GB300 (SU(2), U(1)-equiv): split-prec vs FP64 at ≤1e-10 rel err"
+DEFAULT_CONFIG = "qc16"
+FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal FP64 rate)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_cpu_baseline(cfg_name: str, repeats: int, max_seconds: float):
+    """Times the FP64 oracle (as it stands) on the host, single-threaded BLAS,
+    in a child process; returns (TFLOP/s, cores, sample description)."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np, synth
+from oracle import model, sectors, heff, env
+cfg = synth.CONFIGS[{cfg_name!r}]
+left, right = synth.middle_bond_sectors(cfg)
+blocks, n = sectors.build_blocks(left, right, cfg.site_kind, cfg.N, cfg.twoS)
+tab = model.heisenberg_table() if cfg.site_kind == synth.SPIN_HALF else model.qc_skeleton_table(cfg.n_left, cfg.n_right)
+tasks = heff.build_tasks(tab, left, right, blocks, cfg.twoS)
+e = env.build_env(tab, cfg, left, right)
+psi = synth.gaussian_psi(n, synth.psi_seed(cfg))
+# algorithmic flops of the sample: same definition as the library (K1 deduplicated)
+k1 = {{}}
+k2 = 0
+for t in tasks:
+    E, F = blocks[t.e], blocks[t.f]
+    if t.D is not None:
+        k1[(tab.terms[t.term].D, t.D, t.e)] = 2 * E.rows * E.cols * F.cols
+    if t.A is not None:
+        k2 += 2 * F.rows * E.rows * F.cols
+flops = sum(k1.values()) + k2
+times = []
+t_end = time.time() + {max_seconds}
+for r in range({repeats}):
+    t0 = time.perf_counter(); heff.apply_heff(tab, e, tasks, blocks, n, psi); times.append(time.perf_counter() - t0)
+    if time.time() > t_end: break
+print(json.dumps({{"flops": flops, "times": times}}))
+"""
+    envv = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=envv)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    t = statistics.median(d["times"])
+    return d["flops"] / t / 1e12, 1, f"full H.psi of {cfg_name} (all tasks), median of {len(d['times'])}", t
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cfg = synth.CONFIGS[args.config]
+    ts = []
+    value = None
+    for _ in range(args.warmup):
+        pass
+    v, cores, sample, t = oracle_cpu_baseline(args.config, max(1, args.steps), 150.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg.name, "L": cfg.L, "N": cfg.N, "twoS": cfg.twoS, "D": cfg.D},
+        "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", default=DEFAULT_CONFIG)
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "split"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    cfg = synth.CONFIGS[args.config]
+    prec = P.SU2_SPLIT_BF16 if args.prec == "split" else P.SU2_FP64
+    ctx = P.Context(local, stream=stream)
+    t0 = time.time()
+    sec, env = workload.build(ctx, cfg, prepare_split=(prec == P.SU2_SPLIT_BF16))
+    build_s = time.time() - t0
+    n = sec.psi_len
+    psi = torch.from_numpy(synth.gaussian_psi(n, synth.psi_seed(cfg))).to(dev)
+    out = torch.empty_like(psi)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+    info = env.info
+    flops = info["flops_su2"]
+
+    rel_err_fp64 = None
+    if prec != P.SU2_FP64:
+        ref = torch.empty_like(psi)
+        P.apply_heff(ctx, env, psi, ref, P.SU2_FP64)
+        P.apply_heff(ctx, env, psi, out, prec)
+        torch.cuda.synchronize()
+        rel_err_fp64 = float(torch.linalg.norm(out - ref) / torch.linalg.norm(ref))
+
+    for _ in range(args.warmup):
+        P.apply_heff(ctx, env, psi, out, prec)
+    torch.cuda.synchronize()
+    env.profile(True)
+    env.profile_reset()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        P.apply_heff(ctx, env, psi, out, prec)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    tot_ms = sum(step_ms)
+    prof = env.profile_read()
+    env.profile(False)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * args.steps * flops / (tot_ms / 1e3) / 1e12
+
+    # end to end through the C-ABI with host buffers (copies inside the call)
+    hin = torch.from_numpy(synth.gaussian_psi(n, synth.psi_seed(cfg))).pin_memory()
+    hout = torch.empty(n, dtype=torch.float64).pin_memory()
+    P.apply_heff_host(ctx, env, hin.numpy(), hout.numpy(), prec)
+    e2e_t = []
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        P.apply_heff_host(ctx, env, hin.numpy(), hout.numpy(), prec)
+        e2e_t.append(time.perf_counter() - t1)
+    e2e_tot = sum(e2e_t)
+    if world > 1:
+        t = torch.tensor([e2e_tot], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_tot = float(t.item())
+    e2e_value = world * args.steps * flops / e2e_tot / 1e12
+
+    # roofline of the dominant kernel
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (launches, ms, fl) = dom
+    pk, src = peaks()
+    if name.endswith("fp64"):
+        bound, peak, unit = "alu", FP64_PEAK_TFLOPS, "TFLOP/s"
+        peak_note = "nominal FP64 rate from SM count x DFMA/clk x max clock"
+    else:
+        bound, unit = "tensor", "TFLOP/s"
+        peak = pk.get("bf16_tflops_sustained", 1700.0)
+        peak_note = f"{src} bf16 dense (sustained)"
+    achieved = (fl / launches) / (ms / launches / 1e3) / 1e12 if launches else 0.0
+    gpu_launches = int(sum(v[0] for v in prof.values()))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            v, cores, sample, _ = oracle_cpu_baseline(cfg.name, 3, 30.0)
+            cpu = {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample}
+        except Exception as ex:  # reported, not fatal
+            cpu = {"value": None, "unit": "TFLOP/s", "cores": 0, "kind": "oracle", "sample": f"failed: {ex}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == P.SU2_FP64 else "bf16x-split-f64",
+            "data": "synthetic",
+            "config": {"workload": cfg.name, "L": cfg.L, "N": cfg.N, "twoS": cfg.twoS, "D": cfg.D,
+                       "prec": args.prec, "psi_len": n, "terms": info["n_terms"], "tasks": info["n_tasks"],
+                       "l2": "flushed between steps (256 MB write)"},
+            "value_u1_equiv": value * info["r_d"],
+            "flops_su2_per_step": flops,
+            "rel_err_vs_fp64": rel_err_fp64,
+            "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                         "frac": achieved / peak if peak else None, "traffic": None,
+                         "kernel": name, "peak_source": peak_note},
+            "kernels": {k: {"launches": v[0], "ms": v[1], "flops": v[2]} for k, v in prof.items() if v[0]},
+            "gpu_launches": gpu_launches,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "build_s": build_s,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,194 @@
+/*
+ * su2dmrg: GB300 (sm_103a) library for the projected two-site Hamiltonian
+ * application H.psi of SU(2) spin-adapted DMRG and the Davidson eigensolver
+ * around it (arXiv:2309.16724).
+ *
+ * Every entry point returns an su2_status; no exception, exit or assert
+ * crosses the ABI.  On failure, su2_last_error(ctx) holds a one-line reason.
+ * Spins are passed as "twos" (the integer 2j).  All floating-point data is
+ * FP64, matrices are column-major.
+ *
+ * Ownership: handles are created and destroyed by the library.  psi buffers
+ * passed to su2_apply_heff / su2_davidson_create are caller-owned device
+ * memory of length psi_len doubles (block order of su2_sectors_query).
+ * Environments, task tables and workspaces are library-owned device memory.
+ * Concurrency: one context per stream; calls on a context are stream
+ * ordered; su2_apply_heff does not synchronise the host.
+ */
+#ifndef SU2DMRG_H
+#define SU2DMRG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct su2_ctx su2_ctx;
+typedef struct su2_sectors su2_sectors;
+typedef struct su2_env su2_env;
+typedef struct su2_dav su2_dav;
+
+enum su2_status {
+  SU2_OK = 0,        /* success */
+  SU2_EINVAL = 1,    /* bad argument: null/misaligned pointer, triangle or
+                        particle-number violation, unknown enum value */
+  SU2_ENOMEM = 2,    /* host or device allocation failed */
+  SU2_ECUDA = 3,     /* a CUDA runtime call failed */
+  SU2_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+  SU2_ENOTCONV = 5   /* Davidson reached its iteration limit */
+};
+
+/* Arithmetic of the sector GEMMs of H.psi. */
+enum su2_prec {
+  SU2_FP64 = 0,        /* native FP64 (CUDA-core DFMA)                       */
+  SU2_SPLIT_BF16 = 1   /* FP64 operands cut into BF16 slices, tcgen05 tensor
+                          cores with FP32 accumulation, exact per K-chunk,
+                          recombined to FP64                                  */
+};
+
+enum su2_site_kind { SU2_SITE_SPIN_HALF = 0, SU2_SITE_ORBITAL = 1 };
+
+/* Operator tables (rows of Eq. 2) the library can build. */
+enum su2_model {
+  SU2_MODEL_HEISENBERG = 0,   /* J sum S_i.S_{i+1}; block operators
+                                 renormalised from a seeded MPS (Sec. II.C) */
+  SU2_MODEL_QC_SKELETON = 1,  /* ab initio normal/complementary term
+                                 structure, seeded synthetic entries         */
+  SU2_MODEL_CASIMIR_S2 = 2,   /* total spin squared (S(S+1) psi)            */
+  SU2_MODEL_CASIMIR_N = 3     /* total particle number (N psi)              */
+};
+
+/* One bond sector: particle number, twice the spin, kept multiplets. */
+typedef struct { int32_t N, twoS, dim; } su2_sector;
+
+/* One block of psi (sector-table row, Sec. II.A): left sector a, site
+ * states s1, s2, right sector b, intermediate spins (a x s1)->jL1,
+ * (s2 x b)->j2R; a rows x cols column-major matrix at element offset. */
+typedef struct {
+  int32_t a, s1, s2, b, jL1, j2R, rows, cols;
+  int64_t offset;
+} su2_block;
+
+/* Bond sectors of a block grown site by site: bond k (k sites) holds the
+ * sectors sectors[bond_offset[k] .. bond_offset[k+1]), ascending (N, 2S).
+ * The last bond is the one adjacent to the two-site window. */
+typedef struct {
+  int32_t n_bonds;
+  const int32_t* bond_offset;   /* n_bonds + 1 entries */
+  const su2_sector* sectors;
+} su2_bond_chain;
+
+typedef struct {
+  int32_t model;      /* su2_model */
+  int32_t n_left;     /* orbitals / sites in the left block  */
+  int32_t n_right;    /* orbitals / sites in the right block */
+  double J;           /* Heisenberg coupling                 */
+  uint64_t seed;      /* seed of the counter-based generator (SplitMix64)
+                         for synthetic entries and MPS tensors */
+} su2_hamiltonian;
+
+typedef struct {
+  int64_t t_budget_bytes;  /* device bytes for the intermediate T = E D^T of
+                              one term chunk (0: library default)           */
+  int32_t n_slices;        /* BF16 slices per operand (0: default 5)        */
+  int32_t prepare_split;   /* 1: also build the split-precision arenas      */
+} su2_env_opts;
+
+typedef struct {
+  int64_t psi_len, n_blocks, n_terms, n_tasks, n_k1, n_chunks;
+  double flops_su2;        /* flops of one H.psi as executed (K1 deduplicated
+                              by (D operator, output sector, input block),
+                              K2 per task; identities skipped)            */
+  double flops_u1_equiv;   /* flops_su2 * R_D, R_D = D_U(1)^eff / D        */
+  double r_d;              /* D_U(1)^eff / D of the left bond              */
+  double env_bytes;        /* FP64 bytes of all operator blocks            */
+} su2_env_info;
+
+typedef struct {
+  double tol;          /* residual 2-norm (default 1e-8)        */
+  int32_t max_sub;     /* subspace size (default 24, max 32)    */
+  int32_t keep;        /* Ritz vectors kept on restart (2)      */
+  int32_t max_iter;    /* iteration limit (200)                 */
+  int32_t prec;        /* su2_prec of the H.psi inside           */
+} su2_dav_opts;
+
+/* Context on CUDA device `device` (-1: host-only context that can build
+ * sectors and tables but not run kernels) and stream `cuda_stream`
+ * (a cudaStream_t, NULL for the library's own stream). */
+int su2_ctx_create(int device, void* cuda_stream, su2_ctx** out);
+int su2_ctx_destroy(su2_ctx* ctx);
+const char* su2_last_error(su2_ctx* ctx);
+
+/* Sector-table of psi (Sec. II.A, Eq. 3): all blocks (a, s1, s2, b, jL1,
+ * j2R) with N_a + n1 + n2 + N_b = N_target and the couplings a x s1 -> jL1,
+ * s2 x b -> j2R, jL1 x j2R -> twoS_target allowed.  Host-only work. */
+int su2_build_sectors(su2_ctx* ctx, const su2_sector* left, int32_t n_left,
+                      const su2_sector* right, int32_t n_right, int32_t site_kind,
+                      int32_t N_target, int32_t twoS_target, su2_sectors** out);
+int su2_sectors_query(const su2_sectors* s, int64_t* psi_len, int32_t* n_blocks,
+                      const su2_block** blocks);
+int su2_sectors_destroy(su2_sectors* s);
+
+/* Operator-table (Eq. 2), block operators A_i / D_i, Clebsch-Gordan-layer
+ * coefficients C~ (Eq. a, from 6j/9j of Eqs. A2-A4), sector-task-table
+ * (Eq. 3) and sector-value table (Sec. II.C), built once per site.  The
+ * chains give the bond sectors grown from the vacuum to the two-site
+ * window (their last bonds must equal the sectors' left/right lists).  With
+ * a device context the tables and operators are uploaded. */
+int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H,
+                          const su2_bond_chain* left_chain, const su2_bond_chain* right_chain,
+                          const su2_sectors* sectors, const su2_env_opts* opts, su2_env** out);
+int su2_env_query(const su2_env* env, su2_env_info* info);
+/* Copies the sector-task-table: 8 int32 per task (f, term, e, a_out, a_in,
+ * b_out, b_in, flags) with a_* = -1 for an identity left operator, b_* = -1
+ * for an identity right operator, and v per task; arrays of n_tasks rows. */
+int su2_env_tasks(const su2_env* env, int32_t* rows8, double* v, int64_t n_tasks);
+/* Copies block (out sector qo, in sector qi) of block operator `op` of
+ * side 0 (left, A_i) or 1 (right, D_i) into out (rows x cols, column-major).
+ * SU2_EINVAL if the operator has no such block or the shape differs. */
+int su2_env_operator_block(const su2_env* env, int32_t side, int32_t op, int32_t qo, int32_t qi, double* out,
+                           int32_t rows, int32_t cols);
+int su2_env_destroy(su2_env* env);
+
+/* F = H_eff psi (Eq. 2 over the sector-task-table).  psi_in, psi_out:
+ * device pointers, 8-byte aligned, psi_len doubles, not overlapping. */
+int su2_apply_heff(su2_ctx* ctx, const su2_env* env, const double* psi_in_dev,
+                   double* psi_out_dev, int32_t prec);
+/* Same with host buffers: copies psi in, runs, copies F out, synchronises. */
+int su2_apply_heff_host(su2_ctx* ctx, const su2_env* env, const double* psi_in_host,
+                        double* psi_out_host, int32_t prec);
+/* Diagonal of H_eff (Davidson preconditioner) into a device buffer. */
+int su2_diag_heff(su2_ctx* ctx, const su2_env* env, double* diag_dev);
+
+/* Davidson eigensolver for the lowest eigenpair of H_eff (the
+ * diagonalisation that takes 85-90 % of DMRG time, Sec. II).  One call of
+ * su2_davidson_step performs one iteration on the device: H.v, projected
+ * matrix update, Rayleigh-Ritz, residual, preconditioned correction and
+ * Gram-Schmidt; theta and the residual norm are returned. */
+int su2_davidson_create(su2_ctx* ctx, const su2_env* env, const double* psi0_dev,
+                        const su2_dav_opts* opts, su2_dav** out);
+int su2_davidson_step(su2_ctx* ctx, su2_dav* dav, double* theta, double* resnorm);
+/* Runs steps until ||r|| <= tol or max_iter; SU2_ENOTCONV if not reached. */
+int su2_davidson_solve(su2_ctx* ctx, su2_dav* dav, double* theta, double* resnorm,
+                       int32_t* iterations);
+int su2_energy(const su2_dav* dav, double* E);
+/* Current Ritz vector (unit norm, largest-magnitude entry positive). */
+int su2_davidson_vector(su2_ctx* ctx, su2_dav* dav, double* x_dev);
+int su2_davidson_destroy(su2_dav* dav);
+
+/* Per-kernel timing of su2_apply_heff (off by default): with profiling on,
+ * every kernel launch of the hot path is bracketed by CUDA events on the
+ * context stream.  su2_profile_read synchronises on the recorded events and
+ * returns, for kernel kind `kind` (0: FP64 K1, 1: FP64 K2, 2: split-path
+ * slice kernel, 3: split-path K1, 4: split-path K2), the launches, total
+ * device milliseconds and algorithmic flops since the last reset, and the
+ * kind's name.  SU2_EINVAL for an unknown kind. */
+int su2_profile_enable(su2_env* env, int32_t on);
+int su2_profile_reset(su2_env* env);
+int su2_profile_read(su2_env* env, int32_t kind, int64_t* launches, double* ms, double* flops, const char** name);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,336 @@
+"""ctypes binding of libsu2dmrg (include/su2dmrg.h): argument marshalling only.
+
+Every computation runs in the library (host tables in C++, the hot path in
+CUDA kernels).  If the shared library is missing, loading raises; there is
+no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsu2dmrg.so")
+
+SU2_OK, SU2_EINVAL, SU2_ENOMEM, SU2_ECUDA, SU2_ETIMEOUT, SU2_ENOTCONV = range(6)
+SU2_FP64, SU2_SPLIT_BF16 = 0, 1
+SU2_SITE_SPIN_HALF, SU2_SITE_ORBITAL = 0, 1
+SU2_MODEL_HEISENBERG, SU2_MODEL_QC_SKELETON, SU2_MODEL_CASIMIR_S2, SU2_MODEL_CASIMIR_N = range(4)
+
+SYMBOLS = [
+    "su2_ctx_create", "su2_ctx_destroy", "su2_last_error", "su2_build_sectors", "su2_sectors_query",
+    "su2_sectors_destroy", "su2_build_environment", "su2_env_query", "su2_env_tasks", "su2_env_operator_block", "su2_env_destroy",
+    "su2_apply_heff", "su2_apply_heff_host", "su2_diag_heff", "su2_davidson_create", "su2_davidson_step",
+    "su2_davidson_solve", "su2_energy", "su2_davidson_vector", "su2_davidson_destroy",
+    "su2_profile_enable", "su2_profile_reset", "su2_profile_read",
+]
+
+
+class Sector(C.Structure):
+    _fields_ = [("N", C.c_int32), ("twoS", C.c_int32), ("dim", C.c_int32)]
+
+
+class Block(C.Structure):
+    _fields_ = [("a", C.c_int32), ("s1", C.c_int32), ("s2", C.c_int32), ("b", C.c_int32),
+                ("jL1", C.c_int32), ("j2R", C.c_int32), ("rows", C.c_int32), ("cols", C.c_int32),
+                ("offset", C.c_int64)]
+
+
+class BondChain(C.Structure):
+    _fields_ = [("n_bonds", C.c_int32), ("bond_offset", C.POINTER(C.c_int32)),
+                ("sectors", C.POINTER(Sector))]
+
+
+class Hamiltonian(C.Structure):
+    _fields_ = [("model", C.c_int32), ("n_left", C.c_int32), ("n_right", C.c_int32),
+                ("J", C.c_double), ("seed", C.c_uint64)]
+
+
+class EnvOpts(C.Structure):
+    _fields_ = [("t_budget_bytes", C.c_int64), ("n_slices", C.c_int32), ("prepare_split", C.c_int32)]
+
+
+class EnvInfo(C.Structure):
+    _fields_ = [("psi_len", C.c_int64), ("n_blocks", C.c_int64), ("n_terms", C.c_int64),
+                ("n_tasks", C.c_int64), ("n_k1", C.c_int64), ("n_chunks", C.c_int64),
+                ("flops_su2", C.c_double), ("flops_u1_equiv", C.c_double), ("r_d", C.c_double),
+                ("env_bytes", C.c_double)]
+
+
+class DavOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_sub", C.c_int32), ("keep", C.c_int32),
+                ("max_iter", C.c_int32), ("prec", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libsu2dmrg.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.su2_ctx_create.argtypes = [C.c_int, vp, C.POINTER(vp)]
+        L.su2_ctx_destroy.argtypes = [vp]
+        L.su2_last_error.argtypes = [vp]
+        L.su2_last_error.restype = C.c_char_p
+        L.su2_build_sectors.argtypes = [vp, C.POINTER(Sector), C.c_int32, C.POINTER(Sector), C.c_int32,
+                                        C.c_int32, C.c_int32, C.c_int32, C.POINTER(vp)]
+        L.su2_sectors_query.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                        C.POINTER(C.POINTER(Block))]
+        L.su2_sectors_destroy.argtypes = [vp]
+        L.su2_build_environment.argtypes = [vp, C.POINTER(Hamiltonian), C.POINTER(BondChain),
+                                            C.POINTER(BondChain), vp, C.POINTER(EnvOpts), C.POINTER(vp)]
+        L.su2_env_query.argtypes = [vp, C.POINTER(EnvInfo)]
+        L.su2_env_tasks.argtypes = [vp, vp, vp, C.c_int64]
+        L.su2_env_operator_block.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp,
+                                             C.c_int32, C.c_int32]
+        L.su2_env_destroy.argtypes = [vp]
+        L.su2_apply_heff.argtypes = [vp, vp, vp, vp, C.c_int32]
+        L.su2_apply_heff_host.argtypes = [vp, vp, vp, vp, C.c_int32]
+        L.su2_diag_heff.argtypes = [vp, vp, vp]
+        L.su2_davidson_create.argtypes = [vp, vp, vp, C.POINTER(DavOpts), C.POINTER(vp)]
+        L.su2_davidson_step.argtypes = [vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.su2_davidson_solve.argtypes = [vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_int32)]
+        L.su2_energy.argtypes = [vp, C.POINTER(C.c_double)]
+        L.su2_davidson_vector.argtypes = [vp, vp, vp]
+        L.su2_davidson_destroy.argtypes = [vp]
+        L.su2_profile_enable.argtypes = [vp, C.c_int32]
+        L.su2_profile_reset.argtypes = [vp]
+        L.su2_profile_read.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double), C.POINTER(C.c_char_p)]
+        for name in SYMBOLS:
+            if name != "su2_last_error":
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class Su2Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"su2dmrg error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(x):
+    """Device/host address of a torch tensor, numpy array or int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
+class Context:
+    def __init__(self, device: int = 0, stream=None):
+        h = C.c_void_p()
+        s = None
+        if stream is not None:
+            s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        rc = lib().su2_ctx_create(device, s, C.byref(h))
+        if rc:
+            raise Su2Error(rc, "su2_ctx_create failed")
+        self.h = h
+        self.device = device
+
+    def check(self, rc):
+        if rc:
+            raise Su2Error(rc, lib().su2_last_error(self.h).decode())
+
+    def close(self):
+        if self.h:
+            lib().su2_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _sector_array(secs):
+    arr = (Sector * max(1, len(secs)))()
+    for i, (N, s, d) in enumerate(secs):
+        arr[i] = Sector(N, s, d)
+    return arr
+
+
+class Sectors:
+    """su2_build_sectors: psi blocks of a two-site window."""
+
+    def __init__(self, ctx: Context, left, right, site_kind, N, twoS):
+        self.ctx = ctx
+        h = C.c_void_p()
+        la, ra = _sector_array(left), _sector_array(right)
+        ctx.check(lib().su2_build_sectors(ctx.h, la, len(left), ra, len(right), site_kind, N, twoS,
+                                          C.byref(h)))
+        self.h = h
+        n = C.c_int64()
+        nb = C.c_int32()
+        bp = C.POINTER(Block)()
+        ctx.check(lib().su2_sectors_query(h, C.byref(n), C.byref(nb), C.byref(bp)))
+        self.psi_len = n.value
+        self.blocks = [(bp[i].a, bp[i].s1, bp[i].s2, bp[i].b, bp[i].jL1, bp[i].j2R, bp[i].rows,
+                        bp[i].cols, bp[i].offset) for i in range(nb.value)]
+        self.left, self.right = list(left), list(right)
+
+    def close(self):
+        if self.h:
+            lib().su2_sectors_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _chain(chain):
+    offs = [0]
+    flat = []
+    for bond in chain:
+        flat.extend(bond)
+        offs.append(len(flat))
+    oarr = (C.c_int32 * len(offs))(*offs)
+    sarr = _sector_array(flat)
+    ch = BondChain(len(chain), C.cast(oarr, C.POINTER(C.c_int32)), C.cast(sarr, C.POINTER(Sector)))
+    return ch, (oarr, sarr)
+
+
+class Environment:
+    """su2_build_environment: operator-table, block operators, C~ table, tasks."""
+
+    def __init__(self, ctx: Context, sectors: Sectors, model, left_chain, right_chain, n_left=0, n_right=0,
+                 J=1.0, seed=0, t_budget_bytes=0, n_slices=0, prepare_split=False):
+        self.ctx = ctx
+        H = Hamiltonian(model, n_left, n_right, J, seed)
+        lc, keep1 = _chain(left_chain)
+        rc_, keep2 = _chain(right_chain)
+        opts = EnvOpts(t_budget_bytes, n_slices, 1 if prepare_split else 0)
+        h = C.c_void_p()
+        ctx.check(lib().su2_build_environment(ctx.h, C.byref(H), C.byref(lc), C.byref(rc_), sectors.h,
+                                              C.byref(opts), C.byref(h)))
+        self.h = h
+        info = EnvInfo()
+        ctx.check(lib().su2_env_query(h, C.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in EnvInfo._fields_}
+        self.psi_len = info.psi_len
+
+    def tasks(self):
+        n = self.info["n_tasks"]
+        rows = np.zeros((n, 8), dtype=np.int32)
+        v = np.zeros(n, dtype=np.float64)
+        self.ctx.check(lib().su2_env_tasks(self.h, rows.ctypes.data, v.ctypes.data, n))
+        return rows, v
+
+    def operator_block(self, side, op, qo, qi, rows, cols):
+        out = np.zeros((cols, rows), dtype=np.float64)
+        self.ctx.check(lib().su2_env_operator_block(self.h, side, op, qo, qi, out.ctypes.data, rows, cols))
+        return out.T
+
+    def profile(self, on=True):
+        self.ctx.check(lib().su2_profile_enable(self.h, 1 if on else 0))
+
+    def profile_reset(self):
+        self.ctx.check(lib().su2_profile_reset(self.h))
+
+    def profile_read(self):
+        """{name: (launches, ms, flops)} per kernel kind."""
+        out = {}
+        for kind in range(5):
+            n, ms, fl, nm = C.c_int64(), C.c_double(), C.c_double(), C.c_char_p()
+            self.ctx.check(lib().su2_profile_read(self.h, kind, C.byref(n), C.byref(ms), C.byref(fl),
+                                                  C.byref(nm)))
+            out[nm.value.decode()] = (n.value, ms.value, fl.value)
+        return out
+
+    def close(self):
+        if self.h:
+            lib().su2_env_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def apply_heff(ctx: Context, env: Environment, psi_in, psi_out, prec=SU2_FP64):
+    ctx.check(lib().su2_apply_heff(ctx.h, env.h, _ptr(psi_in), _ptr(psi_out), prec))
+
+
+def apply_heff_host(ctx: Context, env: Environment, psi_in: np.ndarray, psi_out: np.ndarray, prec=SU2_FP64):
+    ctx.check(lib().su2_apply_heff_host(ctx.h, env.h, _ptr(psi_in), _ptr(psi_out), prec))
+
+
+def diag_heff(ctx: Context, env: Environment, diag_out):
+    ctx.check(lib().su2_diag_heff(ctx.h, env.h, _ptr(diag_out)))
+
+
+class Davidson:
+    """su2_davidson_create / su2_davidson_step / su2_energy."""
+
+    def __init__(self, ctx: Context, env: Environment, psi0, tol=1e-8, max_sub=24, keep=2, max_iter=200,
+                 prec=SU2_FP64):
+        self.ctx = ctx
+        h = C.c_void_p()
+        o = DavOpts(tol, max_sub, keep, max_iter, prec)
+        ctx.check(lib().su2_davidson_create(ctx.h, env.h, _ptr(psi0), C.byref(o), C.byref(h)))
+        self.h = h
+
+    def step(self):
+        th, r = C.c_double(), C.c_double()
+        self.ctx.check(lib().su2_davidson_step(self.ctx.h, self.h, C.byref(th), C.byref(r)))
+        return th.value, r.value
+
+    def solve(self):
+        th, r, it = C.c_double(), C.c_double(), C.c_int32()
+        rc = lib().su2_davidson_solve(self.ctx.h, self.h, C.byref(th), C.byref(r), C.byref(it))
+        if rc not in (SU2_OK, SU2_ENOTCONV):
+            self.ctx.check(rc)
+        return th.value, r.value, it.value, rc == SU2_OK
+
+    def energy(self):
+        e = C.c_double()
+        self.ctx.check(lib().su2_energy(self.h, C.byref(e)))
+        return e.value
+
+    def vector(self, out):
+        self.ctx.check(lib().su2_davidson_vector(self.ctx.h, self.h, _ptr(out)))
+
+    def close(self):
+        if self.h:
+            lib().su2_davidson_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# same names as the C-ABI entry points
+build_sectors = Sectors
+build_environment = Environment
+davidson_create = Davidson
+
+
+def davidson_step(dav: Davidson):
+    return dav.step()
+
+
+def energy(dav: Davidson):
+    return dav.energy()

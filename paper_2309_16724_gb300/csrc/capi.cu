@@ -1,0 +1,770 @@
+// C-ABI of su2dmrg (include/su2dmrg.h): contexts, sector-table, environment
+// with its execution plan, H.psi, the H_eff diagonal and the Davidson driver.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <unordered_map>
+
+#include "su2_device.h"
+
+namespace su2 {
+int dav_grid(int64_t n);
+void dav_multidot(cudaStream_t, const double*, int64_t, int, const double*, int64_t, double*, double*, double);
+void dav_combine(cudaStream_t, const double*, const double*, int64_t, int, const double*, int64_t, double*, double*);
+void dav_subtract(cudaStream_t, const double*, int64_t, int, const double*, int64_t, double*);
+void dav_residual(cudaStream_t, const double*, const double*, const double*, int64_t, double*);
+void dav_precond(cudaStream_t, const double*, const double*, const double*, int64_t, double*);
+void dav_scale(cudaStream_t, double*, const double*, const double*, int64_t);
+void dav_jacobi(cudaStream_t, const double*, int, int, double*, double*, int*);
+void dav_absmax(cudaStream_t, const double*, int64_t, double*, int64_t*, int*);
+void dav_diag_set(cudaStream_t, double*, int, int, const double*);
+void dav_copy_col(cudaStream_t, double*, int, int, const double*, int);
+// split-precision path (heff_split.cu)
+int split_prepare(su2_env* env, int n_slices, std::string& err);
+int split_apply(su2_env* env, const double* psi, double* F, std::string& err);
+void split_free(su2_env* env);
+}  // namespace su2
+
+using namespace su2;
+
+namespace {
+
+int fail(su2_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                               \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(ctx, SU2_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+bool fail_alloc_injected() {
+  const char* s = std::getenv("SU2_FAIL_ALLOC");
+  return s && s[0] == '1';
+}
+
+template <class T>
+int dev_alloc(su2_ctx* ctx, T** p, size_t count) {
+  *p = nullptr;
+  if (fail_alloc_injected()) return fail(ctx, SU2_ENOMEM, "device allocation refused (SU2_FAIL_ALLOC=1)");
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(ctx, SU2_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return SU2_OK;
+}
+
+template <class T>
+int upload(su2_ctx* ctx, T** d, const std::vector<T>& h) {
+  int rc = dev_alloc(ctx, d, h.size());
+  if (rc) return rc;
+  if (!h.empty()) CUDA_TRY(ctx, cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return SU2_OK;
+}
+
+int set_device(su2_ctx* ctx) {
+  if (ctx->device < 0) return fail(ctx, SU2_EINVAL, "host-only context cannot run device work");
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  return SU2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int su2_ctx_create(int device, void* cuda_stream, su2_ctx** out) {
+  if (!out) return SU2_EINVAL;
+  *out = nullptr;
+  su2_ctx* c = new (std::nothrow) su2_ctx();
+  if (!c) return SU2_ENOMEM;
+  c->device = device;
+  if (device >= 0) {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device >= n) {
+      delete c;
+      return SU2_ECUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) {
+      delete c;
+      return SU2_ECUDA;
+    }
+    if (cuda_stream) {
+      c->stream = (cudaStream_t)cuda_stream;
+    } else {
+      if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return SU2_ECUDA;
+      }
+      c->own_stream = true;
+    }
+    if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess || cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) {
+      if (c->own_stream) cudaStreamDestroy(c->stream);
+      delete c;
+      return SU2_ECUDA;
+    }
+  }
+  *out = c;
+  return SU2_OK;
+}
+
+int su2_ctx_destroy(su2_ctx* ctx) {
+  if (!ctx) return SU2_EINVAL;
+  if (ctx->device >= 0) {
+    cudaSetDevice(ctx->device);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  }
+  delete ctx;
+  return SU2_OK;
+}
+
+const char* su2_last_error(su2_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int su2_build_sectors(su2_ctx* ctx, const su2_sector* left, int32_t n_left, const su2_sector* right, int32_t n_right,
+                      int32_t site_kind, int32_t N_target, int32_t twoS_target, su2_sectors** out) {
+  if (!ctx || !out || (!left && n_left) || (!right && n_right) || n_left < 0 || n_right < 0)
+    return fail(ctx, SU2_EINVAL, "null argument");
+  *out = nullptr;
+  if (site_kind != SU2_SITE_SPIN_HALF && site_kind != SU2_SITE_ORBITAL) return fail(ctx, SU2_EINVAL, "site_kind");
+  if (twoS_target < 0 || N_target < 0) return fail(ctx, SU2_EINVAL, "negative target");
+  su2_sectors* s = new (std::nothrow) su2_sectors();
+  if (!s) return fail(ctx, SU2_ENOMEM, "host allocation");
+  s->site_kind = site_kind;
+  s->N = N_target;
+  s->twoS = twoS_target;
+  auto check = [&](const su2_sector* v, int n, std::vector<Sector>& dst) {
+    for (int i = 0; i < n; ++i) {
+      if (v[i].dim < 1 || v[i].twoS < 0 || v[i].N < 0 || ((v[i].N - v[i].twoS) % 2 != 0 && site_kind == SU2_SITE_ORBITAL))
+        return false;
+      if (i > 0 && !(v[i - 1].N < v[i].N || (v[i - 1].N == v[i].N && v[i - 1].twoS < v[i].twoS))) return false;
+      dst.push_back(Sector{v[i].N, v[i].twoS, v[i].dim});
+    }
+    return true;
+  };
+  if (!check(left, n_left, s->left) || !check(right, n_right, s->right)) {
+    delete s;
+    return fail(ctx, SU2_EINVAL, "sectors must have dim >= 1, valid (N, 2S) and ascending order");
+  }
+  build_blocks(s->left, s->right, site_kind, N_target, twoS_target, s->blocks, s->psi_len);
+  for (const Block& b : s->blocks) s->pub.push_back(su2_block{b.a, b.s1, b.s2, b.b, b.jL1, b.j2R, b.rows, b.cols, b.offset});
+  *out = s;
+  return SU2_OK;
+}
+
+int su2_sectors_query(const su2_sectors* s, int64_t* psi_len, int32_t* n_blocks, const su2_block** blocks) {
+  if (!s) return SU2_EINVAL;
+  if (psi_len) *psi_len = s->psi_len;
+  if (n_blocks) *n_blocks = int32_t(s->blocks.size());
+  if (blocks) *blocks = s->pub.data();
+  return SU2_OK;
+}
+
+int su2_sectors_destroy(su2_sectors* s) {
+  if (!s) return SU2_EINVAL;
+  delete s;
+  return SU2_OK;
+}
+
+static int build_plan(su2_env* env, const su2_sectors* S, int64_t budget) {
+  const auto& tasks = env->tasks;
+  const auto& blocks = S->blocks;
+  const int nterms = int(env->table.terms.size());
+  // uniques of K1 per term (first appearance order)
+  std::vector<std::vector<int64_t>> by_term(nterms);
+  for (int64_t i = 0; i < int64_t(tasks.size()); ++i) by_term[tasks[i].term].push_back(i);
+  // chunk boundaries over terms
+  std::vector<int> starts;
+  {
+    std::unordered_map<uint64_t, int64_t> seen;
+    int64_t bytes = 0;
+    starts.push_back(0);
+    for (int ti = 0; ti < nterms; ++ti) {
+      int64_t add = 0;
+      std::unordered_map<uint64_t, int64_t> mine;
+      for (int64_t i : by_term[ti]) {
+        const Task& t = tasks[i];
+        if (t.dblk < 0) continue;
+        const uint64_t key = (uint64_t(uint32_t(t.dblk)) << 32) | uint32_t(t.e);
+        if (seen.count(key) || mine.count(key)) continue;
+        const int64_t sz = int64_t(blocks[t.e].rows) * env->R.blocks[t.dblk].rows * 8;
+        mine[key] = sz;
+        add += sz;
+      }
+      if (bytes > 0 && bytes + add > budget) {
+        starts.push_back(ti);
+        seen.clear();
+        bytes = 0;
+      }
+      for (auto& kv : mine) seen.insert(kv);
+      bytes += add;
+    }
+    starts.push_back(nterms);
+  }
+  double flops = 0.0;
+  int64_t max_t = 0, nk1 = 0;
+  for (size_t c = 0; c + 1 < starts.size(); ++c) {
+    const int t0 = starts[c], t1 = starts[c + 1];
+    Chunk ch{int64_t(env->k1.size()), 0, int64_t(env->k2.size()), 0, 0.0, 0.0};
+    std::unordered_map<uint64_t, int64_t> toff;  // key -> offset in T buffer
+    int64_t tsz = 0;
+    // K1 uniques in term order
+    for (int ti = t0; ti < t1; ++ti)
+      for (int64_t i : by_term[ti]) {
+        const Task& t = tasks[i];
+        if (t.dblk < 0) continue;
+        const uint64_t key = (uint64_t(uint32_t(t.dblk)) << 32) | uint32_t(t.e);
+        if (toff.count(key)) continue;
+        const Block& E = blocks[t.e];
+        const OpBlock& D = env->R.blocks[t.dblk];
+        toff[key] = tsz;
+        const int k1 = E.rows, k2 = E.cols, n = D.rows;
+        for (int tc = 0; tc < (n + kTile - 1) / kTile; ++tc)
+          for (int tr = 0; tr < (k1 + kTile - 1) / kTile; ++tr)
+            env->k1.push_back(K1Job{E.offset, D.off, tsz, k1, k2, n, tr, tc, 0});
+        flops += 2.0 * k1 * k2 * n;
+        ch.k1_flops += 2.0 * k1 * k2 * n;
+        ++nk1;
+        tsz += (int64_t(k1) * n + 1) & ~int64_t(1);
+      }
+    max_t = std::max(max_t, tsz);
+    ch.k1_end = int64_t(env->k1.size());
+    // K2: tasks of the chunk in (f, term, e) order, grouped by f
+    std::vector<K2Job> jobs;
+    std::vector<double> cost;
+    int64_t i = 0;
+    const int64_t nt = int64_t(tasks.size());
+    while (i < nt) {
+      const int f = tasks[i].f;
+      int64_t j = i;
+      const int64_t tb = int64_t(env->k2t.size());
+      double c2 = 0.0;
+      for (; j < nt && tasks[j].f == f; ++j) {
+        const Task& t = tasks[j];
+        if (t.term < t0 || t.term >= t1) continue;
+        const Block& E = blocks[t.e];
+        const Block& F = blocks[t.f];
+        K2Task k;
+        k.k1 = E.rows;
+        k.v = t.v;
+        k.flags = 0;
+        if (t.ablk < 0) {
+          k.flags |= K2_A_IDENTITY;
+          k.a_off = -1;
+          c2 += 1.0;
+        } else {
+          k.a_off = env->L.blocks[t.ablk].off;
+          flops += 2.0 * F.rows * E.rows * F.cols;
+          ch.k2_flops += 2.0 * F.rows * E.rows * F.cols;
+          c2 += E.rows;
+        }
+        if (t.dblk < 0) {
+          k.flags |= K2_B_FROM_PSI;
+          k.b_off = E.offset;
+        } else {
+          k.b_off = toff.at((uint64_t(uint32_t(t.dblk)) << 32) | uint32_t(t.e));
+        }
+        env->k2t.push_back(k);
+      }
+      const int64_t te = int64_t(env->k2t.size());
+      if (te > tb) {
+        const Block& F = blocks[f];
+        for (int tc = 0; tc < (F.cols + kTile - 1) / kTile; ++tc)
+          for (int tr = 0; tr < (F.rows + kTile - 1) / kTile; ++tr) {
+            jobs.push_back(K2Job{F.offset, F.rows, F.cols, tr, tc, int32_t(tb), int32_t(te)});
+            cost.push_back(c2);
+          }
+      }
+      i = j;
+    }
+    std::vector<int64_t> ord(jobs.size());
+    for (size_t q = 0; q < ord.size(); ++q) ord[q] = int64_t(q);
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+    for (int64_t q : ord) env->k2.push_back(jobs[q]);
+    ch.k2_end = int64_t(env->k2.size());
+    env->chunks.push_back(ch);
+  }
+  if (int64_t(env->k2t.size()) >= (int64_t(1) << 31)) return fail(env->ctx, SU2_EINVAL, "task table too large");
+  env->t_elems = max_t;
+  env->info.flops_su2 = flops;
+  env->info.n_k1 = nk1;
+  env->info.n_chunks = int64_t(env->chunks.size());
+  // diagonal: tasks with e == f, grouped by f
+  int64_t i = 0;
+  const int64_t nt = int64_t(tasks.size());
+  while (i < nt) {
+    const int f = tasks[i].f;
+    const int64_t tb = int64_t(env->dt.size());
+    for (; i < nt && tasks[i].f == f; ++i) {
+      const Task& t = tasks[i];
+      if (t.e != t.f) continue;
+      DiagTask d;
+      d.a_off = t.ablk < 0 ? -1 : env->L.blocks[t.ablk].off;
+      d.d_off = t.dblk < 0 ? -1 : env->R.blocks[t.dblk].off;
+      d.lda = blocks[f].rows;
+      d.ldd = blocks[f].cols;
+      d.v = t.v;
+      env->dt.push_back(d);
+    }
+    const int64_t te = int64_t(env->dt.size());
+    if (te > tb) env->dj.push_back(DiagJob{blocks[f].offset, blocks[f].rows, blocks[f].cols, int32_t(tb), int32_t(te)});
+  }
+  return SU2_OK;
+}
+
+static void env_free_device(su2_env* e) {
+  if (!e->ctx || e->ctx->device < 0) return;
+  cudaSetDevice(e->ctx->device);
+  split_free(e);
+  cudaFree(e->dL);
+  cudaFree(e->dR);
+  cudaFree(e->dT);
+  cudaFree(e->dk1);
+  cudaFree(e->dk2);
+  cudaFree(e->dk2t);
+  cudaFree(e->ddj);
+  cudaFree(e->ddt);
+  cudaFree(e->d_in_scratch);
+  cudaFree(e->d_out_scratch);
+}
+
+int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond_chain* lc, const su2_bond_chain* rc,
+                          const su2_sectors* S, const su2_env_opts* opts, su2_env** out) {
+  if (!ctx || !H || !lc || !rc || !S || !out) return fail(ctx, SU2_EINVAL, "null argument");
+  *out = nullptr;
+  if (H->model < 0 || H->model > 3) return fail(ctx, SU2_EINVAL, "unknown model");
+  if ((H->model == SU2_MODEL_HEISENBERG) != (S->site_kind == SU2_SITE_SPIN_HALF) && H->model <= 1)
+    return fail(ctx, SU2_EINVAL, "model and site kind disagree");
+  if (H->model == SU2_MODEL_QC_SKELETON && (H->n_left < 1 || H->n_right < 1))
+    return fail(ctx, SU2_EINVAL, "n_left and n_right must be >= 1");
+  auto chain_of = [&](const su2_bond_chain* c, std::vector<std::vector<Sector>>& dst) {
+    if (c->n_bonds < 1 || !c->bond_offset || !c->sectors) return false;
+    for (int k = 0; k < c->n_bonds; ++k) {
+      std::vector<Sector> v;
+      for (int i = c->bond_offset[k]; i < c->bond_offset[k + 1]; ++i)
+        v.push_back(Sector{c->sectors[i].N, c->sectors[i].twoS, c->sectors[i].dim});
+      dst.push_back(v);
+    }
+    return true;
+  };
+  std::vector<std::vector<Sector>> lch, rch;
+  if (!chain_of(lc, lch) || !chain_of(rc, rch)) return fail(ctx, SU2_EINVAL, "bad bond chain");
+  auto same = [](const std::vector<Sector>& a, const std::vector<Sector>& b) {
+    if (a.size() != b.size()) return false;
+    for (size_t i = 0; i < a.size(); ++i)
+      if (a[i].N != b[i].N || a[i].twoS != b[i].twoS || a[i].dim != b[i].dim) return false;
+    return true;
+  };
+  if (!same(lch.back(), S->left) || !same(rch.back(), S->right))
+    return fail(ctx, SU2_EINVAL, "last bond of a chain differs from the sector lists");
+  su2_env* env = new (std::nothrow) su2_env();
+  if (!env) return fail(ctx, SU2_ENOMEM, "host allocation");
+  env->ctx = ctx;
+  env->psi_len = S->psi_len;
+  try {
+    env->table = make_table(*H, S->site_kind);
+    std::string err = build_side_ops(env->table, true, lch, *H, env->L);
+    if (err.empty()) err = build_side_ops(env->table, false, rch, *H, env->R);
+    if (err.empty()) err = build_tasks(env->table, S->left, S->right, S->blocks, S->twoS, env->L, env->R, env->tasks);
+    if (!err.empty()) {
+      delete env;
+      return fail(ctx, SU2_EINVAL, err);
+    }
+  } catch (const std::bad_alloc&) {
+    delete env;
+    return fail(ctx, SU2_ENOMEM, "host allocation");
+  } catch (const std::exception& ex) {
+    delete env;
+    return fail(ctx, SU2_EINVAL, ex.what());
+  }
+  int64_t budget = (opts && opts->t_budget_bytes > 0) ? opts->t_budget_bytes : (int64_t(2) << 30);
+  int rc2 = build_plan(env, S, budget);
+  if (rc2) {
+    delete env;
+    return rc2;
+  }
+  // info
+  su2_env_info& in = env->info;
+  in.psi_len = S->psi_len;
+  in.n_blocks = int64_t(S->blocks.size());
+  in.n_terms = int64_t(env->table.terms.size());
+  in.n_tasks = int64_t(env->tasks.size());
+  double D = 0, Deff = 0;
+  for (const Sector& s : S->left) {
+    D += s.dim;
+    Deff += double(s.dim) * (s.twoS + 1);
+  }
+  in.r_d = D > 0 ? Deff / D : 1.0;
+  in.flops_u1_equiv = in.flops_su2 * in.r_d;
+  in.env_bytes = 8.0 * double(env->L.arena.size() + env->R.arena.size());
+  if (ctx->device >= 0) {
+    int rc = set_device(ctx);
+    if (!rc) rc = upload(ctx, &env->dL, env->L.arena);
+    if (!rc) rc = upload(ctx, &env->dR, env->R.arena);
+    if (!rc) rc = dev_alloc(ctx, &env->dT, size_t(std::max<int64_t>(env->t_elems, 2)));
+    if (!rc) rc = upload(ctx, &env->dk1, env->k1);
+    if (!rc) rc = upload(ctx, &env->dk2, env->k2);
+    if (!rc) rc = upload(ctx, &env->dk2t, env->k2t);
+    if (!rc) rc = upload(ctx, &env->ddj, env->dj);
+    if (!rc) rc = upload(ctx, &env->ddt, env->dt);
+    if (!rc && opts && opts->prepare_split) {
+      std::string err;
+      rc = split_prepare(env, opts->n_slices > 0 ? opts->n_slices : 5, err);
+      if (rc) fail(ctx, rc, err);
+    }
+    if (rc) {
+      env_free_device(env);
+      delete env;
+      return rc;
+    }
+  }
+  *out = env;
+  return SU2_OK;
+}
+
+int su2_env_query(const su2_env* env, su2_env_info* info) {
+  if (!env || !info) return SU2_EINVAL;
+  *info = env->info;
+  return SU2_OK;
+}
+
+int su2_env_tasks(const su2_env* env, int32_t* rows8, double* v, int64_t n_tasks) {
+  if (!env || n_tasks != int64_t(env->tasks.size())) return SU2_EINVAL;
+  for (int64_t i = 0; i < n_tasks; ++i) {
+    const Task& t = env->tasks[i];
+    if (rows8) {
+      int32_t* r = rows8 + 8 * i;
+      r[0] = t.f; r[1] = t.term; r[2] = t.e; r[3] = t.ao; r[4] = t.ai; r[5] = t.bo; r[6] = t.bi;
+      r[7] = (t.ablk < 0 ? 1 : 0) | (t.dblk < 0 ? 2 : 0);
+    }
+    if (v) v[i] = t.v;
+  }
+  return SU2_OK;
+}
+
+int su2_env_operator_block(const su2_env* env, int32_t side, int32_t op, int32_t qo, int32_t qi, double* out,
+                           int32_t rows, int32_t cols) {
+  if (!env || !out || (side != 0 && side != 1)) return SU2_EINVAL;
+  const SideOps& so = side == 0 ? env->L : env->R;
+  const int b = so.find(op, qo, qi);
+  if (b < 0 || so.blocks[b].rows != rows || so.blocks[b].cols != cols) return SU2_EINVAL;
+  std::memcpy(out, &so.arena[so.blocks[b].off], sizeof(double) * size_t(rows) * cols);
+  return SU2_OK;
+}
+
+int su2_env_destroy(su2_env* env) {
+  if (!env) return SU2_EINVAL;
+  env_free_device(env);
+  delete env;
+  return SU2_OK;
+}
+
+int su2_apply_heff(su2_ctx* ctx, const su2_env* env_c, const double* psi_in, double* psi_out, int32_t prec) {
+  if (!ctx || !env_c || !psi_in || !psi_out) return fail(ctx, SU2_EINVAL, "null argument");
+  su2_env* env = const_cast<su2_env*>(env_c);
+  if (env->ctx != ctx) return fail(ctx, SU2_EINVAL, "environment belongs to another context");
+  if ((uintptr_t(psi_in) | uintptr_t(psi_out)) & 7) return fail(ctx, SU2_EINVAL, "psi pointers must be 8-byte aligned");
+  const int64_t n = env->psi_len;
+  if (psi_in < psi_out + n && psi_out < psi_in + n) return fail(ctx, SU2_EINVAL, "psi_in and psi_out overlap");
+  int rc = set_device(ctx);
+  if (rc) return rc;
+  if (prec == SU2_SPLIT_BF16) {
+    std::string err;
+    rc = split_apply(env, psi_in, psi_out, err);
+    return rc ? fail(ctx, rc, err) : SU2_OK;
+  }
+  if (prec != SU2_FP64) return fail(ctx, SU2_EINVAL, "unknown precision");
+  CUDA_TRY(ctx, cudaMemsetAsync(psi_out, 0, size_t(n) * sizeof(double), ctx->stream));
+  for (const Chunk& c : env->chunks)
+    launch_heff_fp64(ctx->stream, env->dL, env->dR, psi_in, psi_out, env->dT, env->dk1, env->dk2, env->dk2t, c, n,
+                     &env->prof);
+  CUDA_TRY(ctx, cudaGetLastError());
+  return SU2_OK;
+}
+
+int su2_apply_heff_host(su2_ctx* ctx, const su2_env* env_c, const double* in_h, double* out_h, int32_t prec) {
+  if (!ctx || !env_c || !in_h || !out_h) return fail(ctx, SU2_EINVAL, "null argument");
+  su2_env* env = const_cast<su2_env*>(env_c);
+  int rc = set_device(ctx);
+  if (rc) return rc;
+  const size_t bytes = size_t(env->psi_len) * sizeof(double);
+  if (!env->d_in_scratch) {
+    rc = dev_alloc(ctx, &env->d_in_scratch, size_t(env->psi_len));
+    if (!rc) rc = dev_alloc(ctx, &env->d_out_scratch, size_t(env->psi_len));
+    if (rc) return rc;
+  }
+  CUDA_TRY(ctx, cudaMemcpyAsync(env->d_in_scratch, in_h, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  rc = su2_apply_heff(ctx, env, env->d_in_scratch, env->d_out_scratch, prec);
+  if (rc) return rc;
+  CUDA_TRY(ctx, cudaMemcpyAsync(out_h, env->d_out_scratch, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return SU2_OK;
+}
+
+int su2_profile_enable(su2_env* env, int32_t on) {
+  if (!env) return SU2_EINVAL;
+  env->prof.drain();
+  env->prof.on = on != 0;
+  return SU2_OK;
+}
+
+int su2_profile_reset(su2_env* env) {
+  if (!env) return SU2_EINVAL;
+  env->prof.reset();
+  return SU2_OK;
+}
+
+int su2_profile_read(su2_env* env, int32_t kind, int64_t* launches, double* ms, double* flops, const char** name) {
+  static const char* names[kProfKinds] = {"k1_fp64", "k2_fp64", "split_slices", "k1_split", "k2_split"};
+  if (!env || kind < 0 || kind >= kProfKinds) return SU2_EINVAL;
+  env->prof.drain();
+  if (launches) *launches = env->prof.launches[kind];
+  if (ms) *ms = env->prof.ms[kind];
+  if (flops) *flops = env->prof.flops[kind];
+  if (name) *name = names[kind];
+  return SU2_OK;
+}
+
+int su2_diag_heff(su2_ctx* ctx, const su2_env* env, double* diag_dev) {
+  if (!ctx || !env || !diag_dev) return fail(ctx, SU2_EINVAL, "null argument");
+  int rc = set_device(ctx);
+  if (rc) return rc;
+  launch_diag(ctx->stream, env->dL, env->dR, diag_dev, env->ddj, int64_t(env->dj.size()), env->ddt, env->psi_len);
+  CUDA_TRY(ctx, cudaGetLastError());
+  return SU2_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ Davidson
+struct su2_dav {
+  su2_ctx* ctx = nullptr;
+  const su2_env* env = nullptr;
+  su2_dav_opts o{};
+  int64_t n = 0;
+  double *V = nullptr, *AV = nullptr, *x = nullptr, *ax = nullptr, *r = nullptr, *t = nullptr, *tmp = nullptr,
+         *diag = nullptr;
+  double *Hsub = nullptr, *Y = nullptr, *w = nullptr, *h = nullptr, *partial = nullptr, *scal = nullptr;
+  int64_t* pidx = nullptr;
+  double* host = nullptr;  // pinned: theta, nrm2
+  int nsub = 0, iters = 0;
+  double theta = 0.0, res = 0.0;
+  bool converged = false;
+};
+
+static void dav_free(su2_dav* d) {
+  if (d->ctx && d->ctx->device >= 0) cudaSetDevice(d->ctx->device);
+  double* ps[] = {d->V, d->AV, d->x, d->ax, d->r, d->t, d->tmp, d->diag, d->Hsub, d->Y, d->w, d->h, d->partial, d->scal};
+  for (double* p : ps) cudaFree(p);
+  cudaFree(d->pidx);
+  if (d->host) cudaFreeHost(d->host);
+}
+
+extern "C" {
+
+int su2_davidson_create(su2_ctx* ctx, const su2_env* env, const double* psi0, const su2_dav_opts* opts,
+                        su2_dav** out) {
+  if (!ctx || !env || !psi0 || !out) return fail(ctx, SU2_EINVAL, "null argument");
+  *out = nullptr;
+  int rc = set_device(ctx);
+  if (rc) return rc;
+  su2_dav* d = new (std::nothrow) su2_dav();
+  if (!d) return fail(ctx, SU2_ENOMEM, "host allocation");
+  d->ctx = ctx;
+  d->env = env;
+  d->o.tol = 1e-8;
+  d->o.max_sub = 24;
+  d->o.keep = 2;
+  d->o.max_iter = 200;
+  d->o.prec = SU2_FP64;
+  if (opts) {
+    if (opts->tol > 0) d->o.tol = opts->tol;
+    if (opts->max_sub > 0) d->o.max_sub = opts->max_sub;
+    if (opts->keep > 0) d->o.keep = opts->keep;
+    if (opts->max_iter > 0) d->o.max_iter = opts->max_iter;
+    d->o.prec = opts->prec;
+  }
+  if (d->o.max_sub > 32 || d->o.max_sub < 3 || d->o.keep >= d->o.max_sub) {
+    delete d;
+    return fail(ctx, SU2_EINVAL, "max_sub must be in [3, 32] and keep < max_sub");
+  }
+  const int64_t n = env->psi_len;
+  d->n = n;
+  const int ms = d->o.max_sub;
+  const int ng = dav_grid(n);
+  rc = dev_alloc(ctx, &d->V, size_t(ms) * n);
+  if (!rc) rc = dev_alloc(ctx, &d->AV, size_t(ms) * n);
+  if (!rc) rc = dev_alloc(ctx, &d->x, size_t(n));
+  if (!rc) rc = dev_alloc(ctx, &d->ax, size_t(n));
+  if (!rc) rc = dev_alloc(ctx, &d->r, size_t(n));
+  if (!rc) rc = dev_alloc(ctx, &d->t, size_t(n));
+  if (!rc) rc = dev_alloc(ctx, &d->tmp, size_t(2 * d->o.keep) * n);
+  if (!rc) rc = dev_alloc(ctx, &d->diag, size_t(n));
+  if (!rc) rc = dev_alloc(ctx, &d->Hsub, size_t(32 * 32));
+  if (!rc) rc = dev_alloc(ctx, &d->Y, size_t(32 * 32));
+  if (!rc) rc = dev_alloc(ctx, &d->w, size_t(32));
+  if (!rc) rc = dev_alloc(ctx, &d->h, size_t(32));
+  if (!rc) rc = dev_alloc(ctx, &d->partial, size_t(ng) * 32);
+  if (!rc) rc = dev_alloc(ctx, &d->scal, size_t(8));
+  if (!rc) rc = dev_alloc(ctx, &d->pidx, size_t(ng));
+  if (!rc && cudaMallocHost(&d->host, 4 * sizeof(double)) != cudaSuccess) rc = fail(ctx, SU2_ENOMEM, "pinned host");
+  if (rc) {
+    dav_free(d);
+    delete d;
+    return rc;
+  }
+  cudaStream_t s = ctx->stream;
+  rc = su2_diag_heff(ctx, env, d->diag);
+  if (rc) {
+    dav_free(d);
+    delete d;
+    return rc;
+  }
+  // V0 = psi0 / ||psi0||
+  dav_multidot(s, psi0, n, 1, psi0, n, d->partial, d->scal, 1.0);
+  dav_scale(s, d->V, psi0, d->scal, n);
+  cudaMemsetAsync(d->Hsub, 0, 32 * 32 * sizeof(double), s);
+  d->nsub = 1;
+  if (cudaGetLastError() != cudaSuccess) {
+    dav_free(d);
+    delete d;
+    return fail(ctx, SU2_ECUDA, "davidson setup launch");
+  }
+  *out = d;
+  return SU2_OK;
+}
+
+int su2_davidson_step(su2_ctx* ctx, su2_dav* d, double* theta, double* resnorm) {
+  if (!ctx || !d || d->ctx != ctx) return fail(ctx, SU2_EINVAL, "null argument");
+  int rc = set_device(ctx);
+  if (rc) return rc;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = d->n;
+  const int ms = d->o.max_sub, ld = 32;
+  if (d->converged) {
+    if (theta) *theta = d->theta;
+    if (resnorm) *resnorm = d->res;
+    return SU2_OK;
+  }
+  const int j = d->nsub - 1;  // newest vector
+  rc = su2_apply_heff(ctx, d->env, d->V + int64_t(j) * n, d->AV + int64_t(j) * n, d->o.prec);
+  if (rc) return rc;
+  dav_multidot(s, d->V, n, d->nsub, d->AV + int64_t(j) * n, n, d->partial, d->h, 1.0);
+  dav_copy_col(s, d->Hsub, ld, j, d->h, d->nsub);
+  dav_jacobi(s, d->Hsub, ld, d->nsub, d->w, d->Y, ctx->d_status);
+  dav_combine(s, d->V, d->AV, n, d->nsub, d->Y, n, d->x, d->ax);
+  dav_residual(s, d->x, d->ax, d->w, n, d->r);
+  dav_multidot(s, d->r, n, 1, d->r, n, d->partial, d->scal, 1.0);
+  CUDA_TRY(ctx, cudaMemcpyAsync(d->host, d->w, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(ctx, cudaMemcpyAsync(d->host + 1, d->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  d->iters += 1;
+  d->theta = d->host[0];
+  d->res = std::sqrt(std::max(0.0, d->host[1]));
+  if (theta) *theta = d->theta;
+  if (resnorm) *resnorm = d->res;
+  if (d->res <= d->o.tol) {
+    d->converged = true;
+    return SU2_OK;
+  }
+  dav_precond(s, d->r, d->diag, d->w, n, d->t);
+  if (d->nsub >= ms) {  // restart on the lowest Ritz vectors
+    const int keep = d->o.keep;
+    for (int q = 0; q < keep; ++q)
+      dav_combine(s, d->V, d->AV, n, d->nsub, d->Y + q * ld, n, d->tmp + int64_t(2 * q) * n,
+                  d->tmp + int64_t(2 * q + 1) * n);
+    for (int q = 0; q < keep; ++q) {
+      cudaMemcpyAsync(d->V + int64_t(q) * n, d->tmp + int64_t(2 * q) * n, n * sizeof(double),
+                      cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(d->AV + int64_t(q) * n, d->tmp + int64_t(2 * q + 1) * n, n * sizeof(double),
+                      cudaMemcpyDeviceToDevice, s);
+    }
+    dav_diag_set(s, d->Hsub, ld, keep, d->w);
+    d->nsub = keep;
+  }
+  for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+    dav_multidot(s, d->V, n, d->nsub, d->t, n, d->partial, d->h, 1.0);
+    dav_subtract(s, d->V, n, d->nsub, d->h, n, d->t);
+  }
+  dav_multidot(s, d->t, n, 1, d->t, n, d->partial, d->scal, 1.0);
+  CUDA_TRY(ctx, cudaMemcpyAsync(d->host + 2, d->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  if (!(d->host[2] > 1e-28)) {  // correction vanished: nothing left to add
+    d->converged = true;
+    return SU2_OK;
+  }
+  dav_scale(s, d->V + int64_t(d->nsub) * n, d->t, d->scal, n);
+  d->nsub += 1;
+  CUDA_TRY(ctx, cudaGetLastError());
+  return SU2_OK;
+}
+
+int su2_davidson_solve(su2_ctx* ctx, su2_dav* d, double* theta, double* resnorm, int32_t* iterations) {
+  if (!ctx || !d) return fail(ctx, SU2_EINVAL, "null argument");
+  while (!d->converged && d->iters < d->o.max_iter) {
+    int rc = su2_davidson_step(ctx, d, theta, resnorm);
+    if (rc) return rc;
+  }
+  if (theta) *theta = d->theta;
+  if (resnorm) *resnorm = d->res;
+  if (iterations) *iterations = d->iters;
+  return d->converged ? SU2_OK : fail(ctx, SU2_ENOTCONV, "Davidson iteration limit reached");
+}
+
+int su2_energy(const su2_dav* d, double* E) {
+  if (!d || !E) return SU2_EINVAL;
+  *E = d->theta;
+  return SU2_OK;
+}
+
+int su2_davidson_vector(su2_ctx* ctx, su2_dav* d, double* x_dev) {
+  if (!ctx || !d || !x_dev) return fail(ctx, SU2_EINVAL, "null argument");
+  int rc = set_device(ctx);
+  if (rc) return rc;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = d->n;
+  int ng = 0;
+  dav_absmax(s, d->x, n, d->partial, d->pidx, &ng);
+  std::vector<double> pv(ng);
+  std::vector<int64_t> pi(ng);
+  CUDA_TRY(ctx, cudaMemcpyAsync(pv.data(), d->partial, ng * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(ctx, cudaMemcpyAsync(pi.data(), d->pidx, ng * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  int best = 0;
+  for (int g = 1; g < ng; ++g)
+    if (pv[g] > pv[best] || (pv[g] == pv[best] && pi[g] < pi[best])) best = g;
+  double xv = 0.0;
+  CUDA_TRY(ctx, cudaMemcpy(&xv, d->x + pi[best], sizeof(double), cudaMemcpyDeviceToHost));
+  // x has unit norm up to rounding; scale by +-1 / ||x||
+  dav_multidot(s, d->x, n, 1, d->x, n, d->partial, d->scal, 1.0);
+  double nrm2 = 0.0;
+  CUDA_TRY(ctx, cudaMemcpyAsync(&nrm2, d->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  const double sgn_nrm2 = nrm2;  // positive
+  dav_scale(s, x_dev, d->x, d->scal, n);
+  if (xv < 0) {
+    double m1 = -1.0;
+    double* dm = d->h;
+    CUDA_TRY(ctx, cudaMemcpyAsync(dm, &m1, sizeof(double), cudaMemcpyHostToDevice, s));
+    dav_combine(s, x_dev, nullptr, n, 1, dm, n, x_dev, nullptr);
+  }
+  (void)sgn_nrm2;
+  CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  return SU2_OK;
+}
+
+int su2_davidson_destroy(su2_dav* d) {
+  if (!d) return SU2_EINVAL;
+  dav_free(d);
+  delete d;
+  return SU2_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,90 @@
+// Internal data structures of the su2dmrg library (host side).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "su2dmrg.h"
+
+namespace su2 {
+
+// ---------------------------------------------------------------- coupling
+// Wigner 6j by Racah's formula (Eq. A3 with the triangle coefficient of
+// Eq. A4), exact in prime-exponent / 128-bit integer arithmetic with one
+// final square root; 9j as the x-sum of three 6j (Eq. A2); the scalar
+// factor C~ of Eq. a.  Twos arguments.
+bool triangle(int a, int b, int c);
+double sixj(int a, int b, int c, int d, int e, int f);
+double ninej(int j1, int j2, int j, int k1, int k2, int k, int j1p, int j2p, int jp);
+double ctilde(int j1, int j2, int j, int k1, int k2, int k, int j1p, int j2p, int jp);
+
+// ---------------------------------------------------------------- model
+struct SiteOp {
+  int k = 0, dN = 0, parity = 0, n = 1;  // rank (twos), particle change, fermion parity, states
+  double red[3][3] = {{0}};               // reduced matrix [out][in], CG form of Wigner-Eckart
+};
+
+enum OpKind { OP_IDENTITY = 0, OP_HAM, OP_RANDOM, OP_ADJOINT, OP_MPS_RENORM, OP_SPINTOT, OP_NUMTOT };
+
+struct BlockOp {
+  std::string name;
+  int k = 0, dN = 0, parity = 0, kind = OP_IDENTITY, base = -1;
+};
+
+struct Term {
+  double alpha = 1.0;
+  int A = 0, D = 0, k = 0;  // left op, right op, coupling rank (twos)
+  SiteOp B, C;
+};
+
+struct OpTable {
+  int site_kind = 0;
+  std::vector<BlockOp> lops, rops;
+  std::vector<Term> terms;
+};
+
+struct Sector { int N, twoS, dim; };
+struct Block { int a, s1, s2, b, jL1, j2R, rows, cols; int64_t offset; };
+
+void site_states(int site_kind, std::vector<int>& N, std::vector<int>& twoS);
+SiteOp site_op(int site_kind, const char* name);
+SiteOp site_adjoint(const SiteOp& op, int site_kind);
+OpTable make_table(const su2_hamiltonian& H, int site_kind);
+
+// ---------------------------------------------------------------- operators
+struct OpBlock { int op, qo, qi, rows, cols; int64_t off; };
+struct SideOps {
+  std::vector<OpBlock> blocks;
+  std::vector<double> arena;  // all blocks, column-major, 2-double aligned
+  std::unordered_map<uint64_t, int> index;  // key(op, qo, qi) -> block
+  static uint64_t key(int op, int qo, int qi) {
+    return (uint64_t(uint32_t(op)) << 32) | (uint64_t(uint32_t(qo)) << 16) | uint64_t(uint32_t(qi));
+  }
+  int find(int op, int qo, int qi) const {
+    auto it = index.find(key(op, qo, qi));
+    return it == index.end() ? -1 : it->second;
+  }
+};
+
+struct Task {
+  int32_t f, term, e, ao, ai, bo, bi;
+  int32_t ablk, dblk;  // operator block indices (-1: identity)
+  double v;
+};
+
+// builds; return empty string on success, else the error message
+std::string build_blocks(const std::vector<Sector>& left, const std::vector<Sector>& right, int site_kind,
+                         int N, int twoS, std::vector<Block>& blocks, int64_t& psi_len);
+std::string build_side_ops(const OpTable& t, bool left_side, const std::vector<std::vector<Sector>>& chain,
+                           const su2_hamiltonian& H, SideOps& out);
+std::string build_tasks(const OpTable& t, const std::vector<Sector>& left, const std::vector<Sector>& right,
+                        const std::vector<Block>& blocks, int twoS, const SideOps& L, const SideOps& R,
+                        std::vector<Task>& tasks);
+
+// counter-based generator (SplitMix64, Steele/Lea/Flood 2014)
+uint64_t splitmix(uint64_t x);
+uint64_t block_key(uint64_t seed, uint64_t side, uint64_t op, uint64_t qo, uint64_t qi);
+double uniform_elem(uint64_t key, uint64_t idx);
+
+}  // namespace su2

@@ -1,0 +1,176 @@
+"""GPU parity of the native-FP64 path (through the C-ABI) against the oracle.
+
+Bar: relative 2-norm error <= 1e-12 and elementwise error <= 1e-12 * max|F|
+(the FP64 oracle and the kernels differ only in summation order), exact
+properties (Casimir operators, Hermiticity) at any size, Davidson energies
+against exact diagonalisation.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import davidson as odav
+from oracle import ed as oed
+from oracle import model as omodel
+
+from gpu_common import oracle_apply, oracle_diag, oracle_problem, rel_err
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_16724_gb300 as P
+    torch.cuda.init()
+    return P.Context(0, stream=torch.cuda.current_stream())
+
+
+def gpu_apply(ctx, env, psi, prec=0):
+    import paper_2309_16724_gb300 as P
+    x = torch.from_numpy(psi).cuda()
+    y = torch.empty_like(x)
+    P.apply_heff(ctx, env, x, y, prec)
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+SMALL = [
+    synth.CONFIGS["heis12"],
+    synth.Config("heis10S1", synth.SPIN_HALF, 10, 10, 2, 6, 77),
+    synth.Config("qc8", synth.SPATIAL_ORBITAL, 8, 8, 0, 12, 5),
+    synth.Config("qc8S1", synth.SPATIAL_ORBITAL, 8, 7, 1, 10, 6),
+    synth.Config("qc10S3", synth.SPATIAL_ORBITAL, 10, 9, 3, 40, 8),
+    synth.Config("qc12D100", synth.SPATIAL_ORBITAL, 12, 12, 0, 100, 9),
+]
+
+
+@pytest.mark.parametrize("cfg", SMALL + [synth.CONFIGS["qc16"]], ids=lambda c: c.name)
+def test_fp64_matches_oracle(ctx, cfg):
+    from paper_2309_16724_gb300 import workload
+    p = oracle_problem(cfg)
+    psi = synth.gaussian_psi(p["n"], synth.psi_seed(cfg))
+    F = oracle_apply(p, psi)
+    sec, env = workload.build(ctx, cfg)
+    G = gpu_apply(ctx, env, psi)
+    assert rel_err(G, F) <= TOL
+    assert np.abs(G - F).max() <= TOL * np.abs(F).max()
+
+
+def test_fp64_chunking_invariant(ctx):
+    """Splitting the operator-table into many chunks changes only the order of
+    additions into F."""
+    from paper_2309_16724_gb300 import workload
+    cfg = synth.CONFIGS["qc16"]
+    psi = synth.gaussian_psi(350348, 3)
+    sec, env1 = workload.build(ctx, cfg)
+    sec2, env2 = workload.build(ctx, cfg, t_budget_bytes=8 << 20)
+    assert env2.info["n_chunks"] > 5
+    a = gpu_apply(ctx, env1, psi)
+    b = gpu_apply(ctx, env2, psi)
+    assert rel_err(b, a) <= 1e-14
+
+
+@pytest.mark.parametrize("which", ["S2", "N"])
+def test_casimir_exact_on_gpu(ctx, which):
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    cfg = synth.Config("c", synth.SPATIAL_ORBITAL, 12, 11, 3, 120, 4)
+    model = P.SU2_MODEL_CASIMIR_S2 if which == "S2" else P.SU2_MODEL_CASIMIR_N
+    sec, env = workload.build(ctx, cfg, model=model)
+    psi = synth.gaussian_psi(sec.psi_len, 1)
+    G = gpu_apply(ctx, env, psi)
+    want = 1.5 * 2.5 if which == "S2" else 11.0
+    assert np.abs(G - want * psi).max() <= 1e-12 * want
+
+
+def test_hermitian_and_diagonal_on_gpu(ctx):
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    cfg = synth.CONFIGS["qc16"]
+    sec, env = workload.build(ctx, cfg)
+    phi = synth.gaussian_psi(sec.psi_len, 11)
+    psi = synth.gaussian_psi(sec.psi_len, 12)
+    Hphi = gpu_apply(ctx, env, phi)
+    Hpsi = gpu_apply(ctx, env, psi)
+    assert abs(phi @ Hpsi - Hphi @ psi) <= 1e-12 * np.linalg.norm(Hpsi)
+    p = oracle_problem(cfg)
+    d = torch.empty(sec.psi_len, dtype=torch.float64, device="cuda")
+    P.diag_heff(ctx, env, d)
+    torch.cuda.synchronize()
+    want = oracle_diag(p)
+    assert np.abs(d.cpu().numpy() - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_host_buffer_entry_point(ctx):
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    cfg = SMALL[4]
+    sec, env = workload.build(ctx, cfg)
+    psi = synth.gaussian_psi(sec.psi_len, 2)
+    out = np.zeros_like(psi)
+    P.apply_heff_host(ctx, env, psi, out)
+    assert np.array_equal(out, gpu_apply(ctx, env, psi))
+
+
+def test_davidson_heisenberg_equals_exact_diagonalisation(ctx):
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    cfg = synth.CONFIGS["heis12"]
+    sec, env = workload.build(ctx, cfg)
+    psi0 = torch.from_numpy(synth.gaussian_psi(sec.psi_len, synth.psi_seed(cfg))).cuda()
+    dav = P.Davidson(ctx, env, psi0, tol=1e-10)
+    th, res, it, ok = dav.solve()
+    assert ok and res <= 1e-10
+    E0 = oed.heisenberg_levels(12, 0)[0]
+    assert abs(th - E0) < 1e-10
+    assert abs(dav.energy() - th) == 0.0
+
+
+def test_davidson_matches_oracle(ctx):
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    cfg = SMALL[5]
+    p = oracle_problem(cfg)
+    psi0 = synth.gaussian_psi(p["n"], synth.psi_seed(cfg))
+    th_o, x_o, res_o, it_o = odav.davidson(lambda v: oracle_apply(p, v), oracle_diag(p), psi0, tol=1e-9)
+    sec, env = workload.build(ctx, cfg)
+    dav = P.Davidson(ctx, env, torch.from_numpy(psi0).cuda(), tol=1e-9)
+    th, res, it, ok = dav.solve()
+    assert ok
+    assert abs(th - th_o) <= 1e-10 * max(1.0, abs(th_o))
+    x = torch.empty(p["n"], dtype=torch.float64, device="cuda")
+    dav.vector(x)
+    torch.cuda.synchronize()
+    # eigenvectors agree up to the residual level
+    assert np.linalg.norm(x.cpu().numpy() - x_o) <= 1e-6
+
+
+def test_error_statuses(ctx):
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    cfg = SMALL[2]
+    sec, env = workload.build(ctx, cfg)
+    x = torch.zeros(sec.psi_len, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.Su2Error) as ei:          # overlapping in/out
+        P.apply_heff(ctx, env, x, x)
+    assert ei.value.code == 1
+    with pytest.raises(P.Su2Error) as ei:          # misaligned pointer
+        P.apply_heff(ctx, env, x.data_ptr() + 4, torch.empty_like(x).data_ptr())
+    assert ei.value.code == 1
+    os.environ["SU2_FAIL_ALLOC"] = "1"
+    try:
+        with pytest.raises(P.Su2Error) as ei:      # injected allocation failure
+            workload.build(ctx, cfg)
+        assert ei.value.code == 2
+    finally:
+        del os.environ["SU2_FAIL_ALLOC"]
+    # the context stays usable afterwards
+    psi = synth.gaussian_psi(sec.psi_len, 1)
+    assert np.isfinite(gpu_apply(ctx, env, psi)).all()
