@@ -91,7 +91,7 @@ typedef struct {
 typedef struct {
   int64_t t_budget_bytes;  /* device bytes for the intermediate T = E D^T of
                               one term chunk (0: library default)           */
-  int32_t n_slices;        /* BF16 slices per operand (0: default 5)        */
+  int32_t n_slices;        /* BF16 slices per operand, 2..6 (0: default 6)  */
   int32_t prepare_split;   /* 1: also build the split-precision arenas      */
 } su2_env_opts;
 
@@ -115,10 +115,16 @@ typedef struct {
 
 /* Context on CUDA device `device` (-1: host-only context that can build
  * sectors and tables but not run kernels) and stream `cuda_stream`
- * (a cudaStream_t, NULL for the library's own stream). */
+ * (a cudaStream_t; NULL means the legacy default stream).  All device work
+ * of the context is ordered on that stream. */
 int su2_ctx_create(int device, void* cuda_stream, su2_ctx** out);
 int su2_ctx_destroy(su2_ctx* ctx);
 const char* su2_last_error(su2_ctx* ctx);
+/* Synchronises the context stream and returns (then clears) the device
+ * status word that kernels set instead of trapping: 0 = fine, 4 = a
+ * bounded device-side wait gave up (SU2_ETIMEOUT).  The call itself
+ * returns SU2_ECUDA if the stream reports an error. */
+int su2_ctx_status(su2_ctx* ctx, int32_t* device_status);
 
 /* Sector-table of psi (Sec. II.A, Eq. 3): all blocks (a, s1, s2, b, jL1,
  * j2R) with N_a + n1 + n2 + N_b = N_target and the couplings a x s1 -> jL1,

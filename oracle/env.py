@@ -280,3 +280,62 @@ def build_env(table, cfg, left, right):
         for oid, blk in synthetic_ops(table, sectors, side, cfg.seed).items():
             env[(side, oid)] = blk
     return env
+
+
+class _LazyOp:
+    def __init__(self, owner, side, oid):
+        self.owner, self.side, self.oid = owner, side, oid
+        self.cache = {}
+
+    def __getitem__(self, key):
+        if key not in self.cache:
+            self.cache[key] = self.owner.block(self.side, self.oid, key)
+        return self.cache[key]
+
+
+class LazySyntheticEnv:
+    """Synthetic-entry operators computed block by block on demand (same
+    values as ``synthetic_ops``), for sampled checks of large problems."""
+
+    def __init__(self, table, cfg, left, right):
+        self.table, self.cfg = table, cfg
+        self.sectors = {"L": left, "R": right}
+        self.ops = {"L": table.left_ops, "R": table.right_ops}
+        self._lazy = {}
+
+    def __getitem__(self, key):
+        if key not in self._lazy:
+            self._lazy[key] = _LazyOp(self, *key)
+        return self._lazy[key]
+
+    def get(self, key, default=None):
+        return self[key]
+
+    def block(self, side, oid, key):
+        qo, qi = key
+        op = self.ops[side][oid]
+        sec = self.sectors[side]
+        sid = SIDE_L if side == "L" else SIDE_R
+        if op.kind == RANDOM:
+            if not (sec[qo][0] == sec[qi][0] + op.dN and triangle(sec[qi][1], op.k, sec[qo][1])):
+                raise KeyError(key)
+            do, di = sec[qo][2], sec[qi][2]
+            s = 1.0 / math.sqrt(max(do, di))
+            return uniform_block(block_key(self.cfg.seed, sid, oid, qo, qi), do, di) * s
+        if op.kind == HAM:
+            if qo != qi:
+                raise KeyError(key)
+            d = sec[qo][2]
+            s = 1.0 / math.sqrt(d)
+            X = uniform_block(block_key(self.cfg.seed, sid, oid, qo, qo), d, d) * s
+            H = 0.1 * (X + X.T)
+            H[np.diag_indices(d)] += (2.0 * np.arange(d)) / d
+            return H
+        if op.kind == ADJOINT:
+            base = self[(side, op.base)][(qi, qo)]
+            k = self.ops[side][op.base].k
+            Sa, Sb = sec[qo][1], sec[qi][1]
+            e = Sb + k - Sa
+            sign = -1.0 if (e // 2) % 2 else 1.0
+            return sign * math.sqrt((Sb + 1) / (Sa + 1)) * base.T
+        raise KeyError(key)

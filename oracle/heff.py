@@ -61,7 +61,10 @@ def _out_sectors(op, sectors, a):
     return res
 
 
-def build_tasks(table: OperatorTable, left, right, blocks, twoS_target):
+def build_tasks(table: OperatorTable, left, right, blocks, twoS_target, only_f=None):
+    """Sector-task-table; ``only_f`` (a set of output block indices) keeps
+    only the tasks writing into those blocks (sampled checks of large
+    problems)."""
     sk = table.site_kind
     sites = synth.site_states(sk)
     bidx = block_index(blocks)
@@ -100,7 +103,7 @@ def build_tasks(table: OperatorTable, left, right, blocks, twoS_target):
                                     if not triangle(E.j2R, k, j2Rp) or not triangle(jL1p, j2Rp, S):
                                         continue
                                     f = bidx.get((ap, s1p, s2p, bp, jL1p, j2Rp))
-                                    if f is None:
+                                    if f is None or (only_f is not None and f not in only_f):
                                         continue
                                     cl = ctilde(Sa, t1, E.jL1, Aop.k, term.B.k, k, Sap, t1p, jL1p)
                                     cr = ctilde(t2, Sb, E.j2R, term.C.k, Dop.k, k, t2p, Sbp, j2Rp)
@@ -117,7 +120,9 @@ def build_tasks(table: OperatorTable, left, right, blocks, twoS_target):
 def apply_heff(table, env, tasks, blocks, psi_len, psi):
     """F = H_eff psi as the sum of Eq. 2 over the sector-task-table, FP64.
 
-    ``env`` maps (side, op id) -> {(out sector, in sector): matrix}.
+    ``env`` maps (side, op id) -> {(out sector, in sector): matrix}.  With a
+    task list restricted to some output blocks, only those blocks of F are
+    computed (the rest stays zero).
     """
     F = np.zeros(psi_len)
     for t in tasks:

@@ -20,7 +20,7 @@ SU2_SITE_SPIN_HALF, SU2_SITE_ORBITAL = 0, 1
 SU2_MODEL_HEISENBERG, SU2_MODEL_QC_SKELETON, SU2_MODEL_CASIMIR_S2, SU2_MODEL_CASIMIR_N = range(4)
 
 SYMBOLS = [
-    "su2_ctx_create", "su2_ctx_destroy", "su2_last_error", "su2_build_sectors", "su2_sectors_query",
+    "su2_ctx_create", "su2_ctx_destroy", "su2_last_error", "su2_ctx_status", "su2_build_sectors", "su2_sectors_query",
     "su2_sectors_destroy", "su2_build_environment", "su2_env_query", "su2_env_tasks", "su2_env_operator_block", "su2_env_destroy",
     "su2_apply_heff", "su2_apply_heff_host", "su2_diag_heff", "su2_davidson_create", "su2_davidson_step",
     "su2_davidson_solve", "su2_energy", "su2_davidson_vector", "su2_davidson_destroy",
@@ -78,6 +78,7 @@ def lib():
         L.su2_ctx_destroy.argtypes = [vp]
         L.su2_last_error.argtypes = [vp]
         L.su2_last_error.restype = C.c_char_p
+        L.su2_ctx_status.argtypes = [vp, C.POINTER(C.c_int32)]
         L.su2_build_sectors.argtypes = [vp, C.POINTER(Sector), C.c_int32, C.POINTER(Sector), C.c_int32,
                                         C.c_int32, C.c_int32, C.c_int32, C.POINTER(vp)]
         L.su2_sectors_query.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
@@ -145,6 +146,12 @@ class Context:
     def check(self, rc):
         if rc:
             raise Su2Error(rc, lib().su2_last_error(self.h).decode())
+
+    def status(self):
+        """Synchronise and return (then clear) the device status word."""
+        v = C.c_int32()
+        self.check(lib().su2_ctx_status(self.h, C.byref(v)))
+        return v.value
 
     def close(self):
         if self.h:

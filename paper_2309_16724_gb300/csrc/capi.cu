@@ -96,17 +96,8 @@ int su2_ctx_create(int device, void* cuda_stream, su2_ctx** out) {
       delete c;
       return SU2_ECUDA;
     }
-    if (cuda_stream) {
-      c->stream = (cudaStream_t)cuda_stream;
-    } else {
-      if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
-        delete c;
-        return SU2_ECUDA;
-      }
-      c->own_stream = true;
-    }
+    c->stream = (cudaStream_t)cuda_stream;  // NULL: the legacy default stream
     if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess || cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) {
-      if (c->own_stream) cudaStreamDestroy(c->stream);
       delete c;
       return SU2_ECUDA;
     }
@@ -127,6 +118,18 @@ int su2_ctx_destroy(su2_ctx* ctx) {
 }
 
 const char* su2_last_error(su2_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int su2_ctx_status(su2_ctx* ctx, int32_t* device_status) {
+  if (!ctx || !device_status) return fail(ctx, SU2_EINVAL, "null argument");
+  int rc = set_device(ctx);
+  if (rc) return rc;
+  int v = 0;
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpy(&v, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+  *device_status = v;
+  return SU2_OK;
+}
 
 int su2_build_sectors(su2_ctx* ctx, const su2_sector* left, int32_t n_left, const su2_sector* right, int32_t n_right,
                       int32_t site_kind, int32_t N_target, int32_t twoS_target, su2_sectors** out) {
@@ -368,6 +371,10 @@ int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond
   if (!env) return fail(ctx, SU2_ENOMEM, "host allocation");
   env->ctx = ctx;
   env->psi_len = S->psi_len;
+  env->blocks = S->blocks;
+  env->lsec = S->left;
+  env->rsec = S->right;
+  env->split_budget = (opts && opts->t_budget_bytes > 0) ? opts->t_budget_bytes : 0;
   try {
     env->table = make_table(*H, S->site_kind);
     std::string err = build_side_ops(env->table, true, lch, *H, env->L);
@@ -416,7 +423,7 @@ int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond
     if (!rc) rc = upload(ctx, &env->ddt, env->dt);
     if (!rc && opts && opts->prepare_split) {
       std::string err;
-      rc = split_prepare(env, opts->n_slices > 0 ? opts->n_slices : 5, err);
+      rc = split_prepare(env, opts->n_slices > 0 ? opts->n_slices : 6, err);
       if (rc) fail(ctx, rc, err);
     }
     if (rc) {

@@ -1,16 +1,773 @@
-// Split-precision path of H.psi (placeholder until the tcgen05 kernels land).
+// Split-precision path of H.psi (Eq. 2 over the sector-task-table, Eq. 3):
+// FP64 operands are cut into S BF16 slices with power-of-two row / column
+// scales, the sector GEMMs run on tcgen05 tensor cores (split_gemm.cuh) and
+// are recombined in float-float and finally in FP64.
+//
+// Scales:
+//  * left operator blocks A (K2): a common row exponent rho(a', r) per row of
+//    each left sector (max over every operator block with that output sector,
+//    identity included) so that all tasks of one output tile share it; each
+//    block is additionally shifted up by delta_b = min_r (rho - e_b(r)) >= 0
+//    and the shift is folded into its tasks' coefficient (v * 2^-delta).
+//  * T'_t = v_t 2^-delta T_u (K2 B operand): a common column exponent
+//    gamma(f, c) per output column, the max over the tasks into f.
+//  * K1 (T = E D^T): per-row exponents of the psi blocks and of the right
+//    operator blocks.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
 #include <string>
+#include <unordered_map>
+#include <vector>
 
+#include <cuda_bf16.h>
+
+#include "split_gemm.cuh"
 #include "su2_device.h"
 
 namespace su2 {
-int split_prepare(su2_env*, int, std::string& err) {
-  err = "split-precision path not available in this build";
-  return SU2_EINVAL;
+namespace {
+
+using sp::Item;
+using sp::Job;
+constexpr int kSentinel = -100000;
+constexpr int kSub = sp::kSub;
+
+struct SlabDesc {        // one FP64 source matrix -> slab (rows = slab rows, K = cols)
+  int64_t src_off;       // element offset in the FP64 source, -1 = identity
+  int64_t slab_off;      // byte offset in the slab arena
+  int32_t rows, cols, ld;
+  int32_t exp_off;       // row exponent array offset (own exponents or rho of the sector)
+  int32_t shift_idx;     // index into the delta array (-1: no shift)
+  int32_t own_off;       // offset of the block's own row exponents (A side), -1 otherwise
+  int32_t pad0, pad1;
+};
+struct Unit { int32_t desc, tr, ks, pad; };
+
+struct Source {          // float-float matrix whose columns feed T' (K2 B operand)
+  int64_t off;           // element offset in Th/Tl (sel 0) or psi_ff (sel 1)
+  int32_t rows, cols, sel, cexp_off;
+};
+struct TPTask {
+  int32_t src;           // Source index (chunk-local)
+  int32_t gcol;          // gamma offset of the output block
+  int32_t aid;           // A slab descriptor (its delta is folded into v)
+  int32_t pad;
+  double v;              // sector-value table entry
+  int64_t tp_off;        // byte offset of the T' slab in the chunk buffer
+};
+struct TPUnit { int32_t task, tr, ks, pad; };
+
+struct SChunk {
+  int64_t k1_j0, k1_j1, src0, src1, tp0, tp1, tpu0, tpu1, k2_j0, k2_j1;
+  double k1_flops, k2_flops;
+};
+
+struct SplitState {
+  int S = 5;
+  // slabs
+  unsigned char *dA = nullptr, *dD = nullptr, *dE = nullptr, *dTP = nullptr;
+  int64_t a_bytes = 0, d_bytes = 0, e_bytes = 0, tp_bytes = 0;
+  std::vector<SlabDesc> adesc, ddesc, edesc;
+  std::vector<Unit> aunit, dunit, eunit;
+  SlabDesc *d_adesc = nullptr, *d_ddesc = nullptr, *d_edesc = nullptr;
+  Unit *d_aunit = nullptr, *d_dunit = nullptr, *d_eunit = nullptr;
+  // exponents
+  int *d_rho = nullptr, *d_aown = nullptr, *d_delta = nullptr, *d_zeta = nullptr, *d_eps = nullptr;
+  int *d_gamma = nullptr, *d_cexp = nullptr;
+  int64_t n_rho = 0, n_aown = 0, n_zeta = 0, n_eps = 0, n_gamma = 0, n_cexp = 0;
+  // float-float buffers
+  float *dTh = nullptr, *dTl = nullptr, *dPh = nullptr, *dPl = nullptr;
+  int64_t t_elems = 0;
+  // plan
+  std::vector<SChunk> chunks;
+  std::vector<Job> k1j, k2j;
+  std::vector<Item> k1i, k2i;
+  std::vector<Source> src;
+  std::vector<TPTask> tpt;
+  std::vector<TPUnit> tpu;
+  Job *d_k1j = nullptr, *d_k2j = nullptr;
+  Item *d_k1i = nullptr, *d_k2i = nullptr;
+  Source* d_src = nullptr;
+  int64_t* d_colbase = nullptr;
+  TPTask* d_tpt = nullptr;
+  TPUnit* d_tpu = nullptr;
+  int* d_status = nullptr;
+  int n_sms = 148;
+};
+
+// ------------------------------------------------------------------ device helpers
+__device__ __forceinline__ int exp_of(double x) {  // |x| < 2^e, sentinel for 0
+  if (x == 0.0) return kSentinel;
+  const long long b = __double_as_longlong(x);
+  const int be = int((b >> 52) & 0x7FF);
+  return be == 0 ? -1022 : be - 1022;
 }
-int split_apply(su2_env*, const double*, double*, std::string& err) {
-  err = "split-precision path not prepared (build the environment with prepare_split=1)";
-  return SU2_EINVAL;
+__device__ __forceinline__ int exp_of_f(float x) {
+  if (x == 0.f) return kSentinel;
+  const unsigned b = __float_as_uint(x);
+  const int be = int((b >> 23) & 0xFF);
+  return be == 0 ? -126 : be - 126;
 }
-void split_free(su2_env*) {}
+
+// row exponents of FP64 source matrices: one CTA (128 threads) per (desc, row tile)
+__global__ void rowexp_kernel(const SlabDesc* __restrict__ descs, const Unit* __restrict__ units,
+                              const double* __restrict__ src, int* __restrict__ out, int use_own) {
+  const Unit u = units[blockIdx.x];
+  if (u.ks != 0) return;  // one unit per row tile does the work
+  const SlabDesc d = descs[u.desc];
+  const int r = u.tr * 128 + threadIdx.x;
+  if (r >= d.rows) return;
+  int e = kSentinel;
+  if (d.src_off < 0) {
+    e = 1;  // identity row: max |x| = 1 < 2^1
+  } else {
+    double m = 0.0;
+    for (int c = 0; c < d.cols; ++c) m = fmax(m, fabs(src[d.src_off + r + int64_t(c) * d.ld]));
+    e = exp_of(m);
+  }
+  out[(use_own ? d.own_off : d.exp_off) + r] = e;
+}
+
+// rho(a', r) = max over blocks of own exponents
+__global__ void rho_kernel(const SlabDesc* __restrict__ descs, const Unit* __restrict__ units,
+                           const int* __restrict__ own, int* __restrict__ rho) {
+  const Unit u = units[blockIdx.x];
+  if (u.ks != 0) return;
+  const SlabDesc d = descs[u.desc];
+  const int r = u.tr * 128 + threadIdx.x;
+  if (r >= d.rows) return;
+  atomicMax(&rho[d.exp_off + r], own[d.own_off + r]);
+}
+
+// delta_b = min over non-zero rows of (rho - own)
+__global__ void delta_kernel(const SlabDesc* __restrict__ descs, const Unit* __restrict__ units,
+                             const int* __restrict__ own, const int* __restrict__ rho, int* __restrict__ delta) {
+  const Unit u = units[blockIdx.x];
+  if (u.ks != 0) return;
+  const SlabDesc d = descs[u.desc];
+  const int r = u.tr * 128 + threadIdx.x;
+  if (r >= d.rows) return;
+  const int e = own[d.own_off + r];
+  if (e == kSentinel) return;
+  atomicMin(&delta[d.shift_idx], rho[d.exp_off + r] - e);
+}
+
+__global__ void delta_fix_kernel(int* __restrict__ delta, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && delta[i] == INT_MAX) delta[i] = 0;
+}
+
+// slab of FP64 matrices: one CTA of 128 threads per (desc, row tile, K stage);
+// thread = one slab row, 32 K elements = 4 core-matrix columns
+__global__ void slab_fp64_kernel(const SlabDesc* __restrict__ descs, const Unit* __restrict__ units,
+                                 const double* __restrict__ src, const int* __restrict__ rexp,
+                                 const int* __restrict__ delta, unsigned char* __restrict__ slab, int S) {
+  const Unit u = units[blockIdx.x];
+  const SlabDesc d = descs[u.desc];
+  const int t = threadIdx.x;
+  const int r = u.tr * 128 + t;
+  const int kst = (d.cols + 31) / 32;
+  unsigned char* base = slab + d.slab_off + (int64_t(u.tr) * kst + u.ks) * S * kSub;
+  int sigma = 0;
+  if (r < d.rows) {
+    sigma = rexp[d.exp_off + r];
+    if (d.shift_idx >= 0) sigma -= delta[d.shift_idx];
+    if (sigma < -1000) sigma = 0;
+  }
+  const int mi = t >> 3, rr = t & 7;
+#pragma unroll
+  for (int kg = 0; kg < 4; ++kg) {
+    double y[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = u.ks * 32 + kg * 8 + q;
+      double x = 0.0;
+      if (r < d.rows && k < d.cols) {
+        if (d.src_off < 0) x = (r == k) ? 1.0 : 0.0;
+        else x = src[d.src_off + r + int64_t(k) * d.ld];
+      }
+      y[q] = ldexp(x, 8 - sigma);  // |y| < 2^8
+    }
+    for (int i = 0; i < S; ++i) {
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const double qi = rint(y[q]);
+        y[q] = (y[q] - qi) * 256.0;
+        v[q] = __float2bfloat16_rn(ldexpf((float)qi, -8 * i));
+      }
+      *(uint4*)(base + i * kSub + (mi * 4 + kg) * 128 + rr * 16) = *(const uint4*)v;
+    }
+  }
+}
+
+__global__ void psi_ff_kernel(const double* __restrict__ x, float* __restrict__ h, float* __restrict__ l, int64_t n) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double v = x[i];
+    const float a = (float)v;
+    h[i] = a;
+    l[i] = (float)(v - (double)a);
+  }
+}
+
+// column exponents of the float-float sources: one warp per (source, column);
+// colbase[i] = first column of source i (chunk-local, = its cexp offset)
+__global__ void cexp_kernel(const Source* __restrict__ src, int nsrc, const int64_t* __restrict__ colbase,
+                            const float* __restrict__ Th, const float* __restrict__ Ph, int* __restrict__ cexp,
+                            int64_t total_cols) {
+  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= total_cols) return;
+  // locate the source by binary search over colbase
+  int lo = 0, hi = nsrc - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (colbase[mid] <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  const Source s = src[lo];
+  const int c = int(w - colbase[lo]);
+  const float* h = (s.sel ? Ph : Th) + s.off + int64_t(c) * s.rows;
+  float m = 0.f;
+  for (int r = lane; r < s.rows; r += 32) m = fmaxf(m, fabsf(h[r]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) cexp[s.cexp_off + c] = exp_of_f(m);
+}
+
+__global__ void fill_kernel(int* __restrict__ p, int64_t n, int v) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = v;
+}
+
+// gamma(f, c) = max over tasks of vexp + cexp(c): one CTA per task, threads over columns
+__global__ void gamma_kernel(const TPTask* __restrict__ tasks, const Source* __restrict__ src,
+                             const int* __restrict__ cexp, const int* __restrict__ delta, int* __restrict__ gamma) {
+  const TPTask t = tasks[blockIdx.x];
+  const Source s = src[t.src];
+  if (t.v == 0.0) return;
+  const int vexp = exp_of(t.v) - delta[t.aid];
+  for (int c = threadIdx.x; c < s.cols; c += blockDim.x) {
+    const int ce = cexp[s.cexp_off + c];
+    if (ce == kSentinel) continue;
+    atomicMax(&gamma[t.gcol + c], vexp + ce);
+  }
+}
+
+// T' slab: rows = columns of the source, K = rows of the source
+__global__ void slab_tprime_kernel(const TPTask* __restrict__ tasks, const TPUnit* __restrict__ units,
+                                   const Source* __restrict__ src, const float* __restrict__ Th,
+                                   const float* __restrict__ Tl, const float* __restrict__ Ph,
+                                   const float* __restrict__ Pl, const int* __restrict__ gamma,
+                                   const int* __restrict__ delta, unsigned char* __restrict__ slab, int S) {
+  const TPUnit u = units[blockIdx.x];
+  const TPTask t = tasks[u.task];
+  const double vs = ldexp(t.v, -delta[t.aid]);
+  const float vh = (float)vs, vl = (float)(vs - (double)vh);
+  const Source s = src[t.src];
+  const int tt = threadIdx.x;
+  const int c = u.tr * 128 + tt;  // slab row = source column
+  const int kst = (s.rows + 31) / 32;
+  unsigned char* base = slab + t.tp_off + (int64_t(u.tr) * kst + u.ks) * S * kSub;
+  const float* H = s.sel ? Ph : Th;
+  const float* Lo = s.sel ? Pl : Tl;
+  int sc = 0;
+  if (c < s.cols) {
+    sc = gamma[t.gcol + c];
+    if (sc < -1000) sc = 0;
+  }
+  const int mi = tt >> 3, rr = tt & 7;
+#pragma unroll
+  for (int kg = 0; kg < 4; ++kg) {
+    float ph[8], pl[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = u.ks * 32 + kg * 8 + q;
+      float a = 0.f, b = 0.f;
+      if (c < s.cols && k < s.rows) {
+        a = H[s.off + k + int64_t(c) * s.rows];
+        b = Lo[s.off + k + int64_t(c) * s.rows];
+      }
+      // (a + b) * (vh + vl) in float-float
+      const float p = a * vh;
+      float e = fmaf(a, vh, -p);
+      e = fmaf(a, vl, e);
+      e = fmaf(b, vh, e);
+      // scale to |x| < 2^8 (exact power of two)
+      ph[q] = ldexpf(p, 8 - sc);
+      pl[q] = ldexpf(e, 8 - sc);
+      const float hs = ph[q] + pl[q];
+      pl[q] = pl[q] - (hs - ph[q]);
+      ph[q] = hs;
+    }
+    for (int i = 0; i < S; ++i) {
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float qi = rintf(ph[q]);
+        const float rh = ph[q] - qi;           // exact
+        const float hs = rh + pl[q];
+        pl[q] = (pl[q] - (hs - rh)) * 256.f;
+        ph[q] = hs * 256.f;
+        v[q] = __float2bfloat16_rn(ldexpf(qi, -8 * i));
+      }
+      *(uint4*)(base + i * kSub + (mi * 4 + kg) * 128 + rr * 16) = *(const uint4*)v;
+    }
+  }
+}
+
+template <class T>
+int dalloc(T** p, size_t n, std::string& err) {
+  *p = nullptr;
+  const char* s = std::getenv("SU2_FAIL_ALLOC");
+  if (s && s[0] == '1') {
+    err = "device allocation refused (SU2_FAIL_ALLOC=1)";
+    return SU2_ENOMEM;
+  }
+  if (n == 0) n = 1;
+  if (cudaMalloc((void**)p, n * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    err = "cudaMalloc failed in the split-precision setup";
+    return SU2_ENOMEM;
+  }
+  return SU2_OK;
+}
+template <class T>
+int dput(T** p, const std::vector<T>& h, std::string& err) {
+  int rc = dalloc(p, h.size(), err);
+  if (rc) return rc;
+  if (!h.empty() && cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+    err = "cudaMemcpy failed in the split-precision setup";
+    return SU2_ECUDA;
+  }
+  return SU2_OK;
+}
+
+int64_t slab_bytes(int rows, int cols, int S) {
+  return int64_t((rows + 127) / 128) * ((cols + 31) / 32) * S * kSub;
+}
+
+void add_units(std::vector<Unit>& u, int desc, int rows, int cols) {
+  for (int tr = 0; tr < (rows + 127) / 128; ++tr)
+    for (int ks = 0; ks < (cols + 31) / 32; ++ks) u.push_back(Unit{desc, tr, ks, 0});
+}
+
+int exp_host(double x) {
+  if (x == 0.0) return kSentinel;
+  int e;
+  std::frexp(x, &e);
+  return e;
+}
+
+void launch_gemm(int mode, cudaStream_t s, SplitState* st, const Job* jobs, int njobs, const Item* items,
+                 const unsigned char* A, const unsigned char* B, const int* rexp, const int* cexp, float* Th,
+                 float* Tl, double* F) {
+  if (njobs <= 0) return;
+  const int smem = 2 * (2 * st->S * kSub) + 1024;
+  const int grid = std::min(njobs, st->n_sms);
+  if (mode == sp::MODE_T)
+    sp::split_gemm_kernel<sp::MODE_T><<<grid, sp::kThreads, smem, s>>>(jobs, njobs, items, A, B, rexp, cexp, 16,
+                                                                       st->S, Th, Tl, F, st->d_status);
+  else
+    sp::split_gemm_kernel<sp::MODE_F><<<grid, sp::kThreads, smem, s>>>(jobs, njobs, items, A, B, rexp, cexp, 16,
+                                                                       st->S, Th, Tl, F, st->d_status);
+}
+
+}  // namespace
+
+
+int split_prepare(su2_env* env, int S, std::string& err) {
+  if (S < 2 || S > sp::kMaxS) {
+    err = "n_slices must be in [2, 6]";
+    return SU2_EINVAL;
+  }
+  auto* st = new SplitState();
+  env->split = st;
+  st->S = S;
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, env->ctx->device);
+  st->n_sms = prop.multiProcessorCount;
+  const int smem = 2 * (2 * S * kSub) + 1024;
+  if (cudaFuncSetAttribute(sp::split_gemm_kernel<sp::MODE_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(sp::split_gemm_kernel<sp::MODE_F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess) {
+    err = "cannot set the shared-memory size of the split GEMM";
+    return SU2_ECUDA;
+  }
+  st->d_status = env->ctx->d_status;
+  const auto& B = env->blocks;
+  const auto& ls = env->lsec;
+  const auto& L = env->L;
+  const auto& R = env->R;
+  const int nLb = int(L.blocks.size());
+  // ---------------------------------------------------------- A side
+  std::vector<int64_t> rho_off(ls.size());
+  int64_t acc = 0;
+  for (size_t a = 0; a < ls.size(); ++a) {
+    rho_off[a] = acc;
+    acc += ls[a].dim;
+  }
+  st->n_rho = acc;
+  int64_t own = 0, ab = 0;
+  for (int bi = 0; bi < nLb; ++bi) {
+    const OpBlock& ob = L.blocks[bi];
+    st->adesc.push_back(SlabDesc{ob.off, ab, ob.rows, ob.cols, ob.rows, int32_t(rho_off[ob.qo]), bi, int32_t(own), 0, 0});
+    own += ob.rows;
+    ab += slab_bytes(ob.rows, ob.cols, S);
+  }
+  for (size_t a = 0; a < ls.size(); ++a) {
+    const int d = ls[a].dim;
+    st->adesc.push_back(
+        SlabDesc{-1, ab, d, d, d, int32_t(rho_off[a]), int32_t(nLb + a), int32_t(own), 0, 0});
+    own += d;
+    ab += slab_bytes(d, d, S);
+  }
+  st->n_aown = own;
+  st->a_bytes = ab;
+  for (size_t i = 0; i < st->adesc.size(); ++i) add_units(st->aunit, int(i), st->adesc[i].rows, st->adesc[i].cols);
+  // ---------------------------------------------------------- D side
+  int64_t zoff = 0, db = 0;
+  std::vector<int64_t> zeta_off(R.blocks.size());
+  for (size_t bi = 0; bi < R.blocks.size(); ++bi) {
+    const OpBlock& ob = R.blocks[bi];
+    zeta_off[bi] = zoff;
+    st->ddesc.push_back(SlabDesc{ob.off, db, ob.rows, ob.cols, ob.rows, int32_t(zoff), -1, -1, 0, 0});
+    zoff += ob.rows;
+    db += slab_bytes(ob.rows, ob.cols, S);
+  }
+  st->n_zeta = zoff;
+  st->d_bytes = db;
+  for (size_t i = 0; i < st->ddesc.size(); ++i) add_units(st->dunit, int(i), st->ddesc[i].rows, st->ddesc[i].cols);
+  // ---------------------------------------------------------- E side (psi blocks)
+  int64_t eoff = 0, eb = 0;
+  std::vector<int64_t> eps_off(B.size()), e_slab(B.size());
+  for (size_t e = 0; e < B.size(); ++e) {
+    eps_off[e] = eoff;
+    e_slab[e] = eb;
+    st->edesc.push_back(SlabDesc{B[e].offset, eb, B[e].rows, B[e].cols, B[e].rows, int32_t(eoff), -1, -1, 0, 0});
+    eoff += B[e].rows;
+    eb += slab_bytes(B[e].rows, B[e].cols, S);
+  }
+  st->n_eps = eoff;
+  st->e_bytes = eb;
+  for (size_t i = 0; i < st->edesc.size(); ++i) add_units(st->eunit, int(i), st->edesc[i].rows, st->edesc[i].cols);
+  // gamma offsets per psi block (output columns)
+  std::vector<int64_t> goff(B.size());
+  int64_t gacc = 0;
+  for (size_t f = 0; f < B.size(); ++f) {
+    goff[f] = gacc;
+    gacc += B[f].cols;
+  }
+  st->n_gamma = gacc;
+  if (st->n_rho >= INT32_MAX || st->n_zeta >= INT32_MAX || st->n_eps >= INT32_MAX || st->n_gamma >= INT32_MAX) {
+    err = "exponent tables too large";
+    return SU2_EINVAL;
+  }
+  // ---------------------------------------------------------- chunk plan
+  const int nterms = int(env->table.terms.size());
+  std::vector<std::vector<int64_t>> by_term(nterms);
+  for (int64_t i = 0; i < int64_t(env->tasks.size()); ++i) by_term[env->tasks[i].term].push_back(i);
+  const int64_t budget = env->split_budget > 0 ? env->split_budget : (int64_t(4) << 30);
+  std::vector<int> starts{0};
+  {
+    int64_t bytes = 0;
+    std::unordered_map<uint64_t, char> seen;
+    for (int ti = 0; ti < nterms; ++ti) {
+      int64_t add = 0;
+      std::unordered_map<uint64_t, char> mine;
+      for (int64_t i : by_term[ti]) {
+        const Task& t = env->tasks[i];
+        const Block& E = B[t.e];
+        const int n = B[t.f].cols;
+        add += slab_bytes(n, E.rows, S);
+        if (t.dblk >= 0) {
+          const uint64_t key = (uint64_t(uint32_t(t.dblk)) << 32) | uint32_t(t.e);
+          if (!seen.count(key) && !mine.count(key)) {
+            mine[key] = 1;
+            add += 8 * int64_t(E.rows) * n;
+          }
+        }
+      }
+      if (bytes > 0 && bytes + add > budget) {
+        starts.push_back(ti);
+        seen.clear();
+        bytes = 0;
+      }
+      for (auto& kv : mine) seen.insert(kv);
+      bytes += add;
+    }
+    starts.push_back(nterms);
+  }
+  int64_t max_t = 0, max_tp = 0, max_cexp = 0;
+  const int64_t nt = int64_t(env->tasks.size());
+  for (size_t c = 0; c + 1 < starts.size(); ++c) {
+    const int t0 = starts[c], t1 = starts[c + 1];
+    SChunk ch{};
+    ch.k1_j0 = int64_t(st->k1j.size());
+    ch.src0 = int64_t(st->src.size());
+    ch.tp0 = int64_t(st->tpt.size());
+    ch.tpu0 = int64_t(st->tpu.size());
+    ch.k2_j0 = int64_t(st->k2j.size());
+    std::unordered_map<uint64_t, int> umap;  // (dblk, e) -> source index (chunk-local)
+    std::unordered_map<int, int> pmap;       // e -> psi source index
+    int64_t tsz = 0, csz = 0, tpsz = 0;
+    std::vector<Job> k1jobs;
+    std::vector<int> k1cost;
+    auto src_for = [&](const Task& t) -> int {
+      const Block& E = B[t.e];
+      if (t.dblk < 0) {
+        auto it = pmap.find(t.e);
+        if (it != pmap.end()) return it->second;
+        const int id = int(st->src.size() - ch.src0);
+        st->src.push_back(Source{E.offset, E.rows, E.cols, 1, int32_t(csz)});
+        csz += E.cols;
+        pmap[t.e] = id;
+        return id;
+      }
+      const uint64_t key = (uint64_t(uint32_t(t.dblk)) << 32) | uint32_t(t.e);
+      auto it = umap.find(key);
+      if (it != umap.end()) return it->second;
+      const OpBlock& Db = R.blocks[t.dblk];
+      const int k1 = E.rows, k2 = E.cols, n = Db.rows;
+      const int id = int(st->src.size() - ch.src0);
+      st->src.push_back(Source{tsz, k1, n, 0, int32_t(csz)});
+      csz += n;
+      umap[key] = id;
+      const int kst2 = (k2 + 31) / 32;
+      for (int tc = 0; tc < (n + 127) / 128; ++tc)
+        for (int tr = 0; tr < (k1 + 127) / 128; ++tr) {
+          const int ii = int(st->k1i.size());
+          st->k1i.push_back(Item{st->edesc[t.e].slab_off + int64_t(tr) * kst2 * S * kSub,
+                                 st->ddesc[t.dblk].slab_off + int64_t(tc) * kst2 * S * kSub, kst2, 0});
+          k1jobs.push_back(Job{tsz, k1, n, k1, tr, tc, ii, ii + 1, int32_t(eps_off[t.e]),
+                               int32_t(zeta_off[t.dblk]), kst2});
+          k1cost.push_back(kst2);
+        }
+      ch.k1_flops += 2.0 * k1 * k2 * n;
+      tsz += (int64_t(k1) * n + 3) & ~int64_t(3);
+      return id;
+    };
+    // K2 jobs grouped by output block
+    std::vector<Job> k2jobs;
+    std::vector<int64_t> k2cost;
+    int64_t i = 0;
+    while (i < nt) {
+      const int f = env->tasks[i].f;
+      int64_t j = i;
+      std::vector<int64_t> mine;
+      for (; j < nt && env->tasks[j].f == f; ++j) {
+        const Task& t = env->tasks[j];
+        if (t.term >= t0 && t.term < t1) mine.push_back(j);
+      }
+      i = j;
+      if (mine.empty()) continue;
+      const Block& Fb = B[f];
+      std::vector<int> aid(mine.size());
+      std::vector<int64_t> tp(mine.size());
+      std::vector<int> kst(mine.size());
+      for (size_t q = 0; q < mine.size(); ++q) {
+        const Task& t = env->tasks[mine[q]];
+        const Block& E = B[t.e];
+        const int s = src_for(t);
+        aid[q] = t.ablk >= 0 ? t.ablk : nLb + B[t.e].a;
+        tp[q] = tpsz;
+        kst[q] = (E.rows + 31) / 32;
+        const int task_id = int(st->tpt.size() - ch.tp0);
+        st->tpt.push_back(TPTask{s, int32_t(goff[f]), aid[q], 0, t.v, tpsz});
+        for (int tr = 0; tr < (Fb.cols + 127) / 128; ++tr)
+          for (int ks = 0; ks < kst[q]; ++ks) st->tpu.push_back(TPUnit{task_id, tr, ks, 0});
+        tpsz += slab_bytes(Fb.cols, E.rows, S);
+        if (t.ablk >= 0) ch.k2_flops += 2.0 * Fb.rows * E.rows * Fb.cols;
+      }
+      for (int tc = 0; tc < (Fb.cols + 127) / 128; ++tc)
+        for (int tr = 0; tr < (Fb.rows + 127) / 128; ++tr) {
+          const int i0 = int(st->k2i.size());
+          int tot = 0;
+          for (size_t q = 0; q < mine.size(); ++q) {
+            st->k2i.push_back(Item{st->adesc[aid[q]].slab_off + int64_t(tr) * kst[q] * S * kSub,
+                                   tp[q] + int64_t(tc) * kst[q] * S * kSub, kst[q], 0});
+            tot += kst[q];
+          }
+          k2jobs.push_back(Job{Fb.offset, Fb.rows, Fb.cols, Fb.rows, tr, tc, i0, int(st->k2i.size()),
+                               int32_t(rho_off[Fb.a]), int32_t(goff[f]), tot});
+          k2cost.push_back(tot);
+        }
+    }
+    // LPT order
+    std::vector<int> o1(k1jobs.size());
+    for (size_t q = 0; q < o1.size(); ++q) o1[q] = int(q);
+    std::stable_sort(o1.begin(), o1.end(), [&](int a, int b) { return k1cost[a] > k1cost[b]; });
+    for (int q : o1) st->k1j.push_back(k1jobs[q]);
+    std::vector<int> o2(k2jobs.size());
+    for (size_t q = 0; q < o2.size(); ++q) o2[q] = int(q);
+    std::stable_sort(o2.begin(), o2.end(), [&](int a, int b) { return k2cost[a] > k2cost[b]; });
+    for (int q : o2) st->k2j.push_back(k2jobs[q]);
+    ch.k1_j1 = int64_t(st->k1j.size());
+    ch.src1 = int64_t(st->src.size());
+    ch.tp1 = int64_t(st->tpt.size());
+    ch.tpu1 = int64_t(st->tpu.size());
+    ch.k2_j1 = int64_t(st->k2j.size());
+    st->chunks.push_back(ch);
+    max_t = std::max(max_t, tsz);
+    max_tp = std::max(max_tp, tpsz);
+    max_cexp = std::max(max_cexp, csz);
+  }
+  if (int64_t(st->k2i.size()) >= INT32_MAX || int64_t(st->k1i.size()) >= INT32_MAX) {
+    err = "split plan too large";
+    return SU2_EINVAL;
+  }
+  st->t_elems = max_t;
+  st->tp_bytes = max_tp;
+  st->n_cexp = max_cexp;
+  // ---------------------------------------------------------- device memory
+  int rc2 = 0;
+  if (!rc2) rc2 = dalloc(&st->dA, size_t(st->a_bytes), err);
+  if (!rc2) rc2 = dalloc(&st->dD, size_t(st->d_bytes), err);
+  if (!rc2) rc2 = dalloc(&st->dE, size_t(st->e_bytes), err);
+  if (!rc2) rc2 = dalloc(&st->dTP, size_t(std::max<int64_t>(st->tp_bytes, 16)), err);
+  if (!rc2) rc2 = dalloc(&st->dTh, size_t(std::max<int64_t>(st->t_elems, 4)), err);
+  if (!rc2) rc2 = dalloc(&st->dTl, size_t(std::max<int64_t>(st->t_elems, 4)), err);
+  if (!rc2) rc2 = dalloc(&st->dPh, size_t(env->psi_len), err);
+  if (!rc2) rc2 = dalloc(&st->dPl, size_t(env->psi_len), err);
+  if (!rc2) rc2 = dalloc(&st->d_rho, size_t(st->n_rho), err);
+  if (!rc2) rc2 = dalloc(&st->d_aown, size_t(st->n_aown), err);
+  if (!rc2) rc2 = dalloc(&st->d_delta, st->adesc.size(), err);
+  if (!rc2) rc2 = dalloc(&st->d_zeta, size_t(st->n_zeta), err);
+  if (!rc2) rc2 = dalloc(&st->d_eps, size_t(st->n_eps), err);
+  if (!rc2) rc2 = dalloc(&st->d_gamma, size_t(st->n_gamma), err);
+  if (!rc2) rc2 = dalloc(&st->d_cexp, size_t(std::max<int64_t>(st->n_cexp, 1)), err);
+  if (!rc2) rc2 = dput(&st->d_adesc, st->adesc, err);
+  if (!rc2) rc2 = dput(&st->d_ddesc, st->ddesc, err);
+  if (!rc2) rc2 = dput(&st->d_edesc, st->edesc, err);
+  if (!rc2) rc2 = dput(&st->d_aunit, st->aunit, err);
+  if (!rc2) rc2 = dput(&st->d_dunit, st->dunit, err);
+  if (!rc2) rc2 = dput(&st->d_eunit, st->eunit, err);
+  if (!rc2) rc2 = dput(&st->d_k1j, st->k1j, err);
+  if (!rc2) rc2 = dput(&st->d_k2j, st->k2j, err);
+  if (!rc2) rc2 = dput(&st->d_k1i, st->k1i, err);
+  if (!rc2) rc2 = dput(&st->d_k2i, st->k2i, err);
+  if (!rc2) rc2 = dput(&st->d_src, st->src, err);
+  if (!rc2) rc2 = dput(&st->d_tpt, st->tpt, err);
+  if (!rc2) rc2 = dput(&st->d_tpu, st->tpu, err);
+  if (rc2) return rc2;
+  std::vector<int64_t> colbase(st->src.size());
+  for (size_t q = 0; q < st->src.size(); ++q) colbase[q] = st->src[q].cexp_off;
+  int64_t* d_colbase = nullptr;
+  if ((rc2 = dput(&d_colbase, colbase, err))) return rc2;
+  st->d_colbase = d_colbase;
+  // ---------------------------------------------------------- operator slabs (once per site)
+  cudaStream_t s = env->ctx->stream;
+  const int na = int(st->aunit.size()), nd = int(st->dunit.size());
+  fill_kernel<<<256, 256, 0, s>>>(st->d_rho, st->n_rho, kSentinel);
+  fill_kernel<<<64, 256, 0, s>>>(st->d_delta, int64_t(st->adesc.size()), INT_MAX);
+  if (na) {
+    rowexp_kernel<<<na, 128, 0, s>>>(st->d_adesc, st->d_aunit, env->dL, st->d_aown, 1);
+    rho_kernel<<<na, 128, 0, s>>>(st->d_adesc, st->d_aunit, st->d_aown, st->d_rho);
+    delta_kernel<<<na, 128, 0, s>>>(st->d_adesc, st->d_aunit, st->d_aown, st->d_rho, st->d_delta);
+    delta_fix_kernel<<<int((st->adesc.size() + 255) / 256), 256, 0, s>>>(st->d_delta, int(st->adesc.size()));
+    slab_fp64_kernel<<<na, 128, 0, s>>>(st->d_adesc, st->d_aunit, env->dL, st->d_rho, st->d_delta, st->dA, S);
+  }
+  if (nd) {
+    rowexp_kernel<<<nd, 128, 0, s>>>(st->d_ddesc, st->d_dunit, env->dR, st->d_zeta, 0);
+    slab_fp64_kernel<<<nd, 128, 0, s>>>(st->d_ddesc, st->d_dunit, env->dR, st->d_zeta, st->d_delta, st->dD, S);
+  }
+  {
+    const cudaError_t e1 = cudaGetLastError();
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      err = std::string("split-precision operator slabs failed: ") + cudaGetErrorString(e1 != cudaSuccess ? e1 : e2);
+      return SU2_ECUDA;
+    }
+  }
+  return SU2_OK;
+}
+
+#define SPLIT_CHECK(label)                                                        \
+  do {                                                                            \
+    const cudaError_t e_ = cudaGetLastError();                                    \
+    if (e_ != cudaSuccess) {                                                      \
+      err = std::string("split-precision launch failed (") + label + "): " + cudaGetErrorString(e_); \
+      return SU2_ECUDA;                                                           \
+    }                                                                             \
+  } while (0)
+
+int split_apply(su2_env* env, const double* psi, double* F, std::string& err) {
+  auto* st = static_cast<SplitState*>(env->split);
+  if (!st) {
+    err = "split-precision path not prepared (build the environment with prepare_split=1)";
+    return SU2_EINVAL;
+  }
+  cudaStream_t s = env->ctx->stream;
+  Profiler& pf = env->prof;
+  const int S = st->S;
+  const int ne = int(st->eunit.size());
+  SPLIT_CHECK("before");
+  int slot = pf.begin(s, 2, 0.0);
+  psi_ff_kernel<<<1024, 256, 0, s>>>(psi, st->dPh, st->dPl, env->psi_len);
+  if (ne) {
+    rowexp_kernel<<<ne, 128, 0, s>>>(st->d_edesc, st->d_eunit, psi, st->d_eps, 0);
+    slab_fp64_kernel<<<ne, 128, 0, s>>>(st->d_edesc, st->d_eunit, psi, st->d_eps, st->d_delta, st->dE, S);
+  }
+  cudaMemsetAsync(F, 0, size_t(env->psi_len) * sizeof(double), s);
+  pf.end(s, slot);
+  SPLIT_CHECK("psi slabs");
+  const double npairs = S * (S + 1) / 2.0;
+  for (const SChunk& c : st->chunks) {
+    slot = pf.begin(s, 3, c.k1_flops * npairs);
+    launch_gemm(sp::MODE_T, s, st, st->d_k1j + c.k1_j0, int(c.k1_j1 - c.k1_j0), st->d_k1i, st->dE, st->dD, st->d_eps,
+                st->d_zeta, st->dTh, st->dTl, nullptr);
+    pf.end(s, slot);
+    SPLIT_CHECK("K1 split GEMM");
+    slot = pf.begin(s, 2, 0.0);
+    const int nsrc = int(c.src1 - c.src0);
+    int64_t cols = 0;
+    if (nsrc) cols = st->src[c.src1 - 1].cexp_off + st->src[c.src1 - 1].cols;
+    if (cols > 0) {
+      const int64_t threads = cols * 32;
+      cexp_kernel<<<unsigned((threads + 255) / 256), 256, 0, s>>>(st->d_src + c.src0, nsrc, st->d_colbase + c.src0,
+                                                                  st->dTh, st->dPh, st->d_cexp, cols);
+    }
+    SPLIT_CHECK("column exponents");
+    fill_kernel<<<256, 256, 0, s>>>(st->d_gamma, st->n_gamma, kSentinel);
+    const int ntp = int(c.tp1 - c.tp0);
+    if (ntp) gamma_kernel<<<ntp, 128, 0, s>>>(st->d_tpt + c.tp0, st->d_src + c.src0, st->d_cexp, st->d_delta, st->d_gamma);
+    const int64_t nu = c.tpu1 - c.tpu0;
+    if (nu) {
+      // units of this chunk refer to chunk-local task indices
+      slab_tprime_kernel<<<unsigned(nu), 128, 0, s>>>(st->d_tpt + c.tp0, st->d_tpu + c.tpu0, st->d_src + c.src0,
+                                                      st->dTh, st->dTl, st->dPh, st->dPl, st->d_gamma, st->d_delta,
+                                                      st->dTP, S);
+    }
+    pf.end(s, slot);
+    SPLIT_CHECK("T' slabs");
+    slot = pf.begin(s, 4, c.k2_flops * npairs);
+    launch_gemm(sp::MODE_F, s, st, st->d_k2j + c.k2_j0, int(c.k2_j1 - c.k2_j0), st->d_k2i, st->dA, st->dTP,
+                st->d_rho, st->d_gamma, nullptr, nullptr, F);
+    pf.end(s, slot);
+    SPLIT_CHECK("K2 split GEMM");
+  }
+  if (cudaGetLastError() != cudaSuccess) {
+    err = "split-precision launch failed";
+    return SU2_ECUDA;
+  }
+  return SU2_OK;
+}
+
+void split_free(su2_env* env) {
+  auto* st = static_cast<SplitState*>(env->split);
+  if (!st) return;
+  void* ps[] = {st->dA, st->dD, st->dE, st->dTP, st->d_adesc, st->d_ddesc, st->d_edesc, st->d_aunit, st->d_dunit,
+                st->d_eunit, st->d_rho, st->d_aown, st->d_delta, st->d_zeta, st->d_eps, st->d_gamma, st->d_cexp,
+                st->dTh, st->dTl, st->dPh, st->dPl, st->d_k1j, st->d_k2j, st->d_k1i, st->d_k2i, st->d_src,
+                st->d_tpt, st->d_tpu, st->d_colbase};
+  for (void* p : ps) cudaFree(p);
+  delete st;
+  env->split = nullptr;
+}
+
 }  // namespace su2

@@ -1,0 +1,368 @@
+// Persistent split-precision stripe GEMM on tcgen05 (sm_103a).
+//
+// Operands are pre-tiled "slabs": an R x K FP64 matrix (R = M or N side,
+// K-major) cut into S BF16 slices, stored as 128-row x 32-K sub-tiles of
+// 8 KB in the UMMA no-swizzle K-major core-matrix layout (core matrix
+// (mi, ki) at (mi*4 + ki)*128 bytes, row r%8 at 16*(r%8)); for each
+// (row tile, K stage) the S slices follow each other (S*8 KB, one bulk
+// copy).  Slice i holds q_i * 2^-8i where q_i are the integers peeled from
+// x * 2^(8 - sigma_row), |q_i| <= 257.
+//
+// One job = one 128 x 128 output tile and a list of items (A slab, B slab,
+// K stages); all items of a job share the row and column scales, so the
+// K-concatenated stripe sum_items A_item . B_item^T accumulates in TMEM
+// without a separate reduction (the stripe product of Sec. III.A).  Slice
+// pairs (i, j), i + j < S, go to three FP32 TMEM accumulators by level
+// l = min(i + j, 2).  Levels 0 and 1 hold integer multiples of their unit
+// below 2^24 for K chunks of 128, hence are exact; level 2 carries the
+// 2^-16-weighted tail.  Every 128-K chunk the eight drain warps fold the
+// three levels into a float-float register accumulator; at the end of the
+// job they write the tile (K1: float-float T; K2: F += FP64).
+//
+// Warp roles (576 threads): warp 0 bulk-copy producer, warp 1 MMA issuer,
+// warps 2..17 drain/epilogue (TMEM lane quarter w%4, 32-column group (w-2)/4).
+// Every mbarrier wait is bounded; on timeout the CTA records a status,
+// stops issuing, waits (bounded) for its own copies and MMAs, frees TMEM and
+// returns.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace su2 {
+namespace sp {
+
+constexpr int kRows = 128;           // M tile = N tile
+constexpr int kKS = 32;              // K per pipeline stage
+constexpr int kSub = kRows * kKS * 2;  // bytes of one 128 x 32 BF16 sub-tile
+constexpr int kMaxS = 6;
+constexpr int kStages = 2;
+constexpr int kChunkStages = 4;      // 128 K per exact drain
+constexpr int kThreads = 576;      // producer + MMA + 16 drain warps
+constexpr long kSpinLimit = 1L << 26;
+
+struct Item {
+  int64_t a_off, b_off;  // byte offsets of the first (row tile, K stage) group
+  int32_t nst, pad;      // K stages of 32
+};
+struct Job {
+  int64_t out_off;       // element offset of the output block
+  int32_t rows, cols;    // valid extent of the output block
+  int32_t ld, tr, tc;    // leading dimension (rows of the block), tile indices
+  int32_t i0, i1;        // items
+  int32_t rsc, csc;      // offsets of the row / column exponent arrays
+  int32_t nst;           // total K stages of all items
+};
+
+enum { MODE_T = 0, MODE_F = 1 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; false on timeout or when another role aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  for (long it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255) == 255 && *abort_flag) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+  // no swizzle, K-major: LBO = 128 B (next core matrix along K), SBO = 512 B
+  // (next 8-row group), descriptor version 1 (bit 46)
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// x * 2^k for float, exact while the result stays normal
+__device__ __forceinline__ float ldexp_f(float x, int k) { return ldexpf(x, k); }
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+    split_gemm_kernel(const Job* __restrict__ jobs, int njobs, const Item* __restrict__ items,
+                      const unsigned char* __restrict__ Aslab, const unsigned char* __restrict__ Bslab,
+                      const int* __restrict__ rexp, const int* __restrict__ cexp, int shift, int S,
+                      float* __restrict__ Th, float* __restrict__ Tl, double* __restrict__ F, int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int stage_bytes = 2 * S * kSub;
+  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], accf_bar, acce_bar, done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  __shared__ int issued[kStages];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty_bar[s])));
+      issued[s] = 0;
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf_bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 512;" ::"r"(smem_u32(&acce_bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done_bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_flag = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+  const int nlev = S < 3 ? S : 3;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int st = 0;
+      uint32_t use[kStages] = {0, 0};
+      bool ok = true;
+      for (int j = blockIdx.x; j < njobs && ok; j += gridDim.x) {
+        const Job jb = jobs[j];
+        for (int it = jb.i0; it < jb.i1 && ok; ++it) {
+          const Item item = items[it];
+          for (int ks = 0; ks < item.nst; ++ks) {
+            if (!mbar_wait(smem_u32(&empty_bar[st]), (use[st] & 1) ^ 1, &abort_flag)) {
+              ok = false;
+              break;
+            }
+            const uint32_t fb = smem_u32(&full_bar[st]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(stage_bytes)
+                         : "memory");
+            const uint32_t dst = smem_u32(smem + st * stage_bytes);
+            const unsigned char* srcA = Aslab + item.a_off + (int64_t)ks * S * kSub;
+            const unsigned char* srcB = Bslab + item.b_off + (int64_t)ks * S * kSub;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                "l"(srcA), "r"(S * kSub), "r"(fb)
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    dst + S * kSub),
+                "l"(srcB), "r"(S * kSub), "r"(fb)
+                : "memory");
+            issued[st] = (int)use[st] + 1;
+            use[st] += 1;
+            st = (st + 1) % kStages;
+          }
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        atomicExch(status, 4);
+      }
+      // wait (bounded) for every copy this CTA issued
+      for (int s = 0; s < kStages; ++s)
+        if (issued[s] > 0) {
+          bool fin = false;
+          for (long it = 0; it < kSpinLimit && !fin; ++it) fin = mbar_try(smem_u32(&full_bar[s]), (issued[s] - 1) & 1);
+          if (!fin) atomicExch(status, 4);
+        }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int st = 0;
+      uint32_t use[kStages] = {0, 0};
+      uint32_t chunk = 0;
+      bool ok = true;
+      for (int j = blockIdx.x; j < njobs && ok; j += gridDim.x) {
+        const Job jb = jobs[j];
+        const int total = jb.nst;
+        int g = 0;
+        for (int it = jb.i0; it < jb.i1 && ok; ++it) {
+          const int nst = items[it].nst;
+          for (int ks = 0; ks < nst; ++ks, ++g) {
+            const int cpos = g % kChunkStages;
+            if (cpos == 0) {
+              if (!mbar_wait(smem_u32(&acce_bar), (chunk & 1) ^ 1, &abort_flag)) {
+                ok = false;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;");
+            }
+            if (!mbar_wait(smem_u32(&full_bar[st]), use[st] & 1, &abort_flag)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t sa = smem_u32(smem + st * stage_bytes);
+            const uint32_t sb = sa + S * kSub;
+            for (int i = 0; i < S; ++i)
+              for (int jj = 0; jj + i < S; ++jj) {
+                const int lvl = (i + jj) < 2 ? (i + jj) : 2;
+                // first MMA into each level in a chunk resets it
+                const bool first_pair = (lvl == 0) || (lvl == 1 && i == 0 && jj == 1) || (lvl == 2 && i == 0 && jj == 2);
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                  const uint32_t acc = (cpos == 0 && first_pair && kk == 0) ? 0u : 1u;
+                  mma_bf16(tmem + lvl * 128, make_desc(sa + i * kSub + kk * 256), make_desc(sb + jj * kSub + kk * 256),
+                           acc);
+                }
+              }
+            mma_commit(smem_u32(&empty_bar[st]));
+            use[st] += 1;
+            st = (st + 1) % kStages;
+            if (cpos == kChunkStages - 1 || g == total - 1) {
+              mma_commit(smem_u32(&accf_bar));
+              chunk += 1;
+            }
+          }
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        atomicExch(status, 4);
+      }
+      // all MMAs issued by this thread complete before TMEM is released
+      mma_commit(smem_u32(&done_bar));
+      bool fin = false;
+      for (long it = 0; it < kSpinLimit && !fin; ++it) fin = mbar_try(smem_u32(&done_bar), 0);
+      if (!fin) atomicExch(status, 4);
+    }
+  } else {
+    // ------------------------------------------------------------ drain / epilogue
+    const int q = warp & 3;             // TMEM lane quarter
+    const int cgrp = (warp - 2) >> 2;   // 32-column group
+    const int row = q * 32 + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+    uint32_t chunk = 0;
+    bool ok = true;
+    for (int j = blockIdx.x; j < njobs && ok; j += gridDim.x) {
+      const Job jb = jobs[j];
+      const int total = jb.nst;
+      const int nchunks = (total + kChunkStages - 1) / kChunkStages;
+      float hi[32], lo[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        hi[c] = 0.f;
+        lo[c] = 0.f;
+      }
+      for (int ch = 0; ch < nchunks; ++ch) {
+        if (!mbar_wait(smem_u32(&accf_bar), chunk & 1, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+        for (int cg = 0; cg < 4; ++cg) {
+          const uint32_t col = cgrp * 32 + cg * 8;
+          float x0[8], x1[8], x2[8];
+          tmem_ld8(lane_addr + col, x0);
+          if (nlev > 1) tmem_ld8(lane_addr + 128 + col, x1);
+          if (nlev > 2) tmem_ld8(lane_addr + 256 + col, x2);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float a1 = nlev > 1 ? x1[c] : 0.f;
+            const float a2 = nlev > 2 ? x2[c] : 0.f;
+            float s, e, h, e2;
+            two_sum(x0[c], a1, s, e);
+            two_sum(hi[cg * 8 + c], s, h, e2);
+            const float l = lo[cg * 8 + c] + (e2 + (e + a2));
+            const float hs = h + l;
+            lo[cg * 8 + c] = l - (hs - h);
+            hi[cg * 8 + c] = hs;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar)) : "memory");
+        chunk += 1;
+      }
+      if (!ok) break;
+      // epilogue: scale by 2^(rexp + cexp - shift) and write
+      const int r = jb.tr * kRows + row;
+      if (r < jb.rows) {
+        const int er = rexp[jb.rsc + r];
+        const int c0 = jb.tc * kRows + cgrp * 32;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          int ce[8];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) ce[c] = (c0 + g * 8 + c < jb.cols) ? cexp[jb.csc + c0 + g * 8 + c] : 0;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const int cc = c0 + g * 8 + c;
+            if (cc < jb.cols) {
+              const int ex = er + ce[c] - shift;
+              const int64_t o = jb.out_off + r + (int64_t)cc * jb.ld;
+              if (MODE == MODE_T) {
+                Th[o] = ldexp_f(hi[g * 8 + c], ex);
+                Tl[o] = ldexp_f(lo[g * 8 + c], ex);
+              } else {
+                F[o] += ldexp((double)hi[g * 8 + c] + (double)lo[g * 8 + c], ex);
+              }
+            }
+          }
+        }
+      }
+    }
+    if (!ok) {
+      abort_flag = 1;
+      atomicExch(status, 4);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+}
+
+}  // namespace sp
+}  // namespace su2

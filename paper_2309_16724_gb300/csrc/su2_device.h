@@ -124,6 +124,9 @@ struct su2_env {
   std::vector<su2::Task> tasks;
   su2_env_info info{};
   int64_t psi_len = 0;
+  std::vector<su2::Block> blocks;   // psi blocks
+  std::vector<su2::Sector> lsec, rsec;
+  int64_t split_budget = 0;
   // FP64 plan
   std::vector<su2::Chunk> chunks;
   std::vector<su2::K1Job> k1;

@@ -1,0 +1,83 @@
+"""GPU parity of the split-precision (BF16 slices on tcgen05) path.
+
+Bar (the benchmark spec): relative 2-norm error of H.psi <= 1e-10 against the FP64
+oracle and against the GPU FP64 path on the same inputs; the device status
+word stays clear (no bounded wait gave up).
+"""
+import numpy as np
+import pytest
+
+import synth
+
+from gpu_common import oracle_apply, oracle_problem, rel_err
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL_SPLIT = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_16724_gb300 as P
+    return P.Context(0, stream=torch.cuda.current_stream())
+
+
+def run(ctx, env, psi, prec):
+    import paper_2309_16724_gb300 as P
+    x = torch.from_numpy(psi).cuda()
+    y = torch.empty_like(x)
+    P.apply_heff(ctx, env, x, y, prec)
+    assert ctx.status() == 0
+    return y.cpu().numpy()
+
+
+CASES = [
+    synth.Config("qc8", synth.SPATIAL_ORBITAL, 8, 8, 0, 12, 5),
+    synth.Config("qc10S3", synth.SPATIAL_ORBITAL, 10, 9, 3, 40, 8),
+    synth.Config("qc12D100", synth.SPATIAL_ORBITAL, 12, 12, 0, 100, 9),
+    synth.CONFIGS["heis12"],
+    synth.CONFIGS["qc16"],
+]
+
+
+@pytest.mark.parametrize("cfg", CASES, ids=lambda c: c.name)
+def test_split_matches_oracle(ctx, cfg):
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    p = oracle_problem(cfg)
+    psi = synth.gaussian_psi(p["n"], synth.psi_seed(cfg))
+    F = oracle_apply(p, psi)
+    sec, env = workload.build(ctx, cfg, prepare_split=True)
+    G = run(ctx, env, psi, P.SU2_SPLIT_BF16)
+    assert rel_err(G, F) <= TOL_SPLIT, rel_err(G, F)
+    H = run(ctx, env, psi, P.SU2_FP64)
+    assert rel_err(G, H) <= TOL_SPLIT
+
+
+def test_split_chunking_and_repeat(ctx):
+    """Many term chunks, and two calls in a row give identical results."""
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    cfg = CASES[2]
+    sec, env = workload.build(ctx, cfg, prepare_split=True, t_budget_bytes=1 << 20)
+    psi = synth.gaussian_psi(sec.psi_len, 4)
+    a = run(ctx, env, psi, P.SU2_SPLIT_BF16)
+    b = run(ctx, env, psi, P.SU2_SPLIT_BF16)
+    assert np.array_equal(a, b)
+    H = run(ctx, env, psi, P.SU2_FP64)
+    assert rel_err(a, H) <= TOL_SPLIT
+
+
+@pytest.mark.parametrize("S,tol", [(3, 1e-5), (4, 1e-7), (5, 1e-9), (6, 1e-10)])
+def test_slice_count_controls_error(ctx, S, tol):
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    cfg = CASES[2]
+    sec, env = workload.build(ctx, cfg, prepare_split=True, n_slices=S)
+    psi = synth.gaussian_psi(sec.psi_len, 6)
+    G = run(ctx, env, psi, P.SU2_SPLIT_BF16)
+    H = run(ctx, env, psi, P.SU2_FP64)
+    assert rel_err(G, H) <= tol
