@@ -25,6 +25,7 @@ void dav_diag_set(cudaStream_t, double*, int, int, const double*);
 void dav_copy_col(cudaStream_t, double*, int, int, const double*, int);
 // split-precision path (heff_split.cu)
 int split_prepare(su2_env* env, int n_slices, std::string& err);
+int generate_side(const SideOps& so, double* d_arena, cudaStream_t s);
 int split_apply(su2_env* env, const double* psi, double* F, std::string& err);
 void split_free(su2_env* env);
 }  // namespace su2
@@ -377,8 +378,9 @@ int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond
   env->split_budget = (opts && opts->t_budget_bytes > 0) ? opts->t_budget_bytes : 0;
   try {
     env->table = make_table(*H, S->site_kind);
-    std::string err = build_side_ops(env->table, true, lch, *H, env->L);
-    if (err.empty()) err = build_side_ops(env->table, false, rch, *H, env->R);
+    const bool host_values = ctx->device < 0;
+    std::string err = build_side_ops(env->table, true, lch, *H, env->L, host_values);
+    if (err.empty()) err = build_side_ops(env->table, false, rch, *H, env->R, host_values);
     if (err.empty()) err = build_tasks(env->table, S->left, S->right, S->blocks, S->twoS, env->L, env->R, env->tasks);
     if (!err.empty()) {
       delete env;
@@ -410,11 +412,22 @@ int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond
   }
   in.r_d = D > 0 ? Deff / D : 1.0;
   in.flops_u1_equiv = in.flops_su2 * in.r_d;
-  in.env_bytes = 8.0 * double(env->L.arena.size() + env->R.arena.size());
+  in.env_bytes = 8.0 * double(env->L.arena_size + env->R.arena_size);
   if (ctx->device >= 0) {
     int rc = set_device(ctx);
-    if (!rc) rc = upload(ctx, &env->dL, env->L.arena);
-    if (!rc) rc = upload(ctx, &env->dR, env->R.arena);
+    for (int side = 0; side < 2 && !rc; ++side) {
+      SideOps& so = side == 0 ? env->L : env->R;
+      double** dst = side == 0 ? &env->dL : &env->dR;
+      if (so.host_values) {
+        rc = upload(ctx, dst, so.arena);
+      } else {
+        rc = dev_alloc(ctx, dst, size_t(std::max<int64_t>(so.arena_size, 2)));
+        if (!rc) {
+          const int ce = generate_side(so, *dst, ctx->stream);
+          if (ce) rc = fail(ctx, SU2_ECUDA, std::string("operator generation: ") + cudaGetErrorString(cudaError_t(ce)));
+        }
+      }
+    }
     if (!rc) rc = dev_alloc(ctx, &env->dT, size_t(std::max<int64_t>(env->t_elems, 2)));
     if (!rc) rc = upload(ctx, &env->dk1, env->k1);
     if (!rc) rc = upload(ctx, &env->dk2, env->k2);
@@ -462,7 +475,14 @@ int su2_env_operator_block(const su2_env* env, int32_t side, int32_t op, int32_t
   const SideOps& so = side == 0 ? env->L : env->R;
   const int b = so.find(op, qo, qi);
   if (b < 0 || so.blocks[b].rows != rows || so.blocks[b].cols != cols) return SU2_EINVAL;
-  std::memcpy(out, &so.arena[so.blocks[b].off], sizeof(double) * size_t(rows) * cols);
+  if (so.host_values) {
+    std::memcpy(out, &so.arena[so.blocks[b].off], sizeof(double) * size_t(rows) * cols);
+    return SU2_OK;
+  }
+  const double* dsrc = (side == 0 ? env->dL : env->dR) + so.blocks[b].off;
+  if (cudaSetDevice(env->ctx->device) != cudaSuccess ||
+      cudaMemcpy(out, dsrc, sizeof(double) * size_t(rows) * cols, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SU2_ECUDA;
   return SU2_OK;
 }
 

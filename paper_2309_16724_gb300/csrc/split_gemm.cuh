@@ -12,12 +12,15 @@
 // K stages); all items of a job share the row and column scales, so the
 // K-concatenated stripe sum_items A_item . B_item^T accumulates in TMEM
 // without a separate reduction (the stripe product of Sec. III.A).  Slice
-// pairs (i, j), i + j < S, go to three FP32 TMEM accumulators by level
-// l = min(i + j, 2).  Levels 0 and 1 hold integer multiples of their unit
-// below 2^24 for K chunks of 128, hence are exact; level 2 carries the
-// 2^-16-weighted tail.  Every 128-K chunk the eight drain warps fold the
-// three levels into a float-float register accumulator; at the end of the
-// job they write the tile (K1: float-float T; K2: F += FP64).
+// pairs (i, j), i + j < S, go to four FP32 TMEM accumulators (512 columns)
+// by level l = min(i + j, 3).  Levels 0, 1 and 2 hold integer multiples of
+// their unit 2^-8l below 2^24 for K chunks of 128, hence are exact whatever
+// rounding the tensor core applies when it adds into the accumulator
+// (it truncates: a shared tail accumulator of many pairs would collect a
+// biased error of order #adds * 2^-23 of its size); level 3 carries the
+// 2^-24-weighted tail.  Every 128-K chunk the drain warps fold the four
+// levels into a float-float register accumulator; at the end of the job
+// they write the tile (K1: float-float T; K2: F += FP64).
 //
 // Warp roles (576 threads): warp 0 bulk-copy producer, warp 1 MMA issuer,
 // warps 2..17 drain/epilogue (TMEM lane quarter w%4, 32-column group (w-2)/4).
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const int nlev = S < 3 ? S : 3;
+  const int nlev = S < 4 ? S : 4;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -246,9 +249,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t sb = sa + S * kSub;
             for (int i = 0; i < S; ++i)
               for (int jj = 0; jj + i < S; ++jj) {
-                const int lvl = (i + jj) < 2 ? (i + jj) : 2;
-                // first MMA into each level in a chunk resets it
-                const bool first_pair = (lvl == 0) || (lvl == 1 && i == 0 && jj == 1) || (lvl == 2 && i == 0 && jj == 2);
+                const int lvl = (i + jj) < 3 ? (i + jj) : 3;
+                // first MMA into each level in a chunk (pair (0, lvl)) resets it
+                const bool first_pair = (i == 0 && jj == lvl);
 #pragma unroll
                 for (int kk = 0; kk < 2; ++kk) {
                   const uint32_t acc = (cpos == 0 && first_pair && kk == 0) ? 0u : 1u;
@@ -303,19 +306,21 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int cg = 0; cg < 4; ++cg) {
           const uint32_t col = cgrp * 32 + cg * 8;
-          float x0[8], x1[8], x2[8];
+          float x0[8], x1[8], x2[8], x3[8];
           tmem_ld8(lane_addr + col, x0);
           if (nlev > 1) tmem_ld8(lane_addr + 128 + col, x1);
           if (nlev > 2) tmem_ld8(lane_addr + 256 + col, x2);
+          if (nlev > 3) tmem_ld8(lane_addr + 384 + col, x3);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             const float a1 = nlev > 1 ? x1[c] : 0.f;
             const float a2 = nlev > 2 ? x2[c] : 0.f;
+            const float a3 = nlev > 3 ? x3[c] : 0.f;
             float s, e, h, e2;
             two_sum(x0[c], a1, s, e);
             two_sum(hi[cg * 8 + c], s, h, e2);
-            const float l = lo[cg * 8 + c] + (e2 + (e + a2));
+            const float l = lo[cg * 8 + c] + (e2 + (e + (a2 + a3)));
             const float hs = h + l;
             lo[cg * 8 + c] = l - (hs - h);
             hi[cg * 8 + c] = hs;

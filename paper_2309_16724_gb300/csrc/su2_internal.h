@@ -54,9 +54,21 @@ OpTable make_table(const su2_hamiltonian& H, int site_kind);
 
 // ---------------------------------------------------------------- operators
 struct OpBlock { int op, qo, qi, rows, cols; int64_t off; };
+// block of a synthetic operator generated on the device (counter-based
+// SplitMix64 entries; HAM = 0.1 (X + X^T) + diag(2r/d); ADJOINT from its base)
+struct GenBlock {
+  int64_t off, base_off;
+  int32_t rows, cols, kind, pad;  // kind: 0 random, 1 HAM, 2 adjoint
+  uint64_t key;
+  double scale;                   // 1/sqrt(max(rows, cols)) or the adjoint factor
+};
+
 struct SideOps {
   std::vector<OpBlock> blocks;
-  std::vector<double> arena;  // all blocks, column-major, 2-double aligned
+  std::vector<double> arena;  // all blocks, column-major, 2-double aligned (host mode)
+  int64_t arena_size = 0;     // doubles
+  bool host_values = true;
+  std::vector<GenBlock> gen;  // device-generated blocks (device mode)
   std::unordered_map<uint64_t, int> index;  // key(op, qo, qi) -> block
   static uint64_t key(int op, int qo, int qi) {
     return (uint64_t(uint32_t(op)) << 32) | (uint64_t(uint32_t(qo)) << 16) | uint64_t(uint32_t(qi));
@@ -77,7 +89,7 @@ struct Task {
 std::string build_blocks(const std::vector<Sector>& left, const std::vector<Sector>& right, int site_kind,
                          int N, int twoS, std::vector<Block>& blocks, int64_t& psi_len);
 std::string build_side_ops(const OpTable& t, bool left_side, const std::vector<std::vector<Sector>>& chain,
-                           const su2_hamiltonian& H, SideOps& out);
+                           const su2_hamiltonian& H, SideOps& out, bool host_values = true);
 std::string build_tasks(const OpTable& t, const std::vector<Sector>& left, const std::vector<Sector>& right,
                         const std::vector<Block>& blocks, int twoS, const SideOps& L, const SideOps& R,
                         std::vector<Task>& tasks);

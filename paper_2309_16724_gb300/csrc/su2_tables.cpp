@@ -277,12 +277,13 @@ std::string build_blocks(const std::vector<Sector>& left, const std::vector<Sect
 namespace {
 
 void add_block(SideOps& so, int op, int qo, int qi, int rows, int cols) {
-  OpBlock blk{op, qo, qi, rows, cols, int64_t(so.arena.size())};
+  OpBlock blk{op, qo, qi, rows, cols, so.arena_size};
   so.index[SideOps::key(op, qo, qi)] = int(so.blocks.size());
   so.blocks.push_back(blk);
   int64_t n = int64_t(rows) * cols;
   n = (n + 1) & ~int64_t(1);  // keep every block 16-byte aligned
-  so.arena.resize(so.arena.size() + n, 0.0);
+  so.arena_size += n;
+  if (so.host_values) so.arena.resize(size_t(so.arena_size), 0.0);
 }
 
 // structurally allowed (out, in) sector pairs of an operator
@@ -448,11 +449,14 @@ std::string heisenberg_ops(const std::vector<std::vector<Sector>>& chain, bool l
 }  // namespace
 
 std::string build_side_ops(const OpTable& t, bool left_side, const std::vector<std::vector<Sector>>& chain,
-                           const su2_hamiltonian& H, SideOps& out) {
+                           const su2_hamiltonian& H, SideOps& out, bool host_values) {
   const auto& ops = left_side ? t.lops : t.rops;
   const std::vector<Sector>& sec = chain.back();
   const uint64_t side = left_side ? 0 : 1;
   out = SideOps();
+  for (const auto& op : ops)
+    if (op.kind == OP_MPS_RENORM || op.kind == OP_SPINTOT || op.kind == OP_NUMTOT) host_values = true;
+  out.host_values = host_values;
   std::map<std::pair<int, int>, Mat> hH, hS;
   bool heis = false;
   for (const auto& op : ops) heis |= (op.kind == OP_MPS_RENORM);
@@ -467,18 +471,26 @@ std::string build_side_ops(const OpTable& t, bool left_side, const std::vector<s
       for (auto [qo, qi] : allowed(op, sec)) {
         const int ro = sec[qo].dim, ci = sec[qi].dim;
         add_block(out, oid, qo, qi, ro, ci);
-        double* m = &out.arena[out.blocks.back().off];
         const double s = 1.0 / std::sqrt(double(std::max(ro, ci)));
         const uint64_t key = block_key(H.seed, side, uint64_t(oid), uint64_t(qo), uint64_t(qi));
+        if (!host_values) {
+          out.gen.push_back(GenBlock{out.blocks.back().off, 0, ro, ci, 0, 0, key, s});
+          continue;
+        }
+        double* m = &out.arena[out.blocks.back().off];
         for (int64_t i = 0; i < int64_t(ro) * ci; ++i) m[i] = uniform_elem(key, uint64_t(i)) * s;
       }
     } else if (op.kind == OP_HAM) {
       for (int q = 0; q < int(sec.size()); ++q) {
         const int d = sec[q].dim;
         add_block(out, oid, q, q, d, d);
-        double* m = &out.arena[out.blocks.back().off];
         const double s = 1.0 / std::sqrt(double(d));
         const uint64_t key = block_key(H.seed, side, uint64_t(oid), uint64_t(q), uint64_t(q));
+        if (!host_values) {
+          out.gen.push_back(GenBlock{out.blocks.back().off, 0, d, d, 1, 0, key, s});
+          continue;
+        }
+        double* m = &out.arena[out.blocks.back().off];
         std::vector<double> X(size_t(d) * d);
         for (int64_t i = 0; i < int64_t(d) * d; ++i) X[i] = uniform_elem(key, uint64_t(i)) * s;
         for (int c = 0; c < d; ++c)
@@ -519,6 +531,10 @@ std::string build_side_ops(const OpTable& t, bool left_side, const std::vector<s
       const double f = (((e / 2) % 2) ? -1.0 : 1.0) * std::sqrt(double(Sb + 1) / double(Sa + 1));
       const int ro = sec[qi].dim, co = sec[qo].dim;
       add_block(out, oid, qi, qo, ro, co);
+      if (!host_values) {
+        out.gen.push_back(GenBlock{out.blocks.back().off, out.blocks[src].off, ro, co, 2, 0, 0, f});
+        continue;
+      }
       double* m = &out.arena[out.blocks.back().off];
       const double* s = &out.arena[out.blocks[src].off];  // co x ro  (rows qo, cols qi)
       for (int c = 0; c < co; ++c)

@@ -174,3 +174,25 @@ def test_error_statuses(ctx):
     # the context stays usable afterwards
     psi = synth.gaussian_psi(sec.psi_len, 1)
     assert np.isfinite(gpu_apply(ctx, env, psi)).all()
+
+
+def test_device_generated_operators_bit_identical(ctx):
+    """Synthetic entries generated on the GPU equal the host generator's."""
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    from oracle import env as oenv
+    cfg = SMALL[4]
+    p = oracle_problem(cfg)
+    hctx = P.Context(-1)
+    sec_d, env_d = workload.build(ctx, cfg)
+    sec_h, env_h = workload.build(hctx, cfg)
+    n = 0
+    for (side, oid), blk in p["env"].items():
+        for (qo, qi), M in blk.items():
+            s = 0 if side == "L" else 1
+            a = env_d.operator_block(s, oid, qo, qi, M.shape[0], M.shape[1])
+            b = env_h.operator_block(s, oid, qo, qi, M.shape[0], M.shape[1])
+            assert np.array_equal(a, b)
+            assert np.array_equal(a, M)
+            n += 1
+    assert n > 100
