@@ -91,7 +91,7 @@ typedef struct {
 typedef struct {
   int64_t t_budget_bytes;  /* device bytes for the intermediate T = E D^T of
                               one term chunk (0: library default)           */
-  int32_t n_slices;        /* BF16 slices per operand, 2..6 (0: default 6)  */
+  int32_t n_slices;        /* BF16 slices per operand, 2..6 (0: default 5)  */
   int32_t prepare_split;   /* 1: also build the split-precision arenas      */
 } su2_env_opts;
 
@@ -111,6 +111,9 @@ typedef struct {
   int32_t keep;        /* Ritz vectors kept on restart (2)      */
   int32_t max_iter;    /* iteration limit (200)                 */
   int32_t prec;        /* su2_prec of the H.psi inside           */
+  int32_t use_graph;   /* 1: capture one iteration (H.psi included) as a
+                          CUDA graph on the first step and replay it; the
+                          subspace size then lives on the device        */
 } su2_dav_opts;
 
 /* Context on CUDA device `device` (-1: host-only context that can build
@@ -189,7 +192,8 @@ int su2_davidson_destroy(su2_dav* dav);
  * returns, for kernel kind `kind` (0: FP64 K1, 1: FP64 K2, 2: split-path
  * slice kernel, 3: split-path K1, 4: split-path K2), the launches, total
  * device milliseconds and algorithmic flops since the last reset, and the
- * kind's name.  SU2_EINVAL for an unknown kind. */
+ * kind's name.  Kind 5 counts every kernel the hot path launched (also with
+ * profiling off; no timing).  SU2_EINVAL for an unknown kind. */
 int su2_profile_enable(su2_env* env, int32_t on);
 int su2_profile_reset(su2_env* env);
 int su2_profile_read(su2_env* env, int32_t kind, int64_t* launches, double* ms, double* flops, const char** name);

@@ -61,7 +61,7 @@ class EnvInfo(C.Structure):
 
 class DavOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_sub", C.c_int32), ("keep", C.c_int32),
-                ("max_iter", C.c_int32), ("prec", C.c_int32)]
+                ("max_iter", C.c_int32), ("prec", C.c_int32), ("use_graph", C.c_int32)]
 
 
 _lib = None
@@ -255,7 +255,7 @@ class Environment:
     def profile_read(self):
         """{name: (launches, ms, flops)} per kernel kind."""
         out = {}
-        for kind in range(5):
+        for kind in range(6):
             n, ms, fl, nm = C.c_int64(), C.c_double(), C.c_double(), C.c_char_p()
             self.ctx.check(lib().su2_profile_read(self.h, kind, C.byref(n), C.byref(ms), C.byref(fl),
                                                   C.byref(nm)))
@@ -290,10 +290,10 @@ class Davidson:
     """su2_davidson_create / su2_davidson_step / su2_energy."""
 
     def __init__(self, ctx: Context, env: Environment, psi0, tol=1e-8, max_sub=24, keep=2, max_iter=200,
-                 prec=SU2_FP64):
+                 prec=SU2_FP64, use_graph=False):
         self.ctx = ctx
         h = C.c_void_p()
-        o = DavOpts(tol, max_sub, keep, max_iter, prec)
+        o = DavOpts(tol, max_sub, keep, max_iter, prec, 1 if use_graph else 0)
         ctx.check(lib().su2_davidson_create(ctx.h, env.h, _ptr(psi0), C.byref(o), C.byref(h)))
         self.h = h
 

@@ -13,16 +13,22 @@
 
 namespace su2 {
 int dav_grid(int64_t n);
-void dav_multidot(cudaStream_t, const double*, int64_t, int, const double*, int64_t, double*, double*, double);
-void dav_combine(cudaStream_t, const double*, const double*, int64_t, int, const double*, int64_t, double*, double*);
-void dav_subtract(cudaStream_t, const double*, int64_t, int, const double*, int64_t, double*);
+void dav_multidot(cudaStream_t, const double*, int64_t, int, const double*, int64_t, double*, double*, double,
+                  const int* dn = nullptr);
+void dav_combine(cudaStream_t, const double*, const double*, int64_t, int, const double*, int64_t, double*, double*,
+                 const int* dn = nullptr);
+void dav_subtract(cudaStream_t, const double*, int64_t, int, const double*, int64_t, double*, const int* dn = nullptr);
 void dav_residual(cudaStream_t, const double*, const double*, const double*, int64_t, double*);
 void dav_precond(cudaStream_t, const double*, const double*, const double*, int64_t, double*);
 void dav_scale(cudaStream_t, double*, const double*, const double*, int64_t);
-void dav_jacobi(cudaStream_t, const double*, int, int, double*, double*, int*);
+void dav_jacobi(cudaStream_t, const double*, int, int, double*, double*, int*, const int* dn = nullptr);
 void dav_absmax(cudaStream_t, const double*, int64_t, double*, int64_t*, int*);
 void dav_diag_set(cudaStream_t, double*, int, int, const double*);
-void dav_copy_col(cudaStream_t, double*, int, int, const double*, int);
+void dav_copy_col(cudaStream_t, double*, int, int, const double*, int, const int* dn = nullptr);
+void dav_newest(cudaStream_t, double*, int64_t, const int*, double*, int);
+void dav_restart(cudaStream_t, double*, double*, int64_t, const double*, int, double*, const double*, int, int, int*,
+                 double*);
+void dav_append(cudaStream_t, double*, int64_t, int*, const double*, const double*);
 // split-precision path (heff_split.cu)
 int split_prepare(su2_env* env, int n_slices, std::string& err);
 int generate_side(const SideOps& so, double* d_arena, cudaStream_t s);
@@ -436,7 +442,7 @@ int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond
     if (!rc) rc = upload(ctx, &env->ddt, env->dt);
     if (!rc && opts && opts->prepare_split) {
       std::string err;
-      rc = split_prepare(env, opts->n_slices > 0 ? opts->n_slices : 6, err);
+      rc = split_prepare(env, opts->n_slices > 0 ? opts->n_slices : 5, err);
       if (rc) fail(ctx, rc, err);
     }
     if (rc) {
@@ -549,7 +555,8 @@ int su2_profile_reset(su2_env* env) {
 }
 
 int su2_profile_read(su2_env* env, int32_t kind, int64_t* launches, double* ms, double* flops, const char** name) {
-  static const char* names[kProfKinds] = {"k1_fp64", "k2_fp64", "split_slices", "k1_split", "k2_split"};
+  static const char* names[kProfKinds] = {"k1_fp64", "k2_fp64", "split_slices", "k1_split", "k2_split",
+                                          "kernel_launches"};
   if (!env || kind < 0 || kind >= kProfKinds) return SU2_EINVAL;
   env->prof.drain();
   if (launches) *launches = env->prof.launches[kind];
@@ -584,10 +591,27 @@ struct su2_dav {
   int nsub = 0, iters = 0;
   double theta = 0.0, res = 0.0;
   bool converged = false;
+  // graph mode: the subspace size lives on the device and one iteration
+  // (H.v included) is a captured CUDA graph replayed on a private stream
+  bool use_graph = false, graph_ready = false;
+  int* d_nsub = nullptr;
+  double *w_in = nullptr, *w_out = nullptr;
+  cudaStream_t gstream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 };
 
 static void dav_free(su2_dav* d) {
   if (d->ctx && d->ctx->device >= 0) cudaSetDevice(d->ctx->device);
+  if (d->gexec) cudaGraphExecDestroy(d->gexec);
+  if (d->graph) cudaGraphDestroy(d->graph);
+  if (d->gstream) cudaStreamDestroy(d->gstream);
+  if (d->ev_in) cudaEventDestroy(d->ev_in);
+  if (d->ev_out) cudaEventDestroy(d->ev_out);
+  cudaFree(d->d_nsub);
+  cudaFree(d->w_in);
+  cudaFree(d->w_out);
   double* ps[] = {d->V, d->AV, d->x, d->ax, d->r, d->t, d->tmp, d->diag, d->Hsub, d->Y, d->w, d->h, d->partial, d->scal};
   for (double* p : ps) cudaFree(p);
   cudaFree(d->pidx);
@@ -617,6 +641,7 @@ int su2_davidson_create(su2_ctx* ctx, const su2_env* env, const double* psi0, co
     if (opts->keep > 0) d->o.keep = opts->keep;
     if (opts->max_iter > 0) d->o.max_iter = opts->max_iter;
     d->o.prec = opts->prec;
+    d->use_graph = opts->use_graph != 0;
   }
   if (d->o.max_sub > 32 || d->o.max_sub < 3 || d->o.keep >= d->o.max_sub) {
     delete d;
@@ -642,6 +667,15 @@ int su2_davidson_create(su2_ctx* ctx, const su2_env* env, const double* psi0, co
   if (!rc) rc = dev_alloc(ctx, &d->scal, size_t(8));
   if (!rc) rc = dev_alloc(ctx, &d->pidx, size_t(ng));
   if (!rc && cudaMallocHost(&d->host, 4 * sizeof(double)) != cudaSuccess) rc = fail(ctx, SU2_ENOMEM, "pinned host");
+  if (!rc && d->use_graph) {
+    rc = dev_alloc(ctx, &d->d_nsub, 1);
+    if (!rc) rc = dev_alloc(ctx, &d->w_in, size_t(n));
+    if (!rc) rc = dev_alloc(ctx, &d->w_out, size_t(n));
+    if (!rc && (cudaStreamCreateWithFlags(&d->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&d->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&d->ev_out, cudaEventDisableTiming) != cudaSuccess))
+      rc = fail(ctx, SU2_ECUDA, "graph stream/events");
+  }
   if (rc) {
     dav_free(d);
     delete d;
@@ -659,6 +693,11 @@ int su2_davidson_create(su2_ctx* ctx, const su2_env* env, const double* psi0, co
   dav_scale(s, d->V, psi0, d->scal, n);
   cudaMemsetAsync(d->Hsub, 0, 32 * 32 * sizeof(double), s);
   d->nsub = 1;
+  if (d->use_graph) {
+    const int one = 1;
+    cudaMemcpyAsync(d->d_nsub, &one, sizeof(int), cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+  }
   if (cudaGetLastError() != cudaSuccess) {
     dav_free(d);
     delete d;
@@ -668,10 +707,86 @@ int su2_davidson_create(su2_ctx* ctx, const su2_env* env, const double* psi0, co
   return SU2_OK;
 }
 
+// one Davidson iteration with the subspace size on the device, recorded on
+// stream s (for capture); results land in the pinned host buffer
+static int dav_record_iteration(su2_ctx* ctx, su2_dav* d, cudaStream_t s) {
+  const int64_t n = d->n;
+  const int ld = 32;
+  dav_newest(s, d->V, n, d->d_nsub, d->w_in, 0);
+  int rc = su2_apply_heff(ctx, d->env, d->w_in, d->w_out, d->o.prec);
+  if (rc) return rc;
+  dav_newest(s, d->AV, n, d->d_nsub, d->w_out, 1);
+  dav_multidot(s, d->V, n, 0, d->w_out, n, d->partial, d->h, 1.0, d->d_nsub);
+  dav_copy_col(s, d->Hsub, ld, 0, d->h, 0, d->d_nsub);
+  dav_jacobi(s, d->Hsub, ld, 0, d->w, d->Y, ctx->d_status, d->d_nsub);
+  dav_combine(s, d->V, d->AV, n, 0, d->Y, n, d->x, d->ax, d->d_nsub);
+  dav_residual(s, d->x, d->ax, d->w, n, d->r);
+  dav_multidot(s, d->r, n, 1, d->r, n, d->partial, d->scal, 1.0);
+  dav_precond(s, d->r, d->diag, d->w, n, d->t);
+  dav_restart(s, d->V, d->AV, n, d->Y, ld, d->Hsub, d->w, d->o.keep, d->o.max_sub, d->d_nsub, d->tmp);
+  for (int pass = 0; pass < 2; ++pass) {
+    dav_multidot(s, d->V, n, 0, d->t, n, d->partial, d->h, 1.0, d->d_nsub);
+    dav_subtract(s, d->V, n, 0, d->h, n, d->t, d->d_nsub);
+  }
+  dav_multidot(s, d->t, n, 1, d->t, n, d->partial, d->scal + 1, 1.0);
+  dav_append(s, d->V, n, d->d_nsub, d->t, d->scal + 1);
+  cudaMemcpyAsync(d->host, d->w, sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(d->host + 1, d->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  return SU2_OK;
+}
+
+static int dav_graph_step(su2_ctx* ctx, su2_dav* d) {
+  if (!d->graph_ready) {
+    su2_env* env = const_cast<su2_env*>(d->env);
+    const bool prof_on = env->prof.on;
+    env->prof.drain();
+    env->prof.on = false;
+    cudaStream_t saved = ctx->stream;
+    ctx->stream = d->gstream;
+    CUDA_TRY(ctx, cudaStreamBeginCapture(d->gstream, cudaStreamCaptureModeThreadLocal));
+    int rc = dav_record_iteration(ctx, d, d->gstream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(d->gstream, &g);
+    ctx->stream = saved;
+    env->prof.on = prof_on;
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (ce != cudaSuccess) return fail(ctx, SU2_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    d->graph = g;
+    CUDA_TRY(ctx, cudaGraphInstantiate(&d->gexec, d->graph, 0));
+    d->graph_ready = true;
+  }
+  CUDA_TRY(ctx, cudaEventRecord(d->ev_in, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamWaitEvent(d->gstream, d->ev_in, 0));
+  CUDA_TRY(ctx, cudaGraphLaunch(d->gexec, d->gstream));
+  CUDA_TRY(ctx, cudaEventRecord(d->ev_out, d->gstream));
+  CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, d->ev_out, 0));
+  CUDA_TRY(ctx, cudaStreamSynchronize(d->gstream));
+  return SU2_OK;
+}
+
 int su2_davidson_step(su2_ctx* ctx, su2_dav* d, double* theta, double* resnorm) {
   if (!ctx || !d || d->ctx != ctx) return fail(ctx, SU2_EINVAL, "null argument");
   int rc = set_device(ctx);
   if (rc) return rc;
+  if (d->use_graph) {
+    if (d->converged) {
+      if (theta) *theta = d->theta;
+      if (resnorm) *resnorm = d->res;
+      return SU2_OK;
+    }
+    rc = dav_graph_step(ctx, d);
+    if (rc) return rc;
+    d->iters += 1;
+    d->theta = d->host[0];
+    d->res = std::sqrt(std::max(0.0, d->host[1]));
+    if (theta) *theta = d->theta;
+    if (resnorm) *resnorm = d->res;
+    if (d->res <= d->o.tol || !(d->host[2] > 1e-28)) d->converged = true;
+    return SU2_OK;
+  }
   cudaStream_t s = ctx->stream;
   const int64_t n = d->n;
   const int ms = d->o.max_sub, ld = 32;

@@ -21,7 +21,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 // partial[blockIdx.x * nvec + i] = sum over this CTA's slice of V_i . w
 __global__ void __launch_bounds__(kRedThreads) multidot_kernel(const double* __restrict__ V, int64_t ldv, int nvec,
                                                                const double* __restrict__ w, int64_t n,
-                                                               double* __restrict__ partial) {
+                                                               double* __restrict__ partial, const int* __restrict__ dn) {
+  if (dn) nvec = *dn + nvec;
   __shared__ double red[kRedThreads / 32][kMaxSub];
   double acc[kMaxSub];
 #pragma unroll
@@ -50,7 +51,8 @@ __global__ void __launch_bounds__(kRedThreads) multidot_kernel(const double* __r
 
 // out[i] = scale * sum_g partial[g*nvec + i]  (fixed order)
 __global__ void reduce_partials_kernel(const double* __restrict__ partial, int ng, int nvec, double scale,
-                                       double* __restrict__ out) {
+                                       double* __restrict__ out, const int* __restrict__ dn) {
+  if (dn) nvec = *dn + nvec;
   const int i = threadIdx.x;
   if (i < nvec) {
     double s = 0.0;
@@ -62,7 +64,8 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial, int n
 // out = sum_i y[i] V_i    (and optionally out2 = sum_i y[i] W_i)
 __global__ void combine_kernel(const double* __restrict__ V, const double* __restrict__ W, int64_t ldv, int nvec,
                                const double* __restrict__ y, int64_t n, double* __restrict__ out,
-                               double* __restrict__ out2) {
+                               double* __restrict__ out2, const int* __restrict__ dn) {
+  if (dn) nvec = *dn + nvec;
   __shared__ double sy[kMaxSub];
   if (threadIdx.x < nvec) sy[threadIdx.x] = y[threadIdx.x];
   __syncthreads();
@@ -80,7 +83,8 @@ __global__ void combine_kernel(const double* __restrict__ V, const double* __res
 
 // t -= sum_i h[i] V_i
 __global__ void subtract_kernel(const double* __restrict__ V, int64_t ldv, int nvec, const double* __restrict__ h,
-                                int64_t n, double* __restrict__ t) {
+                                int64_t n, double* __restrict__ t, const int* __restrict__ dn) {
+  if (dn) nvec = *dn + nvec;
   __shared__ double sh[kMaxSub];
   if (threadIdx.x < nvec) sh[threadIdx.x] = h[threadIdx.x];
   __syncthreads();
@@ -123,7 +127,8 @@ __global__ void scale_kernel(double* __restrict__ y, const double* __restrict__ 
 // cyclic Jacobi on the symmetrised nsub x nsub matrix H (leading dim ld);
 // outputs ascending eigenvalues w and eigenvectors Y (column j, ld rows)
 __global__ void jacobi_kernel(const double* __restrict__ H, int ld, int n, double* __restrict__ w,
-                              double* __restrict__ Y, int* __restrict__ status) {
+                              double* __restrict__ Y, int* __restrict__ status, const int* __restrict__ dn) {
+  if (dn) n = *dn + n;
   __shared__ double A[kMaxSub][kMaxSub + 1], V[kMaxSub][kMaxSub + 1];
   __shared__ double cs[2];
   __shared__ int done;
@@ -239,12 +244,82 @@ __global__ void diag_set_kernel(double* __restrict__ H, int ld, int n, const dou
   }
 }
 
-__global__ void copy_col_kernel(double* __restrict__ H, int ld, int col, const double* __restrict__ h, int n) {
+__global__ void copy_col_kernel(double* __restrict__ H, int ld, int col, const double* __restrict__ h, int n,
+                                const int* __restrict__ dn) {
+  if (dn) {  // column nsub-1, n = nsub
+    n = *dn;
+    col = n - 1;
+  }
   const int i = threadIdx.x;
   if (i < n) {
     H[i + col * ld] = h[i];
     H[col + i * ld] = h[i];
   }
+}
+
+// ---- device-side subspace bookkeeping (graph-capturable Davidson iteration)
+// dst = V[nsub-1] (dir 0) or V[nsub-1] = src (dir 1)
+__global__ void newest_copy_kernel(double* __restrict__ V, int64_t n, const int* __restrict__ dn,
+                                   double* __restrict__ w, int dir) {
+  const int64_t base = int64_t(*dn - 1) * n;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    if (dir == 0) w[i] = V[base + i];
+    else V[base + i] = w[i];
+  }
+}
+
+// restart when the subspace is full: V[q] <- V Y[:, q], AV[q] <- AV Y[:, q]
+// for q < keep (into tmp, then back), H <- diag(w[:keep]); sets *dn = keep
+__global__ void restart_combine_kernel(const double* __restrict__ V, const double* __restrict__ AV, int64_t n,
+                                       const double* __restrict__ Y, int ld, int keep, int max_sub,
+                                       const int* __restrict__ dn, double* __restrict__ tmp) {
+  if (*dn < max_sub) return;
+  const int nv = *dn;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < n; x += stride)
+    for (int q = 0; q < keep; ++q) {
+      double a = 0.0, b = 0.0;
+      for (int i = 0; i < nv; ++i) {
+        a = fma(Y[i + q * ld], V[int64_t(i) * n + x], a);
+        b = fma(Y[i + q * ld], AV[int64_t(i) * n + x], b);
+      }
+      tmp[int64_t(2 * q) * n + x] = a;
+      tmp[int64_t(2 * q + 1) * n + x] = b;
+    }
+}
+__global__ void restart_copy_kernel(double* __restrict__ V, double* __restrict__ AV, int64_t n, int keep, int max_sub,
+                                    const int* __restrict__ dn, const double* __restrict__ tmp) {
+  if (*dn < max_sub) return;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < n; x += stride)
+    for (int q = 0; q < keep; ++q) {
+      V[int64_t(q) * n + x] = tmp[int64_t(2 * q) * n + x];
+      AV[int64_t(q) * n + x] = tmp[int64_t(2 * q + 1) * n + x];
+    }
+}
+__global__ void restart_finish_kernel(double* __restrict__ H, int ld, const double* __restrict__ w, int keep,
+                                      int max_sub, int* __restrict__ dn) {
+  if (*dn < max_sub) return;
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < ld * ld; idx += blockDim.x) {
+    const int i = idx % ld, j = idx / ld;
+    H[idx] = (i == j && i < keep) ? w[i] : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *dn = keep;
+}
+// V[nsub] = t / ||t|| when ||t||^2 > tiny (else the subspace is left as is)
+__global__ void append_kernel(double* __restrict__ V, int64_t n, const int* __restrict__ dn,
+                              const double* __restrict__ t, const double* __restrict__ nrm2) {
+  if (!(*nrm2 > 1e-28)) return;
+  const double s = 1.0 / sqrt(*nrm2);
+  const int64_t base = int64_t(*dn) * n;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) V[base + i] = t[i] * s;
+}
+__global__ void append_count_kernel(int* __restrict__ dn, const double* __restrict__ nrm2) {
+  if (threadIdx.x == 0 && *nrm2 > 1e-28) *dn += 1;
 }
 
 }  // namespace
@@ -255,17 +330,18 @@ int dav_grid(int64_t n) {
 }
 
 void dav_multidot(cudaStream_t s, const double* V, int64_t ldv, int nvec, const double* w, int64_t n,
-                  double* partial, double* out, double scale) {
+                  double* partial, double* out, double scale, const int* dn) {
   const int g = dav_grid(n);
-  multidot_kernel<<<g, kRedThreads, 0, s>>>(V, ldv, nvec, w, n, partial);
-  reduce_partials_kernel<<<1, 32, 0, s>>>(partial, g, nvec, scale, out);
+  multidot_kernel<<<g, kRedThreads, 0, s>>>(V, ldv, nvec, w, n, partial, dn);
+  reduce_partials_kernel<<<1, 32, 0, s>>>(partial, g, nvec, scale, out, dn);
 }
 void dav_combine(cudaStream_t s, const double* V, const double* W, int64_t ldv, int nvec, const double* y, int64_t n,
-                 double* out, double* out2) {
-  combine_kernel<<<dav_grid(n), 256, 0, s>>>(V, W, ldv, nvec, y, n, out, out2);
+                 double* out, double* out2, const int* dn) {
+  combine_kernel<<<dav_grid(n), 256, 0, s>>>(V, W, ldv, nvec, y, n, out, out2, dn);
 }
-void dav_subtract(cudaStream_t s, const double* V, int64_t ldv, int nvec, const double* h, int64_t n, double* t) {
-  subtract_kernel<<<dav_grid(n), 256, 0, s>>>(V, ldv, nvec, h, n, t);
+void dav_subtract(cudaStream_t s, const double* V, int64_t ldv, int nvec, const double* h, int64_t n, double* t,
+                  const int* dn) {
+  subtract_kernel<<<dav_grid(n), 256, 0, s>>>(V, ldv, nvec, h, n, t, dn);
 }
 void dav_residual(cudaStream_t s, const double* x, const double* ax, const double* theta, int64_t n, double* r) {
   residual_kernel<<<dav_grid(n), 256, 0, s>>>(x, ax, theta, n, r);
@@ -276,8 +352,8 @@ void dav_precond(cudaStream_t s, const double* r, const double* diag, const doub
 void dav_scale(cudaStream_t s, double* y, const double* x, const double* nrm2, int64_t n) {
   scale_kernel<<<dav_grid(n), 256, 0, s>>>(y, x, nrm2, n);
 }
-void dav_jacobi(cudaStream_t s, const double* H, int ld, int n, double* w, double* Y, int* status) {
-  jacobi_kernel<<<1, 32, 0, s>>>(H, ld, n, w, Y, status);
+void dav_jacobi(cudaStream_t s, const double* H, int ld, int n, double* w, double* Y, int* status, const int* dn) {
+  jacobi_kernel<<<1, 32, 0, s>>>(H, ld, n, w, Y, status, dn);
 }
 void dav_absmax(cudaStream_t s, const double* x, int64_t n, double* pv, int64_t* pi, int* ng) {
   const int g = dav_grid(n);
@@ -287,8 +363,21 @@ void dav_absmax(cudaStream_t s, const double* x, int64_t n, double* pv, int64_t*
 void dav_diag_set(cudaStream_t s, double* H, int ld, int n, const double* w) {
   diag_set_kernel<<<1, 256, 0, s>>>(H, ld, n, w);
 }
-void dav_copy_col(cudaStream_t s, double* H, int ld, int col, const double* h, int n) {
-  copy_col_kernel<<<1, 32, 0, s>>>(H, ld, col, h, n);
+void dav_copy_col(cudaStream_t s, double* H, int ld, int col, const double* h, int n, const int* dn) {
+  copy_col_kernel<<<1, 32, 0, s>>>(H, ld, col, h, n, dn);
+}
+void dav_newest(cudaStream_t s, double* V, int64_t n, const int* dn, double* w, int dir) {
+  newest_copy_kernel<<<dav_grid(n), 256, 0, s>>>(V, n, dn, w, dir);
+}
+void dav_restart(cudaStream_t s, double* V, double* AV, int64_t n, const double* Y, int ld, double* H,
+                 const double* w, int keep, int max_sub, int* dn, double* tmp) {
+  restart_combine_kernel<<<dav_grid(n), 256, 0, s>>>(V, AV, n, Y, ld, keep, max_sub, dn, tmp);
+  restart_copy_kernel<<<dav_grid(n), 256, 0, s>>>(V, AV, n, keep, max_sub, dn, tmp);
+  restart_finish_kernel<<<1, 256, 0, s>>>(H, ld, w, keep, max_sub, dn);
+}
+void dav_append(cudaStream_t s, double* V, int64_t n, int* dn, const double* t, const double* nrm2) {
+  append_kernel<<<dav_grid(n), 256, 0, s>>>(V, n, dn, t, nrm2);
+  append_count_kernel<<<1, 32, 0, s>>>(dn, nrm2);
 }
 
 }  // namespace su2

@@ -133,6 +133,7 @@ void launch_heff_fp64(cudaStream_t s, const double* L, const double* R, const do
                       const K1Job* k1, const K2Job* k2, const K2Task* tasks, const Chunk& c, int64_t,
                       Profiler* prof) {
   const int64_t n1 = c.k1_end - c.k1_begin, n2 = c.k2_end - c.k2_begin;
+  prof->count(int(n1 > 0) + int(n2 > 0));
   if (n1 > 0) {
     const int slot = prof->begin(s, 0, c.k1_flops);
     k1_fp64<<<unsigned(n1), NT, 0, s>>>(k1 + c.k1_begin, psi, R, T);

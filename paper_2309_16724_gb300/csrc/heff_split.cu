@@ -9,8 +9,14 @@
 //    identity included) so that all tasks of one output tile share it; each
 //    block is additionally shifted up by delta_b = min_r (rho - e_b(r)) >= 0
 //    and the shift is folded into its tasks' coefficient (v * 2^-delta).
-//  * T'_t = v_t 2^-delta T_u (K2 B operand): a common column exponent
-//    gamma(f, c) per output column, the max over the tasks into f.
+//  * T'_t = v_t 2^-delta T_u (K2 B operand): the task's own column exponents
+//    phi_t + cexp_u(c), so every task keeps all S*8 bits of its own
+//    magnitude in every column; chunks of the K2 stripe end at task
+//    boundaries and the drain multiplies each chunk by the exact power of
+//    two 2^(own - gamma(f, c)), gamma the output block's column exponent (the
+//    max over its tasks).  A common column exponent for all tasks of a tile
+//    was measured to lose ~4 bits: each task's truncation error then scales
+//    with the largest task of the column, and thousands of tasks add up.
 //  * K1 (T = E D^T): per-row exponents of the psi blocks and of the right
 //    operator blocks.
 #include <algorithm>
@@ -94,6 +100,13 @@ struct SplitState {
   TPTask* d_tpt = nullptr;
   TPUnit* d_tpu = nullptr;
   int* d_status = nullptr;
+  int* d_counter = nullptr;
+  int *d_phi = nullptr, *d_tsrc = nullptr, *d_off = nullptr;  // per TP task: phi_t, source cexp offset, (unused)
+  float* d_scale = nullptr;      // per (task, column) drain factors of one chunk
+  int64_t* d_scoff = nullptr;    // per TP task: offset into d_scale (chunk-local)
+  std::vector<int64_t> scoff;
+  int64_t n_scale = 0;
+  std::vector<int> tsrc;
   int n_sms = 148;
 };
 
@@ -160,7 +173,7 @@ __global__ void delta_fix_kernel(int* __restrict__ delta, int n) {
 }
 
 // slab of FP64 matrices: one CTA of 128 threads per (desc, row tile, K stage);
-// thread = one slab row, 32 K elements = 4 core-matrix columns
+// thread = one slab row, 16 K elements = 2 core-matrix columns
 __global__ void slab_fp64_kernel(const SlabDesc* __restrict__ descs, const Unit* __restrict__ units,
                                  const double* __restrict__ src, const int* __restrict__ rexp,
                                  const int* __restrict__ delta, unsigned char* __restrict__ slab, int S) {
@@ -168,7 +181,7 @@ __global__ void slab_fp64_kernel(const SlabDesc* __restrict__ descs, const Unit*
   const SlabDesc d = descs[u.desc];
   const int t = threadIdx.x;
   const int r = u.tr * 128 + t;
-  const int kst = (d.cols + 31) / 32;
+  const int kst = (d.cols + sp::kKS - 1) / sp::kKS;
   unsigned char* base = slab + d.slab_off + (int64_t(u.tr) * kst + u.ks) * S * kSub;
   int sigma = 0;
   if (r < d.rows) {
@@ -178,11 +191,11 @@ __global__ void slab_fp64_kernel(const SlabDesc* __restrict__ descs, const Unit*
   }
   const int mi = t >> 3, rr = t & 7;
 #pragma unroll
-  for (int kg = 0; kg < 4; ++kg) {
+  for (int kg = 0; kg < 2; ++kg) {
     double y[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int k = u.ks * 32 + kg * 8 + q;
+      const int k = u.ks * sp::kKS + kg * 8 + q;
       double x = 0.0;
       if (r < d.rows && k < d.cols) {
         if (d.src_off < 0) x = (r == k) ? 1.0 : 0.0;
@@ -198,7 +211,7 @@ __global__ void slab_fp64_kernel(const SlabDesc* __restrict__ descs, const Unit*
         y[q] = (y[q] - qi) * 256.0;
         v[q] = __float2bfloat16_rn(ldexpf((float)qi, -8 * i));
       }
-      *(uint4*)(base + i * kSub + (mi * 4 + kg) * 128 + rr * 16) = *(const uint4*)v;
+      *(uint4*)(base + i * kSub + (mi * 2 + kg) * 128 + rr * 16) = *(const uint4*)v;
     }
   }
 }
@@ -244,12 +257,16 @@ __global__ void fill_kernel(int* __restrict__ p, int64_t n, int v) {
 }
 
 // gamma(f, c) = max over tasks of vexp + cexp(c): one CTA per task, threads over columns
+// reference column exponents of the output blocks (max over their tasks)
+// and each task's own exponent phi_t = exponent(v_t 2^-delta)
 __global__ void gamma_kernel(const TPTask* __restrict__ tasks, const Source* __restrict__ src,
-                             const int* __restrict__ cexp, const int* __restrict__ delta, int* __restrict__ gamma) {
+                             const int* __restrict__ cexp, const int* __restrict__ delta, int* __restrict__ gamma,
+                             int* __restrict__ phi) {
   const TPTask t = tasks[blockIdx.x];
   const Source s = src[t.src];
+  const int vexp = t.v == 0.0 ? kSentinel : exp_of(t.v) - delta[t.aid];
+  if (threadIdx.x == 0) phi[blockIdx.x] = vexp;
   if (t.v == 0.0) return;
-  const int vexp = exp_of(t.v) - delta[t.aid];
   for (int c = threadIdx.x; c < s.cols; c += blockDim.x) {
     const int ce = cexp[s.cexp_off + c];
     if (ce == kSentinel) continue;
@@ -258,34 +275,80 @@ __global__ void gamma_kernel(const TPTask* __restrict__ tasks, const Source* __r
 }
 
 // T' slab: rows = columns of the source, K = rows of the source
+// per-(task, column) drain factors 2^(phi_t + cexp(c) - gamma(c)) (0 for empty columns)
+__global__ void scale_kernel(const TPTask* __restrict__ tasks, const Source* __restrict__ src,
+                             const int* __restrict__ cexp, const int* __restrict__ gamma,
+                             const int* __restrict__ phi, const int64_t* __restrict__ sc_off, float* __restrict__ scale) {
+  const TPTask t = tasks[blockIdx.x];
+  const Source s = src[t.src];
+  const int ph = phi[blockIdx.x];
+  float* out = scale + sc_off[blockIdx.x];
+  for (int c = threadIdx.x; c < s.cols; c += blockDim.x) {
+    const int ce = cexp[s.cexp_off + c];
+    float f = 0.f;
+    if (ph > -1000 && ce > -1000) {
+      const int d = ph + ce - gamma[t.gcol + c];  // <= 0
+      f = d < -126 ? 0.f : __int_as_float((127 + d) << 23);
+    }
+    out[c] = f;
+  }
+}
+
+// slice offset of each task: o_t = floor(min_c (gamma(c) - phi_t - cexp(c)) / 8), in [0, 3]
+__global__ void offset_kernel(const TPTask* __restrict__ tasks, const Source* __restrict__ src,
+                              const int* __restrict__ cexp, const int* __restrict__ gamma,
+                              const int* __restrict__ phi, int* __restrict__ off) {
+  __shared__ int red[32];
+  const TPTask t = tasks[blockIdx.x];
+  const Source s = src[t.src];
+  const int ph = phi[blockIdx.x];
+  int m = 1 << 30;
+  if (ph > -1000)
+    for (int c = threadIdx.x; c < s.cols; c += blockDim.x) {
+      const int ce = cexp[s.cexp_off + c];
+      if (ce < -1000) continue;
+      m = min(m, gamma[t.gcol + c] - (ph + ce));
+    }
+  for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < int(blockDim.x >> 5); ++w) m = min(m, red[w]);
+    m = min(red[0], m);
+    off[blockIdx.x] = m >= (1 << 29) ? 3 : min(3, max(0, m / 8));
+  }
+}
+
 __global__ void slab_tprime_kernel(const TPTask* __restrict__ tasks, const TPUnit* __restrict__ units,
                                    const Source* __restrict__ src, const float* __restrict__ Th,
                                    const float* __restrict__ Tl, const float* __restrict__ Ph,
-                                   const float* __restrict__ Pl, const int* __restrict__ gamma,
-                                   const int* __restrict__ delta, unsigned char* __restrict__ slab, int S) {
+                                   const float* __restrict__ Pl, const int* __restrict__ cexp,
+                                   const int* __restrict__ phi, const int* __restrict__ delta,
+                                   unsigned char* __restrict__ slab, int S) {
   const TPUnit u = units[blockIdx.x];
   const TPTask t = tasks[u.task];
+  const int ph_t = phi[u.task];
   const double vs = ldexp(t.v, -delta[t.aid]);
   const float vh = (float)vs, vl = (float)(vs - (double)vh);
   const Source s = src[t.src];
   const int tt = threadIdx.x;
   const int c = u.tr * 128 + tt;  // slab row = source column
-  const int kst = (s.rows + 31) / 32;
+  const int kst = (s.rows + sp::kKS - 1) / sp::kKS;
   unsigned char* base = slab + t.tp_off + (int64_t(u.tr) * kst + u.ks) * S * kSub;
   const float* H = s.sel ? Ph : Th;
   const float* Lo = s.sel ? Pl : Tl;
-  int sc = 0;
+  int sc = 0;  // the task's own column exponent: |v 2^-delta T[:, c]| < 2^sc
   if (c < s.cols) {
-    sc = gamma[t.gcol + c];
-    if (sc < -1000) sc = 0;
+    const int ce = cexp[s.cexp_off + c];
+    sc = (ce < -1000 || ph_t < -1000) ? 0 : ph_t + ce;
   }
   const int mi = tt >> 3, rr = tt & 7;
 #pragma unroll
-  for (int kg = 0; kg < 4; ++kg) {
+  for (int kg = 0; kg < 2; ++kg) {
     float ph[8], pl[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int k = u.ks * 32 + kg * 8 + q;
+      const int k = u.ks * sp::kKS + kg * 8 + q;
       float a = 0.f, b = 0.f;
       if (c < s.cols && k < s.rows) {
         a = H[s.off + k + int64_t(c) * s.rows];
@@ -314,7 +377,7 @@ __global__ void slab_tprime_kernel(const TPTask* __restrict__ tasks, const TPUni
         ph[q] = hs * 256.f;
         v[q] = __float2bfloat16_rn(ldexpf(qi, -8 * i));
       }
-      *(uint4*)(base + i * kSub + (mi * 4 + kg) * 128 + rr * 16) = *(const uint4*)v;
+      *(uint4*)(base + i * kSub + (mi * 2 + kg) * 128 + rr * 16) = *(const uint4*)v;
     }
   }
 }
@@ -348,12 +411,18 @@ int dput(T** p, const std::vector<T>& h, std::string& err) {
 }
 
 int64_t slab_bytes(int rows, int cols, int S) {
-  return int64_t((rows + 127) / 128) * ((cols + 31) / 32) * S * kSub;
+  return int64_t((rows + 127) / 128) * ((cols + sp::kKS - 1) / sp::kKS) * S * kSub;
 }
 
 void add_units(std::vector<Unit>& u, int desc, int rows, int cols) {
   for (int tr = 0; tr < (rows + 127) / 128; ++tr)
-    for (int ks = 0; ks < (cols + 31) / 32; ++ks) u.push_back(Unit{desc, tr, ks, 0});
+    for (int ks = 0; ks < (cols + sp::kKS - 1) / sp::kKS; ++ks) u.push_back(Unit{desc, tr, ks, 0});
+}
+
+// MMA N of column tile tc of a block with `cols` columns
+int32_t nmma_of(int cols, int tc) {
+  const int rem = std::min(128, cols - tc * 128);
+  return int32_t((rem + 15) / 16 * 16);
 }
 
 int exp_host(double x) {
@@ -365,16 +434,17 @@ int exp_host(double x) {
 
 void launch_gemm(int mode, cudaStream_t s, SplitState* st, const Job* jobs, int njobs, const Item* items,
                  const unsigned char* A, const unsigned char* B, const int* rexp, const int* cexp, float* Th,
-                 float* Tl, double* F) {
+                 float* Tl, double* F, sp::TaskScale ts) {
   if (njobs <= 0) return;
-  const int smem = 2 * (2 * st->S * kSub) + 1024;
+  const int smem = sp::kStages * (2 * st->S * kSub) + 1024;
   const int grid = std::min(njobs, st->n_sms);
+  cudaMemsetAsync(st->d_counter, 0, sizeof(int), s);
   if (mode == sp::MODE_T)
     sp::split_gemm_kernel<sp::MODE_T><<<grid, sp::kThreads, smem, s>>>(jobs, njobs, items, A, B, rexp, cexp, 16,
-                                                                       st->S, Th, Tl, F, st->d_status);
+                                                                       st->S, Th, Tl, F, st->d_status, st->d_counter, ts);
   else
     sp::split_gemm_kernel<sp::MODE_F><<<grid, sp::kThreads, smem, s>>>(jobs, njobs, items, A, B, rexp, cexp, 16,
-                                                                       st->S, Th, Tl, F, st->d_status);
+                                                                       st->S, Th, Tl, F, st->d_status, st->d_counter, ts);
 }
 
 }  // namespace
@@ -391,7 +461,7 @@ int split_prepare(su2_env* env, int S, std::string& err) {
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, env->ctx->device);
   st->n_sms = prop.multiProcessorCount;
-  const int smem = 2 * (2 * S * kSub) + 1024;
+  const int smem = sp::kStages * (2 * S * kSub) + 1024;
   if (cudaFuncSetAttribute(sp::split_gemm_kernel<sp::MODE_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
           cudaSuccess ||
       cudaFuncSetAttribute(sp::split_gemm_kernel<sp::MODE_F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
@@ -400,6 +470,7 @@ int split_prepare(su2_env* env, int S, std::string& err) {
     return SU2_ECUDA;
   }
   st->d_status = env->ctx->d_status;
+  if (int rc0 = dalloc(&st->d_counter, 1, err)) return rc0;
   const auto& B = env->blocks;
   const auto& ls = env->lsec;
   const auto& L = env->L;
@@ -472,7 +543,12 @@ int split_prepare(su2_env* env, int S, std::string& err) {
   const int nterms = int(env->table.terms.size());
   std::vector<std::vector<int64_t>> by_term(nterms);
   for (int64_t i = 0; i < int64_t(env->tasks.size()); ++i) by_term[env->tasks[i].term].push_back(i);
-  const int64_t budget = env->split_budget > 0 ? env->split_budget : (int64_t(4) << 30);
+  int64_t budget = env->split_budget;
+  if (budget <= 0) {  // default: a quarter of the free device memory, at most 16 GiB
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    budget = std::min<int64_t>(int64_t(16) << 30, std::max<int64_t>(int64_t(fr) / 4, int64_t(1) << 30));
+  }
   std::vector<int> starts{0};
   {
     int64_t bytes = 0;
@@ -515,7 +591,7 @@ int split_prepare(su2_env* env, int S, std::string& err) {
     ch.k2_j0 = int64_t(st->k2j.size());
     std::unordered_map<uint64_t, int> umap;  // (dblk, e) -> source index (chunk-local)
     std::unordered_map<int, int> pmap;       // e -> psi source index
-    int64_t tsz = 0, csz = 0, tpsz = 0;
+    int64_t tsz = 0, csz = 0, tpsz = 0, scsz = 0;
     std::vector<Job> k1jobs;
     std::vector<int> k1cost;
     auto src_for = [&](const Task& t) -> int {
@@ -538,14 +614,14 @@ int split_prepare(su2_env* env, int S, std::string& err) {
       st->src.push_back(Source{tsz, k1, n, 0, int32_t(csz)});
       csz += n;
       umap[key] = id;
-      const int kst2 = (k2 + 31) / 32;
+      const int kst2 = (k2 + sp::kKS - 1) / sp::kKS;
       for (int tc = 0; tc < (n + 127) / 128; ++tc)
         for (int tr = 0; tr < (k1 + 127) / 128; ++tr) {
           const int ii = int(st->k1i.size());
           st->k1i.push_back(Item{st->edesc[t.e].slab_off + int64_t(tr) * kst2 * S * kSub,
-                                 st->ddesc[t.dblk].slab_off + int64_t(tc) * kst2 * S * kSub, kst2, 0});
+                                 st->ddesc[t.dblk].slab_off + int64_t(tc) * kst2 * S * kSub, kst2, 0, -1});
           k1jobs.push_back(Job{tsz, k1, n, k1, tr, tc, ii, ii + 1, int32_t(eps_off[t.e]),
-                               int32_t(zeta_off[t.dblk]), kst2});
+                               int32_t(zeta_off[t.dblk]), kst2, nmma_of(n, tc), 0});
           k1cost.push_back(kst2);
         }
       ch.k1_flops += 2.0 * k1 * k2 * n;
@@ -570,15 +646,22 @@ int split_prepare(su2_env* env, int S, std::string& err) {
       std::vector<int> aid(mine.size());
       std::vector<int64_t> tp(mine.size());
       std::vector<int> kst(mine.size());
+      std::vector<int> tid(mine.size());
+      std::vector<int64_t> sco(mine.size());
       for (size_t q = 0; q < mine.size(); ++q) {
         const Task& t = env->tasks[mine[q]];
         const Block& E = B[t.e];
         const int s = src_for(t);
         aid[q] = t.ablk >= 0 ? t.ablk : nLb + B[t.e].a;
         tp[q] = tpsz;
-        kst[q] = (E.rows + 31) / 32;
+        kst[q] = (E.rows + sp::kKS - 1) / sp::kKS;
         const int task_id = int(st->tpt.size() - ch.tp0);
+        tid[q] = task_id;
         st->tpt.push_back(TPTask{s, int32_t(goff[f]), aid[q], 0, t.v, tpsz});
+        st->tsrc.push_back(st->src[ch.src0 + s].cexp_off);
+        sco[q] = scsz;
+        st->scoff.push_back(scsz);
+        scsz += Fb.cols;
         for (int tr = 0; tr < (Fb.cols + 127) / 128; ++tr)
           for (int ks = 0; ks < kst[q]; ++ks) st->tpu.push_back(TPUnit{task_id, tr, ks, 0});
         tpsz += slab_bytes(Fb.cols, E.rows, S);
@@ -590,11 +673,11 @@ int split_prepare(su2_env* env, int S, std::string& err) {
           int tot = 0;
           for (size_t q = 0; q < mine.size(); ++q) {
             st->k2i.push_back(Item{st->adesc[aid[q]].slab_off + int64_t(tr) * kst[q] * S * kSub,
-                                   tp[q] + int64_t(tc) * kst[q] * S * kSub, kst[q], 0});
+                                   tp[q] + int64_t(tc) * kst[q] * S * kSub, kst[q], 0, sco[q]});
             tot += kst[q];
           }
           k2jobs.push_back(Job{Fb.offset, Fb.rows, Fb.cols, Fb.rows, tr, tc, i0, int(st->k2i.size()),
-                               int32_t(rho_off[Fb.a]), int32_t(goff[f]), tot});
+                               int32_t(rho_off[Fb.a]), int32_t(goff[f]), tot, nmma_of(Fb.cols, tc), 0});
           k2cost.push_back(tot);
         }
     }
@@ -616,6 +699,7 @@ int split_prepare(su2_env* env, int S, std::string& err) {
     max_t = std::max(max_t, tsz);
     max_tp = std::max(max_tp, tpsz);
     max_cexp = std::max(max_cexp, csz);
+    st->n_scale = std::max(st->n_scale, scsz);
   }
   if (int64_t(st->k2i.size()) >= INT32_MAX || int64_t(st->k1i.size()) >= INT32_MAX) {
     err = "split plan too large";
@@ -654,6 +738,11 @@ int split_prepare(su2_env* env, int S, std::string& err) {
   if (!rc2) rc2 = dput(&st->d_src, st->src, err);
   if (!rc2) rc2 = dput(&st->d_tpt, st->tpt, err);
   if (!rc2) rc2 = dput(&st->d_tpu, st->tpu, err);
+  if (!rc2) rc2 = dput(&st->d_tsrc, st->tsrc, err);
+  if (!rc2) rc2 = dalloc(&st->d_phi, std::max<size_t>(st->tpt.size(), 1), err);
+  if (!rc2) rc2 = dalloc(&st->d_off, std::max<size_t>(st->tpt.size(), 1), err);
+  if (!rc2) rc2 = dalloc(&st->d_scale, size_t(std::max<int64_t>(st->n_scale, 1)), err);
+  if (!rc2) rc2 = dput(&st->d_scoff, st->scoff, err);
   if (rc2) return rc2;
   std::vector<int64_t> colbase(st->src.size());
   for (size_t q = 0; q < st->src.size(); ++q) colbase[q] = st->src[q].cexp_off;
@@ -707,6 +796,7 @@ int split_apply(su2_env* env, const double* psi, double* F, std::string& err) {
   const int S = st->S;
   const int ne = int(st->eunit.size());
   SPLIT_CHECK("before");
+  pf.count(ne ? 3 : 1);
   int slot = pf.begin(s, 2, 0.0);
   psi_ff_kernel<<<1024, 256, 0, s>>>(psi, st->dPh, st->dPl, env->psi_len);
   if (ne) {
@@ -718,9 +808,10 @@ int split_apply(su2_env* env, const double* psi, double* F, std::string& err) {
   SPLIT_CHECK("psi slabs");
   const double npairs = S * (S + 1) / 2.0;
   for (const SChunk& c : st->chunks) {
+    pf.count(int(c.k1_j1 > c.k1_j0) + int(c.k2_j1 > c.k2_j0) + 5);
     slot = pf.begin(s, 3, c.k1_flops * npairs);
     launch_gemm(sp::MODE_T, s, st, st->d_k1j + c.k1_j0, int(c.k1_j1 - c.k1_j0), st->d_k1i, st->dE, st->dD, st->d_eps,
-                st->d_zeta, st->dTh, st->dTl, nullptr);
+                st->d_zeta, st->dTh, st->dTl, nullptr, sp::TaskScale{nullptr});
     pf.end(s, slot);
     SPLIT_CHECK("K1 split GEMM");
     slot = pf.begin(s, 2, 0.0);
@@ -735,19 +826,25 @@ int split_apply(su2_env* env, const double* psi, double* F, std::string& err) {
     SPLIT_CHECK("column exponents");
     fill_kernel<<<256, 256, 0, s>>>(st->d_gamma, st->n_gamma, kSentinel);
     const int ntp = int(c.tp1 - c.tp0);
-    if (ntp) gamma_kernel<<<ntp, 128, 0, s>>>(st->d_tpt + c.tp0, st->d_src + c.src0, st->d_cexp, st->d_delta, st->d_gamma);
+    if (ntp)
+      gamma_kernel<<<ntp, 128, 0, s>>>(st->d_tpt + c.tp0, st->d_src + c.src0, st->d_cexp, st->d_delta, st->d_gamma,
+                                       st->d_phi + c.tp0);
+    if (ntp)
+      scale_kernel<<<ntp, 128, 0, s>>>(st->d_tpt + c.tp0, st->d_src + c.src0, st->d_cexp, st->d_gamma,
+                                       st->d_phi + c.tp0, st->d_scoff + c.tp0, st->d_scale);
     const int64_t nu = c.tpu1 - c.tpu0;
     if (nu) {
       // units of this chunk refer to chunk-local task indices
       slab_tprime_kernel<<<unsigned(nu), 128, 0, s>>>(st->d_tpt + c.tp0, st->d_tpu + c.tpu0, st->d_src + c.src0,
-                                                      st->dTh, st->dTl, st->dPh, st->dPl, st->d_gamma, st->d_delta,
-                                                      st->dTP, S);
+                                                      st->dTh, st->dTl, st->dPh, st->dPl, st->d_cexp,
+                                                      st->d_phi + c.tp0, st->d_delta, st->dTP, S);
     }
     pf.end(s, slot);
     SPLIT_CHECK("T' slabs");
     slot = pf.begin(s, 4, c.k2_flops * npairs);
     launch_gemm(sp::MODE_F, s, st, st->d_k2j + c.k2_j0, int(c.k2_j1 - c.k2_j0), st->d_k2i, st->dA, st->dTP,
-                st->d_rho, st->d_gamma, nullptr, nullptr, F);
+                st->d_rho, st->d_gamma, nullptr, nullptr, F,
+                sp::TaskScale{st->d_scale});
     pf.end(s, slot);
     SPLIT_CHECK("K2 split GEMM");
   }
@@ -764,7 +861,8 @@ void split_free(su2_env* env) {
   void* ps[] = {st->dA, st->dD, st->dE, st->dTP, st->d_adesc, st->d_ddesc, st->d_edesc, st->d_aunit, st->d_dunit,
                 st->d_eunit, st->d_rho, st->d_aown, st->d_delta, st->d_zeta, st->d_eps, st->d_gamma, st->d_cexp,
                 st->dTh, st->dTl, st->dPh, st->dPl, st->d_k1j, st->d_k2j, st->d_k1i, st->d_k2i, st->d_src,
-                st->d_tpt, st->d_tpu, st->d_colbase};
+                st->d_tpt, st->d_tpu, st->d_colbase, st->d_counter, st->d_phi, st->d_tsrc, st->d_off,
+                st->d_scale, st->d_scoff};
   for (void* p : ps) cudaFree(p);
   delete st;
   env->split = nullptr;

@@ -1,10 +1,10 @@
 // Persistent split-precision stripe GEMM on tcgen05 (sm_103a).
 //
 // Operands are pre-tiled "slabs": an R x K FP64 matrix (R = M or N side,
-// K-major) cut into S BF16 slices, stored as 128-row x 32-K sub-tiles of
-// 8 KB in the UMMA no-swizzle K-major core-matrix layout (core matrix
-// (mi, ki) at (mi*4 + ki)*128 bytes, row r%8 at 16*(r%8)); for each
-// (row tile, K stage) the S slices follow each other (S*8 KB, one bulk
+// K-major) cut into S BF16 slices, stored as 128-row x 16-K sub-tiles of
+// 4 KB in the UMMA no-swizzle K-major core-matrix layout (core matrix
+// (mi, ki) at (mi*2 + ki)*128 bytes, row r%8 at 16*(r%8)); for each
+// (row tile, K stage) the S slices follow each other (S*4 KB, one bulk
 // copy).  Slice i holds q_i * 2^-8i where q_i are the integers peeled from
 // x * 2^(8 - sigma_row), |q_i| <= 257.
 //
@@ -18,12 +18,16 @@
 // rounding the tensor core applies when it adds into the accumulator
 // (it truncates: a shared tail accumulator of many pairs would collect a
 // biased error of order #adds * 2^-23 of its size); level 3 carries the
-// 2^-24-weighted tail.  Every 128-K chunk the drain warps fold the four
-// levels into a float-float register accumulator; at the end of the job
-// they write the tile (K1: float-float T; K2: F += FP64).
+// 2^-24-weighted tail.  A chunk is up to 128 K of one item; after it the
+// drain warps fold the four levels into a float-float register accumulator
+// (K2: scaled by the item's per-column factor, so every task keeps its own
+// S*8 bits) and zero TMEM; at the end of the job they write the tile (K1:
+// float-float T; K2: F += FP64).
 //
-// Warp roles (576 threads): warp 0 bulk-copy producer, warp 1 MMA issuer,
-// warps 2..17 drain/epilogue (TMEM lane quarter w%4, 32-column group (w-2)/4).
+// Warp roles (576 threads): warp 0 bulk-copy producer and job fetcher
+// (dynamic schedule: an atomic job counter, handed to the other roles through
+// a shared-memory ring), warp 1 MMA issuer, warps 2..17 drain/epilogue (TMEM
+// lane quarter w%4, 32-column group (w-2)/4).
 // Every mbarrier wait is bounded; on timeout the CTA records a status,
 // stops issuing, waits (bounded) for its own copies and MMAs, frees TMEM and
 // returns.
@@ -36,17 +40,26 @@ namespace su2 {
 namespace sp {
 
 constexpr int kRows = 128;           // M tile = N tile
-constexpr int kKS = 32;              // K per pipeline stage
-constexpr int kSub = kRows * kKS * 2;  // bytes of one 128 x 32 BF16 sub-tile
+constexpr int kKS = 16;              // K per pipeline stage (one MMA K step)
+constexpr int kSub = kRows * kKS * 2;  // bytes of one 128 x 16 BF16 sub-tile
 constexpr int kMaxS = 6;
-constexpr int kStages = 2;
-constexpr int kChunkStages = 4;      // 128 K per exact drain
+constexpr int kStages = 4;
+constexpr int kChunkStages = 8;      // 128 K per exact drain
+constexpr int kRing = 4;             // job ring slots
 constexpr int kThreads = 576;      // producer + MMA + 16 drain warps
 constexpr long kSpinLimit = 1L << 26;
 
 struct Item {
   int64_t a_off, b_off;  // byte offsets of the first (row tile, K stage) group
-  int32_t nst, pad;      // K stages of 32
+  int32_t nst;           // K stages of 16
+  int32_t pad;
+  int64_t sc_off;        // MODE_F: offset of the item's per-column scale factors, -1 otherwise
+};
+// MODE_F: task t's B slab is cut relative to its own column exponents; the
+// drain multiplies each chunk of t by scale[sc_off + col] = 2^(own - gamma(col))
+// (an exact power of two, <= 1) before adding it to the tile accumulator.
+struct TaskScale {
+  const float* scale;
 };
 struct Job {
   int64_t out_off;       // element offset of the output block
@@ -55,6 +68,8 @@ struct Job {
   int32_t i0, i1;        // items
   int32_t rsc, csc;      // offsets of the row / column exponent arrays
   int32_t nst;           // total K stages of all items
+  int32_t nmma;          // MMA N of this tile: the valid columns rounded up to 16 (<= 128)
+  int32_t pad2;
 };
 
 enum { MODE_T = 0, MODE_F = 1 };
@@ -81,23 +96,25 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 }
 
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
-  // no swizzle, K-major: LBO = 128 B (next core matrix along K), SBO = 512 B
+  // no swizzle, K-major: LBO = 128 B (next core matrix along K), SBO = 256 B
   // (next 8-row group), descriptor version 1 (bit 46)
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
   d |= (uint64_t)(128 >> 4) << 16;
-  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)(256 >> 4) << 32;
   d |= (uint64_t)1 << 46;
   return d;
 }
 
-// kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// kind::f16, A = B = BF16, D = F32, both K-major, M = 128, N = n (multiple of 16)
+__device__ __forceinline__ uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t(n) >> 3) << 17) | ((128u >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -124,6 +141,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_zero8(uint32_t taddr) {
+  const uint32_t z = 0u;
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr), "r"(z)
+               : "memory");
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   const float bb = s - a;
@@ -138,11 +161,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     split_gemm_kernel(const Job* __restrict__ jobs, int njobs, const Item* __restrict__ items,
                       const unsigned char* __restrict__ Aslab, const unsigned char* __restrict__ Bslab,
                       const int* __restrict__ rexp, const int* __restrict__ cexp, int shift, int S,
-                      float* __restrict__ Th, float* __restrict__ Tl, double* __restrict__ F, int* __restrict__ status) {
+                      float* __restrict__ Th, float* __restrict__ Tl, double* __restrict__ F, int* __restrict__ status,
+                      int* __restrict__ job_counter, TaskScale ts) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int stage_bytes = 2 * S * kSub;
   __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], accf_bar, acce_bar, done_bar;
+  __shared__ __align__(8) uint64_t jq_full[kRing], jq_empty[kRing];
+  __shared__ int job_ring[kRing];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   __shared__ int issued[kStages];
@@ -157,6 +183,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf_bar)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 512;" ::"r"(smem_u32(&acce_bar)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done_bar)));
+    for (int r = 0; r < kRing; ++r) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&jq_full[r])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 513;" ::"r"(smem_u32(&jq_empty[r])));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
   }
@@ -169,15 +199,39 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const int nlev = S < 4 ? S : 4;
+  // all accumulators start at zero; the drain zeroes them again after reading,
+  // so every MMA accumulates (levels need no per-chunk reset)
+  if (warp >= 2) {
+    const uint32_t la = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const int cg = (warp - 2) >> 2;
+    for (int lv = 0; lv < 4; ++lv)
+      for (int c8 = 0; c8 < 4; ++c8) tmem_zero8(la + lv * 128 + cg * 32 + c8 * 8);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       int st = 0;
-      uint32_t use[kStages] = {0, 0};
+      uint32_t use[kStages] = {0, 0, 0, 0};
       bool ok = true;
-      for (int j = blockIdx.x; j < njobs && ok; j += gridDim.x) {
+      for (int k = 0; ok; ++k) {
+        const int slot = k % kRing;
+        if (!mbar_wait(smem_u32(&jq_empty[slot]), ((k / kRing) & 1) ^ 1, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        const int jnext = atomicAdd(job_counter, 1);
+        const int j = jnext < njobs ? jnext : -1;
+        job_ring[slot] = j;
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&jq_full[slot])) : "memory");
+        if (j < 0) break;
         const Job jb = jobs[j];
+        const int bbytes = jb.nmma * 32;  // first nmma rows of each B slice sub-tile
+        const int tx = S * kSub + S * bbytes;
         for (int it = jb.i0; it < jb.i1 && ok; ++it) {
           const Item item = items[it];
           for (int ks = 0; ks < item.nst; ++ks) {
@@ -186,8 +240,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             const uint32_t fb = smem_u32(&full_bar[st]);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(stage_bytes)
-                         : "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(tx) : "memory");
             const uint32_t dst = smem_u32(smem + st * stage_bytes);
             const unsigned char* srcA = Aslab + item.a_off + (int64_t)ks * S * kSub;
             const unsigned char* srcB = Bslab + item.b_off + (int64_t)ks * S * kSub;
@@ -195,11 +248,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                 "l"(srcA), "r"(S * kSub), "r"(fb)
                 : "memory");
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    dst + S * kSub),
-                "l"(srcB), "r"(S * kSub), "r"(fb)
-                : "memory");
+            for (int jj = 0; jj < S; ++jj)
+              asm volatile(
+                  "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                      dst + S * kSub + jj * kSub),
+                  "l"(srcB + jj * kSub), "r"(bbytes), "r"(fb)
+                  : "memory");
             issued[st] = (int)use[st] + 1;
             use[st] += 1;
             st = (st + 1) % kStages;
@@ -222,17 +276,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       int st = 0;
-      uint32_t use[kStages] = {0, 0};
+      uint32_t use[kStages] = {0, 0, 0, 0};
       uint32_t chunk = 0;
       bool ok = true;
-      for (int j = blockIdx.x; j < njobs && ok; j += gridDim.x) {
+      for (int k = 0; ok; ++k) {
+        const int slot = k % kRing;
+        if (!mbar_wait(smem_u32(&jq_full[slot]), (k / kRing) & 1, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        const int j = job_ring[slot];
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&jq_empty[slot])) : "memory");
+        if (j < 0) break;
         const Job jb = jobs[j];
-        const int total = jb.nst;
-        int g = 0;
+        const uint32_t idesc = idesc_n(jb.nmma);
         for (int it = jb.i0; it < jb.i1 && ok; ++it) {
           const int nst = items[it].nst;
-          for (int ks = 0; ks < nst; ++ks, ++g) {
-            const int cpos = g % kChunkStages;
+          for (int ks = 0; ks < nst; ++ks) {
+            const int cpos = ks % kChunkStages;  // a chunk = up to kChunkStages stages of one item
             if (cpos == 0) {
               if (!mbar_wait(smem_u32(&acce_bar), (chunk & 1) ^ 1, &abort_flag)) {
                 ok = false;
@@ -250,19 +311,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int i = 0; i < S; ++i)
               for (int jj = 0; jj + i < S; ++jj) {
                 const int lvl = (i + jj) < 3 ? (i + jj) : 3;
-                // first MMA into each level in a chunk (pair (0, lvl)) resets it
-                const bool first_pair = (i == 0 && jj == lvl);
-#pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                  const uint32_t acc = (cpos == 0 && first_pair && kk == 0) ? 0u : 1u;
-                  mma_bf16(tmem + lvl * 128, make_desc(sa + i * kSub + kk * 256), make_desc(sb + jj * kSub + kk * 256),
-                           acc);
-                }
+                mma_bf16(tmem + lvl * 128, make_desc(sa + i * kSub), make_desc(sb + jj * kSub), idesc, 1u);
               }
             mma_commit(smem_u32(&empty_bar[st]));
             use[st] += 1;
             st = (st + 1) % kStages;
-            if (cpos == kChunkStages - 1 || g == total - 1) {
+            if (cpos == kChunkStages - 1 || ks == nst - 1) {
               mma_commit(smem_u32(&accf_bar));
               chunk += 1;
             }
@@ -287,55 +341,75 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
     uint32_t chunk = 0;
     bool ok = true;
-    for (int j = blockIdx.x; j < njobs && ok; j += gridDim.x) {
+    for (int k = 0; ok; ++k) {
+      const int slot = k % kRing;
+      if (!mbar_wait(smem_u32(&jq_full[slot]), (k / kRing) & 1, &abort_flag)) {
+        ok = false;
+        break;
+      }
+      const int j = job_ring[slot];
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&jq_empty[slot])) : "memory");
+      if (j < 0) break;
       const Job jb = jobs[j];
-      const int total = jb.nst;
-      const int nchunks = (total + kChunkStages - 1) / kChunkStages;
       float hi[32], lo[32];
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
         hi[c] = 0.f;
         lo[c] = 0.f;
       }
-      for (int ch = 0; ch < nchunks; ++ch) {
-        if (!mbar_wait(smem_u32(&accf_bar), chunk & 1, &abort_flag)) {
-          ok = false;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll
-        for (int cg = 0; cg < 4; ++cg) {
-          const uint32_t col = cgrp * 32 + cg * 8;
-          float x0[8], x1[8], x2[8], x3[8];
-          tmem_ld8(lane_addr + col, x0);
-          if (nlev > 1) tmem_ld8(lane_addr + 128 + col, x1);
-          if (nlev > 2) tmem_ld8(lane_addr + 256 + col, x2);
-          if (nlev > 3) tmem_ld8(lane_addr + 384 + col, x3);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const float a1 = nlev > 1 ? x1[c] : 0.f;
-            const float a2 = nlev > 2 ? x2[c] : 0.f;
-            const float a3 = nlev > 3 ? x3[c] : 0.f;
-            float s, e, h, e2;
-            two_sum(x0[c], a1, s, e);
-            two_sum(hi[cg * 8 + c], s, h, e2);
-            const float l = lo[cg * 8 + c] + (e2 + (e + (a2 + a3)));
-            const float hs = h + l;
-            lo[cg * 8 + c] = l - (hs - h);
-            hi[cg * 8 + c] = hs;
+      const int ncg = min(4, max(0, (jb.nmma - cgrp * 32 + 7) / 8));
+      const int c0 = jb.tc * kRows + cgrp * 32;
+      for (int it = jb.i0; it < jb.i1 && ok; ++it) {
+        const Item item = items[it];
+        const float* scl = (MODE == MODE_F && item.sc_off >= 0) ? ts.scale + item.sc_off : nullptr;
+        const int nch = (item.nst + kChunkStages - 1) / kChunkStages;
+        for (int ch = 0; ch < nch; ++ch) {
+          if (!mbar_wait(smem_u32(&accf_bar), chunk & 1, &abort_flag)) {
+            ok = false;
+            break;
           }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+          for (int cg = 0; cg < 4; ++cg) {
+            if (cg >= ncg) break;
+            const uint32_t col = cgrp * 32 + cg * 8;
+            float x0[8], x1[8], x2[8], x3[8];
+            tmem_ld8(lane_addr + col, x0);
+            tmem_ld8(lane_addr + 128 + col, x1);
+            tmem_ld8(lane_addr + 256 + col, x2);
+            tmem_ld8(lane_addr + 384 + col, x3);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            tmem_zero8(lane_addr + col);
+            tmem_zero8(lane_addr + 128 + col);
+            tmem_zero8(lane_addr + 256 + col);
+            tmem_zero8(lane_addr + 384 + col);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              float f = 1.f;
+              if (scl) {
+                const int cc = c0 + cg * 8 + c;
+                f = cc < jb.cols ? scl[cc] : 0.f;
+              }
+              float s, e, h, e2;
+              two_sum(x0[c] * f, x1[c] * f, s, e);
+              two_sum(hi[cg * 8 + c], s, h, e2);
+              const float l = lo[cg * 8 + c] + (e2 + (e + (x2[c] * f + x3[c] * f)));
+              const float hs = h + l;
+              lo[cg * 8 + c] = l - (hs - h);
+              hi[cg * 8 + c] = hs;
+            }
+          }
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar)) : "memory");
+          chunk += 1;
         }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar)) : "memory");
-        chunk += 1;
       }
       if (!ok) break;
       // epilogue: scale by 2^(rexp + cexp - shift) and write
       const int r = jb.tr * kRows + row;
       if (r < jb.rows) {
         const int er = rexp[jb.rsc + r];
-        const int c0 = jb.tc * kRows + cgrp * 32;
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
           int ce[8];

@@ -45,7 +45,7 @@ struct Chunk {
 };
 
 // CUDA-event profiling of the hot-path launches
-constexpr int kProfKinds = 5;
+constexpr int kProfKinds = 6;  // kind 5 counts every hot-path kernel launch
 struct Profiler {
   bool on = false;
   struct Pending { int kind; cudaEvent_t a, b; double flops; };
@@ -61,6 +61,7 @@ struct Profiler {
     return e;
   }
   // returns the pending slot; call end() after the launch
+  void count(int n) { launches[5] += n; }
   int begin(cudaStream_t s, int kind, double fl) {
     if (!on) return -1;
     Pending p{kind, get(), get(), fl};

@@ -60,6 +60,8 @@ CONFIGS = {
     "qc32": Config("qc32", SPATIAL_ORBITAL, 32, 32, 0, 2048, 1003),
     "qc48": Config("qc48", SPATIAL_ORBITAL, 48, 48, 0, 4096, 1004),
     "qc64": Config("qc64", SPATIAL_ORBITAL, 64, 64, 0, 6144, 1005),
+    # profiling case: the sector-dimension mix of qc32 at a few GB of device memory
+    "qc20p": Config("qc20p", SPATIAL_ORBITAL, 20, 20, 0, 1536, 1007),
 }
 
 

@@ -196,3 +196,43 @@ def test_device_generated_operators_bit_identical(ctx):
             assert np.array_equal(a, M)
             n += 1
     assert n > 100
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "split"])
+def test_davidson_graph_replay_matches_eager(ctx, prec_name):
+    """One Davidson iteration captured as a CUDA graph (H.psi included) and
+    replayed gives the same iterates as the eager step."""
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    prec = P.SU2_FP64 if prec_name == "fp64" else P.SU2_SPLIT_BF16
+    cfg = SMALL[5]
+    sec, env = workload.build(ctx, cfg, prepare_split=True)
+    psi0 = torch.from_numpy(synth.gaussian_psi(sec.psi_len, synth.psi_seed(cfg))).cuda()
+    runs = {}
+    for graph in (False, True):
+        dav = P.Davidson(ctx, env, psi0, tol=1e-9, max_sub=8, prec=prec, use_graph=graph)
+        hist = []
+        for _ in range(40):
+            th, r = dav.step()
+            hist.append((th, r))
+            if r <= 1e-9:
+                break
+        runs[graph] = hist
+    a, b = runs[False], runs[True]
+    assert len(a) == len(b)
+    for (t1, r1), (t2, r2) in zip(a, b):
+        assert abs(t1 - t2) <= 1e-12 * max(1.0, abs(t1))
+        assert abs(r1 - r2) <= 1e-9 * max(1.0, r1) + 1e-14
+    assert a[-1][1] <= 1e-9
+
+
+def test_davidson_graph_heisenberg_exact(ctx):
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    cfg = synth.CONFIGS["heis12"]
+    sec, env = workload.build(ctx, cfg)
+    psi0 = torch.from_numpy(synth.gaussian_psi(sec.psi_len, synth.psi_seed(cfg))).cuda()
+    dav = P.Davidson(ctx, env, psi0, tol=1e-10, use_graph=True)
+    th, res, it, ok = dav.solve()
+    assert ok
+    assert abs(th - oed.heisenberg_levels(12, 0)[0]) < 1e-10

@@ -71,7 +71,7 @@ def test_split_chunking_and_repeat(ctx):
     assert rel_err(a, H) <= TOL_SPLIT
 
 
-@pytest.mark.parametrize("S,tol", [(3, 1e-5), (4, 1e-7), (5, 1e-9), (6, 1e-10)])
+@pytest.mark.parametrize("S,tol", [(3, 1e-5), (4, 1e-7), (5, 1e-10), (6, 1e-11)])
 def test_slice_count_controls_error(ctx, S, tol):
     import paper_2309_16724_gb300 as P
     from paper_2309_16724_gb300 import workload
