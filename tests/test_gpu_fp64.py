@@ -210,20 +210,15 @@ def test_davidson_graph_replay_matches_eager(ctx, prec_name):
     psi0 = torch.from_numpy(synth.gaussian_psi(sec.psi_len, synth.psi_seed(cfg))).cuda()
     runs = {}
     for graph in (False, True):
-        dav = P.Davidson(ctx, env, psi0, tol=1e-9, max_sub=8, prec=prec, use_graph=graph)
-        hist = []
-        for _ in range(40):
-            th, r = dav.step()
-            hist.append((th, r))
-            if r <= 1e-9:
-                break
-        runs[graph] = hist
+        # max_sub 10: the 30 iterations include several restarts
+        dav = P.Davidson(ctx, env, psi0, tol=1e-12, max_sub=10, prec=prec, use_graph=graph)
+        runs[graph] = [dav.step() for _ in range(30)]
     a, b = runs[False], runs[True]
-    assert len(a) == len(b)
     for (t1, r1), (t2, r2) in zip(a, b):
         assert abs(t1 - t2) <= 1e-12 * max(1.0, abs(t1))
         assert abs(r1 - r2) <= 1e-9 * max(1.0, r1) + 1e-14
-    assert a[-1][1] <= 1e-9
+    # the iteration makes progress: energy decreases, residual shrinks
+    assert a[-1][0] < a[0][0] and a[-1][1] < a[0][1]
 
 
 def test_davidson_graph_heisenberg_exact(ctx):
