@@ -167,6 +167,25 @@ int su2_apply_heff(su2_ctx* ctx, const su2_env* env, const double* psi_in_dev,
 /* Same with host buffers: copies psi in, runs, copies F out, synchronises. */
 int su2_apply_heff_host(su2_ctx* ctx, const su2_env* env, const double* psi_in_host,
                         double* psi_out_host, int32_t prec);
+/* H.psi for callers that cannot allocate device memory while they run (a
+ * memory pool or arena that owns the device, real-time loops where an
+ * allocation could stall or fail).  The paper has no counterpart; this is
+ * a deployment variant of the native-FP64 su2_apply_heff.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine: the intermediate
+ * T = E D^T of each term chunk lives in a fixed 64 MiB device array that
+ * every GPU loading the library holds until the process exits.  The caller
+ * passes psi_in / psi_out (device, 8-byte aligned, psi_len doubles, not
+ * overlapping) and an environment built on the same context; an
+ * environment whose largest term chunk needs more than 64 MiB of T is
+ * rejected with SU2_EINVAL (build it with t_budget_bytes <= 64 MiB).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device); make that first call before any
+ * stream capture.  All calls share the one array: calls that overlap on the
+ * GPU (other streams, other threads) race on it; calls ordered on one stream
+ * are safe.  The array keeps the last call's contents; nothing in it has to
+ * start at zero (every element of T that is read is written first). */
+int su2_apply_heff_static_scratch(su2_ctx* ctx, const su2_env* env, const double* psi_in_dev,
+                                  double* psi_out_dev);
 /* Diagonal of H_eff (Davidson preconditioner) into a device buffer. */
 int su2_diag_heff(su2_ctx* ctx, const su2_env* env, double* diag_dev);
 

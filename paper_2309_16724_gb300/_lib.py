@@ -22,7 +22,7 @@ SU2_MODEL_HEISENBERG, SU2_MODEL_QC_SKELETON, SU2_MODEL_CASIMIR_S2, SU2_MODEL_CAS
 SYMBOLS = [
     "su2_ctx_create", "su2_ctx_destroy", "su2_last_error", "su2_ctx_status", "su2_build_sectors", "su2_sectors_query",
     "su2_sectors_destroy", "su2_build_environment", "su2_env_query", "su2_env_tasks", "su2_env_operator_block", "su2_env_destroy",
-    "su2_apply_heff", "su2_apply_heff_host", "su2_diag_heff", "su2_davidson_create", "su2_davidson_step",
+    "su2_apply_heff", "su2_apply_heff_host", "su2_apply_heff_static_scratch", "su2_diag_heff", "su2_davidson_create", "su2_davidson_step",
     "su2_davidson_solve", "su2_energy", "su2_davidson_vector", "su2_davidson_destroy",
     "su2_profile_enable", "su2_profile_reset", "su2_profile_read",
 ]
@@ -93,6 +93,7 @@ def lib():
         L.su2_env_destroy.argtypes = [vp]
         L.su2_apply_heff.argtypes = [vp, vp, vp, vp, C.c_int32]
         L.su2_apply_heff_host.argtypes = [vp, vp, vp, vp, C.c_int32]
+        L.su2_apply_heff_static_scratch.argtypes = [vp, vp, vp, vp]
         L.su2_diag_heff.argtypes = [vp, vp, vp]
         L.su2_davidson_create.argtypes = [vp, vp, vp, C.POINTER(DavOpts), C.POINTER(vp)]
         L.su2_davidson_step.argtypes = [vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -280,6 +281,12 @@ def apply_heff(ctx: Context, env: Environment, psi_in, psi_out, prec=SU2_FP64):
 
 def apply_heff_host(ctx: Context, env: Environment, psi_in: np.ndarray, psi_out: np.ndarray, prec=SU2_FP64):
     ctx.check(lib().su2_apply_heff_host(ctx.h, env.h, _ptr(psi_in), _ptr(psi_out), prec))
+
+
+def apply_heff_static_scratch(ctx: Context, env: Environment, psi_in, psi_out):
+    """su2_apply_heff_static_scratch: FP64 H.psi that allocates nothing
+    (its intermediate lives in a fixed 64 MiB device array)."""
+    ctx.check(lib().su2_apply_heff_static_scratch(ctx.h, env.h, _ptr(psi_in), _ptr(psi_out)))
 
 
 def diag_heff(ctx: Context, env: Environment, diag_out):
