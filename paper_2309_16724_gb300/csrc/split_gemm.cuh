@@ -21,8 +21,8 @@
 // 2^-24-weighted tail.  A chunk is up to 128 K of one item; after it the
 // drain warps fold the four levels into a float-float register accumulator
 // (K2: scaled by the item's per-column factor, so every task keeps its own
-// S*8 bits) and zero TMEM; at the end of the job they write the tile (K1:
-// float-float T; K2: F += FP64).
+// S*8 bits); the first MMA of the next chunk into each level overwrites it.
+// At the end of the job they write the tile (K1: float-float T; K2: F += FP64).
 //
 // Warp roles (576 threads): warp 0 bulk-copy producer and job fetcher
 // (dynamic schedule: an atomic job counter, handed to the other roles through
@@ -95,6 +95,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
   return false;
 }
 
+// bounded wait by every lane of a warp, then a warp vote: the warp leaves
+// converged (the .sync.aligned TMEM loads that follow need that) and agrees
+// on success
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  const bool got = mbar_wait(bar, parity, abort_flag);
+  return __all_sync(0xffffffffu, got);
+}
+
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
   // no swizzle, K-major: LBO = 128 B (next core matrix along K), SBO = 256 B
   // (next 8-row group), descriptor version 1 (bit 46)
@@ -121,22 +129,23 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+// four 32x32b.x4 TMEM loads (one per accumulator level) and the wait in one
+// asm statement: tcgen05.ld writes its destination registers asynchronously,
+// so they must not exist as values in the program before tcgen05.wait::ld
+// (a separate wait statement would let the compiler reuse or read them early)
+__device__ __forceinline__ void tmem_ld4x4_wait(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                                float (&v)[16]) {
   uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%17];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8,%9,%10,%11}, [%18];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12,%13,%14,%15}, [%19];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3)
+      : "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
@@ -199,19 +208,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
   const int nlev = S < 4 ? S : 4;
-  // all accumulators start at zero; the drain zeroes them again after reading,
-  // so every MMA accumulates (levels need no per-chunk reset)
-  if (warp >= 2) {
-    const uint32_t la = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    const int cg = (warp - 2) >> 2;
-    for (int lv = 0; lv < 4; ++lv)
-      for (int c8 = 0; c8 < 4; ++c8) tmem_zero8(la + lv * 128 + cg * 32 + c8 * 8);
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
@@ -311,7 +307,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int i = 0; i < S; ++i)
               for (int jj = 0; jj + i < S; ++jj) {
                 const int lvl = (i + jj) < 3 ? (i + jj) : 3;
-                mma_bf16(tmem + lvl * 128, make_desc(sa + i * kSub), make_desc(sb + jj * kSub), idesc, 1u);
+                // the first MMA into each level in a chunk (pair (0, lvl)) overwrites it
+                const uint32_t acc = (cpos == 0 && i == 0 && jj == lvl) ? 0u : 1u;
+                mma_bf16(tmem + lvl * 128, make_desc(sa + i * kSub), make_desc(sb + jj * kSub), idesc, acc);
               }
             mma_commit(smem_u32(&empty_bar[st]));
             use[st] += 1;
@@ -343,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int k = 0; ok; ++k) {
       const int slot = k % kRing;
-      if (!mbar_wait(smem_u32(&jq_full[slot]), (k / kRing) & 1, &abort_flag)) {
+      if (!warp_wait(smem_u32(&jq_full[slot]), (k / kRing) & 1, &abort_flag)) {
         ok = false;
         break;
       }
@@ -357,49 +355,52 @@ __global__ void __launch_bounds__(kThreads, 1)
         hi[c] = 0.f;
         lo[c] = 0.f;
       }
-      const int ncg = min(4, max(0, (jb.nmma - cgrp * 32 + 7) / 8));
+      const int ncg4 = min(8, max(0, (jb.nmma - cgrp * 32 + 3) / 4));
       const int c0 = jb.tc * kRows + cgrp * 32;
       for (int it = jb.i0; it < jb.i1 && ok; ++it) {
         const Item item = items[it];
         const float* scl = (MODE == MODE_F && item.sc_off >= 0) ? ts.scale + item.sc_off : nullptr;
         const int nch = (item.nst + kChunkStages - 1) / kChunkStages;
         for (int ch = 0; ch < nch; ++ch) {
-          if (!mbar_wait(smem_u32(&accf_bar), chunk & 1, &abort_flag)) {
+          if (!warp_wait(smem_u32(&accf_bar), chunk & 1, &abort_flag)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-          for (int cg = 0; cg < 4; ++cg) {
-            if (cg >= ncg) break;
-            const uint32_t col = cgrp * 32 + cg * 8;
-            float x0[8], x1[8], x2[8], x3[8];
-            tmem_ld8(lane_addr + col, x0);
-            tmem_ld8(lane_addr + 128 + col, x1);
-            tmem_ld8(lane_addr + 256 + col, x2);
-            tmem_ld8(lane_addr + 384 + col, x3);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            tmem_zero8(lane_addr + col);
-            tmem_zero8(lane_addr + 128 + col);
-            tmem_zero8(lane_addr + 256 + col);
-            tmem_zero8(lane_addr + 384 + col);
+          for (int cg = 0; cg < 8; ++cg) {
+            if (cg >= ncg4) break;
+            const uint32_t col = cgrp * 32 + cg * 4;
+            float xx[16];  // levels 0..3, four columns each
+            tmem_ld4x4_wait(lane_addr + col, lane_addr + 128 + col, lane_addr + 256 + col, lane_addr + 384 + col,
+                            xx);
+            float x0[4], x1[4], x2[4], x3[4];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
+            for (int c = 0; c < 4; ++c) {
+              x0[c] = xx[c];
+              x1[c] = xx[4 + c];
+              x2[c] = xx[8 + c];
+              x3[c] = xx[12 + c];
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const float y1 = nlev > 1 ? x1[c] : 0.f;
+              const float y2 = nlev > 2 ? x2[c] : 0.f;
+              const float y3 = nlev > 3 ? x3[c] : 0.f;
               float f = 1.f;
               if (scl) {
-                const int cc = c0 + cg * 8 + c;
+                const int cc = c0 + cg * 4 + c;
                 f = cc < jb.cols ? scl[cc] : 0.f;
               }
               float s, e, h, e2;
-              two_sum(x0[c] * f, x1[c] * f, s, e);
-              two_sum(hi[cg * 8 + c], s, h, e2);
-              const float l = lo[cg * 8 + c] + (e2 + (e + (x2[c] * f + x3[c] * f)));
+              two_sum(x0[c] * f, y1 * f, s, e);
+              two_sum(hi[cg * 4 + c], s, h, e2);
+              const float l = lo[cg * 4 + c] + (e2 + (e + (y2 * f + y3 * f)));
               const float hs = h + l;
-              lo[cg * 8 + c] = l - (hs - h);
-              hi[cg * 8 + c] = hs;
+              lo[cg * 4 + c] = l - (hs - h);
+              hi[cg * 4 + c] = hs;
             }
           }
-          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           asm volatile("tcgen05.fence::before_thread_sync;");
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar)) : "memory");
           chunk += 1;
