@@ -432,6 +432,18 @@ int exp_host(double x) {
   return e;
 }
 
+// the stripe GEMM instantiated for each mode and slice count
+using GemmFn = void (*)(const sp::Job*, int, const sp::Item*, const unsigned char*, const unsigned char*, const int*,
+                        const int*, int, float*, float*, double*, int*, int*, sp::TaskScale);
+GemmFn gemm_fn(int mode, int S) {
+  static const GemmFn t[2][sp::kMaxS - 1] = {
+      {sp::split_gemm_kernel<sp::MODE_T, 2>, sp::split_gemm_kernel<sp::MODE_T, 3>, sp::split_gemm_kernel<sp::MODE_T, 4>,
+       sp::split_gemm_kernel<sp::MODE_T, 5>, sp::split_gemm_kernel<sp::MODE_T, 6>},
+      {sp::split_gemm_kernel<sp::MODE_F, 2>, sp::split_gemm_kernel<sp::MODE_F, 3>, sp::split_gemm_kernel<sp::MODE_F, 4>,
+       sp::split_gemm_kernel<sp::MODE_F, 5>, sp::split_gemm_kernel<sp::MODE_F, 6>}};
+  return t[mode == sp::MODE_F ? 1 : 0][S - 2];
+}
+
 void launch_gemm(int mode, cudaStream_t s, SplitState* st, const Job* jobs, int njobs, const Item* items,
                  const unsigned char* A, const unsigned char* B, const int* rexp, const int* cexp, float* Th,
                  float* Tl, double* F, sp::TaskScale ts) {
@@ -439,12 +451,8 @@ void launch_gemm(int mode, cudaStream_t s, SplitState* st, const Job* jobs, int 
   const int smem = sp::kStages * (2 * st->S * kSub) + 1024;
   const int grid = std::min(njobs, st->n_sms);
   cudaMemsetAsync(st->d_counter, 0, sizeof(int), s);
-  if (mode == sp::MODE_T)
-    sp::split_gemm_kernel<sp::MODE_T><<<grid, sp::kThreads, smem, s>>>(jobs, njobs, items, A, B, rexp, cexp, 16,
-                                                                       st->S, Th, Tl, F, st->d_status, st->d_counter, ts);
-  else
-    sp::split_gemm_kernel<sp::MODE_F><<<grid, sp::kThreads, smem, s>>>(jobs, njobs, items, A, B, rexp, cexp, 16,
-                                                                       st->S, Th, Tl, F, st->d_status, st->d_counter, ts);
+  gemm_fn(mode, st->S)<<<grid, sp::kThreads, smem, s>>>(jobs, njobs, items, A, B, rexp, cexp, 16, Th, Tl, F,
+                                                        st->d_status, st->d_counter, ts);
 }
 
 }  // namespace
@@ -462,9 +470,9 @@ int split_prepare(su2_env* env, int S, std::string& err) {
   cudaGetDeviceProperties(&prop, env->ctx->device);
   st->n_sms = prop.multiProcessorCount;
   const int smem = sp::kStages * (2 * S * kSub) + 1024;
-  if (cudaFuncSetAttribute(sp::split_gemm_kernel<sp::MODE_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+  if (cudaFuncSetAttribute((const void*)gemm_fn(sp::MODE_T, S), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(sp::split_gemm_kernel<sp::MODE_F>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+      cudaFuncSetAttribute((const void*)gemm_fn(sp::MODE_F, S), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
           cudaSuccess) {
     err = "cannot set the shared-memory size of the split GEMM";
     return SU2_ECUDA;

@@ -119,10 +119,32 @@ __device__ __forceinline__ uint32_t idesc_n(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t(n) >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+// D (+)= A * B^T; ACC = false overwrites D
+template <bool ACC>
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc) {
+  if (ACC)
+    asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;" ::"r"(tmem), "l"(a), "l"(b), "r"(idesc));
+  else
+    asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 0;" ::"r"(tmem), "l"(a), "l"(b), "r"(idesc));
+}
+
+// the S(S+1)/2 slice products of one 16-K stage, unrolled: pair (i, j) goes to
+// level min(i + j, 3); da / db describe slice 0 of A / B, slice i sits kSub
+// bytes further (the descriptor's address field counts 16-byte units).  In the
+// first stage of a chunk the first product into each level, (0, level),
+// overwrites it.
+template <int S, bool FIRST>
+__device__ __forceinline__ void issue_stage(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc) {
+#pragma unroll
+  for (int i = 0; i < S; ++i)
+#pragma unroll
+    for (int jj = 0; jj < S - i; ++jj) {
+      const int lvl = (i + jj) < 3 ? (i + jj) : 3;
+      const uint64_t a = da + (uint64_t)(i * (kSub >> 4));
+      const uint64_t b = db + (uint64_t)(jj * (kSub >> 4));
+      if (FIRST && i == 0 && jj == lvl) mma_bf16<false>(tmem + lvl * kRows, a, b, idesc);
+      else mma_bf16<true>(tmem + lvl * kRows, a, b, idesc);
+    }
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -165,16 +187,16 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // x * 2^k for float, exact while the result stays normal
 __device__ __forceinline__ float ldexp_f(float x, int k) { return ldexpf(x, k); }
 
-template <int MODE>
+template <int MODE, int S>
 __global__ void __launch_bounds__(kThreads, 1)
     split_gemm_kernel(const Job* __restrict__ jobs, int njobs, const Item* __restrict__ items,
                       const unsigned char* __restrict__ Aslab, const unsigned char* __restrict__ Bslab,
-                      const int* __restrict__ rexp, const int* __restrict__ cexp, int shift, int S,
+                      const int* __restrict__ rexp, const int* __restrict__ cexp, int shift,
                       float* __restrict__ Th, float* __restrict__ Tl, double* __restrict__ F, int* __restrict__ status,
                       int* __restrict__ job_counter, TaskScale ts) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int stage_bytes = 2 * S * kSub;
+  constexpr int stage_bytes = 2 * S * kSub;
   __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], accf_bar, acce_bar, done_bar;
   __shared__ __align__(8) uint64_t jq_full[kRing], jq_empty[kRing];
   __shared__ int job_ring[kRing];
@@ -303,14 +325,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t sa = smem_u32(smem + st * stage_bytes);
-            const uint32_t sb = sa + S * kSub;
-            for (int i = 0; i < S; ++i)
-              for (int jj = 0; jj + i < S; ++jj) {
-                const int lvl = (i + jj) < 3 ? (i + jj) : 3;
-                // the first MMA into each level in a chunk (pair (0, lvl)) overwrites it
-                const uint32_t acc = (cpos == 0 && i == 0 && jj == lvl) ? 0u : 1u;
-                mma_bf16(tmem + lvl * 128, make_desc(sa + i * kSub), make_desc(sb + jj * kSub), idesc, acc);
-              }
+            const uint64_t da = make_desc(sa), db = make_desc(sa + S * kSub);
+            if (cpos == 0) issue_stage<S, true>(tmem, da, db, idesc);
+            else issue_stage<S, false>(tmem, da, db, idesc);
             mma_commit(smem_u32(&empty_bar[st]));
             use[st] += 1;
             st = (st + 1) % kStages;
