@@ -101,12 +101,11 @@ struct SplitState {
   TPUnit* d_tpu = nullptr;
   int* d_status = nullptr;
   int* d_counter = nullptr;
-  int *d_phi = nullptr, *d_tsrc = nullptr, *d_off = nullptr;  // per TP task: phi_t, source cexp offset, (unused)
-  float* d_scale = nullptr;      // per (task, column) drain factors of one chunk
+  int* d_phi = nullptr;          // per TP task: phi_t
+  int8_t* d_scale = nullptr;     // per (task, column) drain exponents of one chunk
   int64_t* d_scoff = nullptr;    // per TP task: offset into d_scale (chunk-local)
   std::vector<int64_t> scoff;
   int64_t n_scale = 0;
-  std::vector<int> tsrc;
   int n_sms = 148;
 };
 
@@ -201,7 +200,7 @@ __global__ void slab_fp64_kernel(const SlabDesc* __restrict__ descs, const Unit*
         if (d.src_off < 0) x = (r == k) ? 1.0 : 0.0;
         else x = src[d.src_off + r + int64_t(k) * d.ld];
       }
-      y[q] = ldexp(x, 8 - sigma);  // |y| < 2^8
+      y[q] = ldexp(x, sp::kLead - sigma);  // |y| < 2^kLead
     }
     for (int i = 0; i < S; ++i) {
       __align__(16) __nv_bfloat16 v[8];
@@ -274,51 +273,29 @@ __global__ void gamma_kernel(const TPTask* __restrict__ tasks, const Source* __r
   }
 }
 
-// T' slab: rows = columns of the source, K = rows of the source
-// per-(task, column) drain factors 2^(phi_t + cexp(c) - gamma(c)) (0 for empty columns)
+// per-(task, column) drain exponents d = phi_t + cexp(c) - gamma(c) <= 0 (the
+// factor is 2^d); -127 (factor 0) for empty columns, for d below -126 and for
+// the padding up to the next multiple of 128 columns
 __global__ void scale_kernel(const TPTask* __restrict__ tasks, const Source* __restrict__ src,
                              const int* __restrict__ cexp, const int* __restrict__ gamma,
-                             const int* __restrict__ phi, const int64_t* __restrict__ sc_off, float* __restrict__ scale) {
+                             const int* __restrict__ phi, const int64_t* __restrict__ sc_off, int8_t* __restrict__ scale) {
   const TPTask t = tasks[blockIdx.x];
   const Source s = src[t.src];
   const int ph = phi[blockIdx.x];
-  float* out = scale + sc_off[blockIdx.x];
-  for (int c = threadIdx.x; c < s.cols; c += blockDim.x) {
-    const int ce = cexp[s.cexp_off + c];
-    float f = 0.f;
-    if (ph > -1000 && ce > -1000) {
-      const int d = ph + ce - gamma[t.gcol + c];  // <= 0
-      f = d < -126 ? 0.f : __int_as_float((127 + d) << 23);
-    }
-    out[c] = f;
-  }
-}
-
-// slice offset of each task: o_t = floor(min_c (gamma(c) - phi_t - cexp(c)) / 8), in [0, 3]
-__global__ void offset_kernel(const TPTask* __restrict__ tasks, const Source* __restrict__ src,
-                              const int* __restrict__ cexp, const int* __restrict__ gamma,
-                              const int* __restrict__ phi, int* __restrict__ off) {
-  __shared__ int red[32];
-  const TPTask t = tasks[blockIdx.x];
-  const Source s = src[t.src];
-  const int ph = phi[blockIdx.x];
-  int m = 1 << 30;
-  if (ph > -1000)
-    for (int c = threadIdx.x; c < s.cols; c += blockDim.x) {
+  int8_t* out = scale + sc_off[blockIdx.x];
+  const int padded = (s.cols + 127) & ~127;
+  for (int c = threadIdx.x; c < padded; c += blockDim.x) {
+    int d = -127;
+    if (c < s.cols && ph > -1000) {
       const int ce = cexp[s.cexp_off + c];
-      if (ce < -1000) continue;
-      m = min(m, gamma[t.gcol + c] - (ph + ce));
+      if (ce > -1000) d = max(-127, ph + ce - gamma[t.gcol + c]);
     }
-  for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < int(blockDim.x >> 5); ++w) m = min(m, red[w]);
-    m = min(red[0], m);
-    off[blockIdx.x] = m >= (1 << 29) ? 3 : min(3, max(0, m / 8));
+    out[c] = (int8_t)d;
   }
 }
 
+// T' slab of one task: rows = columns of its source (the output columns),
+// K = rows of the source, cut relative to the task's own column exponents
 __global__ void slab_tprime_kernel(const TPTask* __restrict__ tasks, const TPUnit* __restrict__ units,
                                    const Source* __restrict__ src, const float* __restrict__ Th,
                                    const float* __restrict__ Tl, const float* __restrict__ Ph,
@@ -359,9 +336,9 @@ __global__ void slab_tprime_kernel(const TPTask* __restrict__ tasks, const TPUni
       float e = fmaf(a, vh, -p);
       e = fmaf(a, vl, e);
       e = fmaf(b, vh, e);
-      // scale to |x| < 2^8 (exact power of two)
-      ph[q] = ldexpf(p, 8 - sc);
-      pl[q] = ldexpf(e, 8 - sc);
+      // scale to |x| < 2^kLead (exact power of two)
+      ph[q] = ldexpf(p, sp::kLead - sc);
+      pl[q] = ldexpf(e, sp::kLead - sc);
       const float hs = ph[q] + pl[q];
       pl[q] = pl[q] - (hs - ph[q]);
       ph[q] = hs;
@@ -451,7 +428,7 @@ void launch_gemm(int mode, cudaStream_t s, SplitState* st, const Job* jobs, int 
   const int smem = sp::kStages * (2 * st->S * kSub) + 1024;
   const int grid = std::min(njobs, st->n_sms);
   cudaMemsetAsync(st->d_counter, 0, sizeof(int), s);
-  gemm_fn(mode, st->S)<<<grid, sp::kThreads, smem, s>>>(jobs, njobs, items, A, B, rexp, cexp, 16, Th, Tl, F,
+  gemm_fn(mode, st->S)<<<grid, sp::kThreads, smem, s>>>(jobs, njobs, items, A, B, rexp, cexp, 2 * sp::kLead, Th, Tl, F,
                                                         st->d_status, st->d_counter, ts);
 }
 
@@ -666,10 +643,9 @@ int split_prepare(su2_env* env, int S, std::string& err) {
         const int task_id = int(st->tpt.size() - ch.tp0);
         tid[q] = task_id;
         st->tpt.push_back(TPTask{s, int32_t(goff[f]), aid[q], 0, t.v, tpsz});
-        st->tsrc.push_back(st->src[ch.src0 + s].cexp_off);
         sco[q] = scsz;
         st->scoff.push_back(scsz);
-        scsz += Fb.cols;
+        scsz += (Fb.cols + 127) & ~127;  // whole 128-column tiles (16-byte aligned drain loads)
         for (int tr = 0; tr < (Fb.cols + 127) / 128; ++tr)
           for (int ks = 0; ks < kst[q]; ++ks) st->tpu.push_back(TPUnit{task_id, tr, ks, 0});
         tpsz += slab_bytes(Fb.cols, E.rows, S);
@@ -746,9 +722,7 @@ int split_prepare(su2_env* env, int S, std::string& err) {
   if (!rc2) rc2 = dput(&st->d_src, st->src, err);
   if (!rc2) rc2 = dput(&st->d_tpt, st->tpt, err);
   if (!rc2) rc2 = dput(&st->d_tpu, st->tpu, err);
-  if (!rc2) rc2 = dput(&st->d_tsrc, st->tsrc, err);
   if (!rc2) rc2 = dalloc(&st->d_phi, std::max<size_t>(st->tpt.size(), 1), err);
-  if (!rc2) rc2 = dalloc(&st->d_off, std::max<size_t>(st->tpt.size(), 1), err);
   if (!rc2) rc2 = dalloc(&st->d_scale, size_t(std::max<int64_t>(st->n_scale, 1)), err);
   if (!rc2) rc2 = dput(&st->d_scoff, st->scoff, err);
   if (rc2) return rc2;
@@ -869,7 +843,7 @@ void split_free(su2_env* env) {
   void* ps[] = {st->dA, st->dD, st->dE, st->dTP, st->d_adesc, st->d_ddesc, st->d_edesc, st->d_aunit, st->d_dunit,
                 st->d_eunit, st->d_rho, st->d_aown, st->d_delta, st->d_zeta, st->d_eps, st->d_gamma, st->d_cexp,
                 st->dTh, st->dTl, st->dPh, st->dPl, st->d_k1j, st->d_k2j, st->d_k1i, st->d_k2i, st->d_src,
-                st->d_tpt, st->d_tpu, st->d_colbase, st->d_counter, st->d_phi, st->d_tsrc, st->d_off,
+                st->d_tpt, st->d_tpu, st->d_colbase, st->d_counter, st->d_phi,
                 st->d_scale, st->d_scoff};
   for (void* p : ps) cudaFree(p);
   delete st;

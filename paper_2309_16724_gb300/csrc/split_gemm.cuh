@@ -6,7 +6,7 @@
 // (mi, ki) at (mi*2 + ki)*128 bytes, row r%8 at 16*(r%8)); for each
 // (row tile, K stage) the S slices follow each other (S*4 KB, one bulk
 // copy).  Slice i holds q_i * 2^-8i where q_i are the integers peeled from
-// x * 2^(8 - sigma_row), |q_i| <= 257.
+// x * 2^(8 - sigma_row) (|x| < 2^sigma_row): |q_0| <= 256, |q_i| <= 128.
 //
 // One job = one 128 x 128 output tile and a list of items (A slab, B slab,
 // K stages); all items of a job share the row and column scales, so the
@@ -14,11 +14,12 @@
 // without a separate reduction (the stripe product of Sec. III.A).  Slice
 // pairs (i, j), i + j < S, go to four FP32 TMEM accumulators (512 columns)
 // by level l = min(i + j, 3).  Levels 0, 1 and 2 hold integer multiples of
-// their unit 2^-8l below 2^24 for K chunks of 128, hence are exact whatever
+// their unit 2^-8l below 2^24 for K chunks of 192 (level 2 grows by at most
+// 2*256*128 + 128^2 = 2^16.3 per K, 192 K give 2^23.9), hence are exact whatever
 // rounding the tensor core applies when it adds into the accumulator
 // (it truncates: a shared tail accumulator of many pairs would collect a
 // biased error of order #adds * 2^-23 of its size); level 3 carries the
-// 2^-24-weighted tail.  A chunk is up to 128 K of one item; after it the
+// 2^-24-weighted tail.  A chunk is up to 192 K of one item; after it the
 // drain warps fold the four levels into a float-float register accumulator
 // (K2: scaled by the item's per-column factor, so every task keeps its own
 // S*8 bits); the first MMA of the next chunk into each level overwrites it.
@@ -44,7 +45,8 @@ constexpr int kKS = 16;              // K per pipeline stage (one MMA K step)
 constexpr int kSub = kRows * kKS * 2;  // bytes of one 128 x 16 BF16 sub-tile
 constexpr int kMaxS = 6;
 constexpr int kStages = 4;
-constexpr int kChunkStages = 8;      // 128 K per exact drain
+constexpr int kLead = 8;             // leading slice |q_0| <= 2^kLead, the others |q_i| <= 128
+constexpr int kChunkStages = 12;     // 192 K per exact drain
 constexpr int kRing = 4;             // job ring slots
 constexpr int kThreads = 576;      // producer + MMA + 16 drain warps
 constexpr long kSpinLimit = 1L << 26;
@@ -53,13 +55,15 @@ struct Item {
   int64_t a_off, b_off;  // byte offsets of the first (row tile, K stage) group
   int32_t nst;           // K stages of 16
   int32_t pad;
-  int64_t sc_off;        // MODE_F: offset of the item's per-column scale factors, -1 otherwise
+  int64_t sc_off;        // MODE_F: offset of the item's per-column drain exponents (a multiple of 128), -1 otherwise
 };
 // MODE_F: task t's B slab is cut relative to its own column exponents; the
-// drain multiplies each chunk of t by scale[sc_off + col] = 2^(own - gamma(col))
-// (an exact power of two, <= 1) before adding it to the tile accumulator.
+// drain multiplies each chunk of t by 2^d, d = dexp[sc_off + col] =
+// own(col) - gamma(col) in [-126, 0], or -127 for a column that is zero (an
+// exact power of two, <= 1) before adding it to the tile accumulator.  The
+// per-task vector is padded to whole 128-column tiles.
 struct TaskScale {
-  const float* scale;
+  const int8_t* dexp;
 };
 struct Job {
   int64_t out_off;       // element offset of the output block
@@ -376,7 +380,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int c0 = jb.tc * kRows + cgrp * 32;
       for (int it = jb.i0; it < jb.i1 && ok; ++it) {
         const Item item = items[it];
-        const float* scl = (MODE == MODE_F && item.sc_off >= 0) ? ts.scale + item.sc_off : nullptr;
+        // MODE_F: this thread's 32 drain exponents of the item, fetched before
+        // the chunk wait (two 16-byte loads; byte k of word w = column 4w + k)
+        uint32_t dx[8];
+        if (MODE == MODE_F) {
+          const int4* p = reinterpret_cast<const int4*>(ts.dexp + item.sc_off + c0);
+          const int4 u0 = __ldg(p), u1 = __ldg(p + 1);
+          dx[0] = u0.x, dx[1] = u0.y, dx[2] = u0.z, dx[3] = u0.w;
+          dx[4] = u1.x, dx[5] = u1.y, dx[6] = u1.z, dx[7] = u1.w;
+        }
         const int nch = (item.nst + kChunkStages - 1) / kChunkStages;
         for (int ch = 0; ch < nch; ++ch) {
           if (!warp_wait(smem_u32(&accf_bar), chunk & 1, &abort_flag)) {
@@ -405,9 +417,9 @@ __global__ void __launch_bounds__(kThreads, 1)
               const float y2 = nlev > 2 ? x2[c] : 0.f;
               const float y3 = nlev > 3 ? x3[c] : 0.f;
               float f = 1.f;
-              if (scl) {
-                const int cc = c0 + cg * 4 + c;
-                f = cc < jb.cols ? scl[cc] : 0.f;
+              if (MODE == MODE_F) {
+                const int d = (int)(int8_t)(dx[cg] >> (8 * c));
+                f = __int_as_float((127 + d) << 23);  // 2^d; d = -127 gives 0
               }
               float s, e, h, e2;
               two_sum(x0[c] * f, y1 * f, s, e);
