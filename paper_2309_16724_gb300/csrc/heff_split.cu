@@ -396,10 +396,18 @@ void add_units(std::vector<Unit>& u, int desc, int rows, int cols) {
     for (int ks = 0; ks < (cols + sp::kKS - 1) / sp::kKS; ++ks) u.push_back(Unit{desc, tr, ks, 0});
 }
 
-// MMA N of column tile tc of a block with `cols` columns
+// MMA N of job column tile tc (kCols wide) of a block with `cols` columns
 int32_t nmma_of(int cols, int tc) {
-  const int rem = std::min(128, cols - tc * 128);
+  const int rem = std::min(sp::kCols, cols - tc * sp::kCols);
   return int32_t((rem + 15) / 16 * 16);
+}
+
+// byte offset of job column tile tc (kCols wide) inside a B slab whose row
+// tiles span 128 rows: its 128-row tile, plus the tile's first row inside it
+// (32 bytes per row in the core-matrix layout)
+int64_t btile_off(int tc, int kst, int S) {
+  const int c0 = tc * sp::kCols;
+  return int64_t(c0 / 128) * kst * S * kSub + (c0 % 128) * 32;
 }
 
 int exp_host(double x) {
@@ -425,7 +433,7 @@ void launch_gemm(int mode, cudaStream_t s, SplitState* st, const Job* jobs, int 
                  const unsigned char* A, const unsigned char* B, const int* rexp, const int* cexp, float* Th,
                  float* Tl, double* F, sp::TaskScale ts) {
   if (njobs <= 0) return;
-  const int smem = sp::kStages * (2 * st->S * kSub) + 1024;
+  const int smem = sp::smem_bytes_of(st->S);
   const int grid = std::min(njobs, st->n_sms);
   cudaMemsetAsync(st->d_counter, 0, sizeof(int), s);
   gemm_fn(mode, st->S)<<<grid, sp::kThreads, smem, s>>>(jobs, njobs, items, A, B, rexp, cexp, 2 * sp::kLead, Th, Tl, F,
@@ -446,7 +454,7 @@ int split_prepare(su2_env* env, int S, std::string& err) {
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, env->ctx->device);
   st->n_sms = prop.multiProcessorCount;
-  const int smem = sp::kStages * (2 * S * kSub) + 1024;
+  const int smem = sp::smem_bytes_of(S);
   if (cudaFuncSetAttribute((const void*)gemm_fn(sp::MODE_T, S), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
           cudaSuccess ||
       cudaFuncSetAttribute((const void*)gemm_fn(sp::MODE_F, S), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
@@ -600,11 +608,12 @@ int split_prepare(su2_env* env, int S, std::string& err) {
       csz += n;
       umap[key] = id;
       const int kst2 = (k2 + sp::kKS - 1) / sp::kKS;
-      for (int tc = 0; tc < (n + 127) / 128; ++tc)
-        for (int tr = 0; tr < (k1 + 127) / 128; ++tr) {
+      // the column tiles of one row tile are neighbouring jobs (they share the E tile)
+      for (int tr = 0; tr < (k1 + 127) / 128; ++tr)
+        for (int tc = 0; tc < (n + sp::kCols - 1) / sp::kCols; ++tc) {
           const int ii = int(st->k1i.size());
           st->k1i.push_back(Item{st->edesc[t.e].slab_off + int64_t(tr) * kst2 * S * kSub,
-                                 st->ddesc[t.dblk].slab_off + int64_t(tc) * kst2 * S * kSub, kst2, 0, -1});
+                                 st->ddesc[t.dblk].slab_off + btile_off(tc, kst2, S), kst2, 0, -1});
           k1jobs.push_back(Job{tsz, k1, n, k1, tr, tc, ii, ii + 1, int32_t(eps_off[t.e]),
                                int32_t(zeta_off[t.dblk]), kst2, nmma_of(n, tc), 0});
           k1cost.push_back(kst2);
@@ -651,13 +660,14 @@ int split_prepare(su2_env* env, int S, std::string& err) {
         tpsz += slab_bytes(Fb.cols, E.rows, S);
         if (t.ablk >= 0) ch.k2_flops += 2.0 * Fb.rows * E.rows * Fb.cols;
       }
-      for (int tc = 0; tc < (Fb.cols + 127) / 128; ++tc)
-        for (int tr = 0; tr < (Fb.rows + 127) / 128; ++tr) {
+      // the column tiles of one row tile are neighbouring jobs (they share the A tiles)
+      for (int tr = 0; tr < (Fb.rows + 127) / 128; ++tr)
+        for (int tc = 0; tc < (Fb.cols + sp::kCols - 1) / sp::kCols; ++tc) {
           const int i0 = int(st->k2i.size());
           int tot = 0;
           for (size_t q = 0; q < mine.size(); ++q) {
             st->k2i.push_back(Item{st->adesc[aid[q]].slab_off + int64_t(tr) * kst[q] * S * kSub,
-                                   tp[q] + int64_t(tc) * kst[q] * S * kSub, kst[q], 0, sco[q]});
+                                   tp[q] + btile_off(tc, kst[q], S), kst[q], 0, sco[q]});
             tot += kst[q];
           }
           k2jobs.push_back(Job{Fb.offset, Fb.rows, Fb.cols, Fb.rows, tr, tc, i0, int(st->k2i.size()),

@@ -8,12 +8,14 @@
 // copy).  Slice i holds q_i * 2^-8i where q_i are the integers peeled from
 // x * 2^(8 - sigma_row) (|x| < 2^sigma_row): |q_0| <= 256, |q_i| <= 128.
 //
-// One job = one 128 x 128 output tile and a list of items (A slab, B slab,
-// K stages); all items of a job share the row and column scales, so the
-// K-concatenated stripe sum_items A_item . B_item^T accumulates in TMEM
-// without a separate reduction (the stripe product of Sec. III.A).  Slice
-// pairs (i, j), i + j < S, go to four FP32 TMEM accumulators (512 columns)
-// by level l = min(i + j, 3).  Levels 0, 1 and 2 hold integer multiples of
+// One job = one 128 x 64 output tile (rows of a slab row tile x half of a
+// B slab row tile) and a list of items (A slab, B slab, K stages); all items
+// of a job share the row and column scales, so the K-concatenated stripe
+// sum_items A_item . B_item^T accumulates in TMEM without a separate
+// reduction (the stripe product of Sec. III.A).  Slice pairs (i, j), i + j < S,
+// go to four FP32 TMEM accumulators of 64 columns by level l = min(i + j, 3);
+// TMEM (512 columns) holds two such buffers, so the MMAs of chunk c + 1 run
+// while the drain reads chunk c.  Levels 0, 1 and 2 hold integer multiples of
 // their unit 2^-8l below 2^24 for K chunks of 192 (level 2 grows by at most
 // 2*256*128 + 128^2 = 2^16.3 per K, 192 K give 2^23.9), hence are exact whatever
 // rounding the tensor core applies when it adds into the accumulator
@@ -22,13 +24,16 @@
 // 2^-24-weighted tail.  A chunk is up to 192 K of one item; after it the
 // drain warps fold the four levels into a float-float register accumulator
 // (K2: scaled by the item's per-column factor, so every task keeps its own
-// S*8 bits); the first MMA of the next chunk into each level overwrites it.
-// At the end of the job they write the tile (K1: float-float T; K2: F += FP64).
+// S*8 bits); the first MMA into each level of the buffer's next chunk
+// overwrites it.  At the end of the job they write the tile (K1: float-float
+// T; K2: F += FP64).  The two 64-column halves of a 128-column slab tile are
+// neighbouring jobs, so the second read of their common A tiles mostly hits L2.
 //
 // Warp roles (576 threads): warp 0 bulk-copy producer and job fetcher
 // (dynamic schedule: an atomic job counter, handed to the other roles through
 // a shared-memory ring), warp 1 MMA issuer, warps 2..17 drain/epilogue (TMEM
-// lane quarter w%4, 32-column group (w-2)/4).
+// lane quarter w%4, 16-column group (w-2)/4).  The drain warps arrive on
+// barriers with one lane each.
 // Every mbarrier wait is bounded; on timeout the CTA records a status,
 // stops issuing, waits (bounded) for its own copies and MMAs, frees TMEM and
 // returns.
@@ -40,19 +45,40 @@
 namespace su2 {
 namespace sp {
 
-constexpr int kRows = 128;           // M tile = N tile
+constexpr int kRows = 128;           // M tile; slab row tile
+// TMEM accumulator buffers: 1 = 128-column job tiles, the drain of a chunk
+// stalls the MMAs; 2 = 64-column tiles, the drain overlaps the next chunk.
+// Each MMA costs about the same time for N = 64 and 128 (measured in place),
+// so the wide single buffer wins.
+constexpr int kNumBuf = 1;
+constexpr int kCols = 128 / kNumBuf;  // N tile of a job
 constexpr int kKS = 16;              // K per pipeline stage (one MMA K step)
-constexpr int kSub = kRows * kKS * 2;  // bytes of one 128 x 16 BF16 sub-tile
+constexpr int kSub = kRows * kKS * 2;  // bytes of one 128 x 16 BF16 sub-tile (slabs, A stage)
+constexpr int kSubB = kCols * kKS * 2;  // bytes of the B part of a stage slice (kCols rows)
+constexpr int kBufCols = 4 * kCols;  // TMEM columns of one accumulator buffer (4 levels)
+constexpr int kDrainCols = kCols / 4;  // columns per drain thread (16 drain warps: 4 lane quarters x 4 groups)
+constexpr int kGroup = kDrainCols >= 32 ? 4 : 8;  // columns per TMEM load group
 constexpr int kMaxS = 6;
-constexpr int kStages = 4;
+constexpr int kStepK = 2;            // 16-K steps per pipeline stage (one barrier wait per 2 S(S+1)/2 MMAs)
+constexpr int kChunkSteps = 12;      // 16-K steps per exact drain chunk (192 K), a multiple of kStepK
 constexpr int kLead = 8;             // leading slice |q_0| <= 2^kLead, the others |q_i| <= 128
-constexpr int kChunkStages = 12;     // 192 K per exact drain
 constexpr int kRing = 4;             // job ring slots
-constexpr int kThreads = 576;      // producer + MMA + 16 drain warps
+constexpr int kMaxStages = 8;
+// bytes of one pipeline stage: kStepK x (S A slices of 128 rows + S B slices of 64 rows)
+__host__ __device__ constexpr int stage_bytes_of(int S) { return kStepK * S * (kSub + kSubB); }
+// stages that fit in 220 KB of shared memory (at most kMaxStages)
+__host__ __device__ constexpr int stages_of(int S) {
+  return (225280 / stage_bytes_of(S)) < kMaxStages ? (225280 / stage_bytes_of(S)) : kMaxStages;
+}
+__host__ __device__ constexpr int smem_bytes_of(int S) { return stages_of(S) * stage_bytes_of(S) + 1024; }
+// per-stage word the producer leaves for the MMA issuer (no global loads on the issue path)
+enum : uint32_t { kMetaFirst = 1, kMetaLast = 2, kMetaTwo = 4, kMetaEnd = 8 };  // bits 8..15: MMA N / 16
+constexpr int kDrainWarps = 16;
+constexpr int kThreads = 64 + 32 * kDrainWarps;  // producer + MMA + drain warps
 constexpr long kSpinLimit = 1L << 26;
 
 struct Item {
-  int64_t a_off, b_off;  // byte offsets of the first (row tile, K stage) group
+  int64_t a_off, b_off;  // byte offsets of the first (row tile, K stage) group (b_off: + the job's row offset inside a 128-row slab tile)
   int32_t nst;           // K stages of 16
   int32_t pad;
   int64_t sc_off;        // MODE_F: offset of the item's per-column drain exponents (a multiple of 128), -1 otherwise
@@ -68,11 +94,11 @@ struct TaskScale {
 struct Job {
   int64_t out_off;       // element offset of the output block
   int32_t rows, cols;    // valid extent of the output block
-  int32_t ld, tr, tc;    // leading dimension (rows of the block), tile indices
+  int32_t ld, tr, tc;    // leading dimension (rows of the block), tile indices (tc counts kCols columns)
   int32_t i0, i1;        // items
   int32_t rsc, csc;      // offsets of the row / column exponent arrays
   int32_t nst;           // total K stages of all items
-  int32_t nmma;          // MMA N of this tile: the valid columns rounded up to 16 (<= 128)
+  int32_t nmma;          // MMA N of this tile: the valid columns rounded up to 16 (<= kCols)
   int32_t pad2;
 };
 
@@ -101,7 +127,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 
 // bounded wait by every lane of a warp, then a warp vote: the warp leaves
 // converged (the .sync.aligned TMEM loads that follow need that) and agrees
-// on success
+// on the outcome (polling by lane 0 alone measured slower)
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
   const bool got = mbar_wait(bar, parity, abort_flag);
   return __all_sync(0xffffffffu, got);
@@ -133,21 +159,21 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, 
 }
 
 // the S(S+1)/2 slice products of one 16-K stage, unrolled: pair (i, j) goes to
-// level min(i + j, 3); da / db describe slice 0 of A / B, slice i sits kSub
-// bytes further (the descriptor's address field counts 16-byte units).  In the
-// first stage of a chunk the first product into each level, (0, level),
-// overwrites it.
+// level min(i + j, 3) (kCols TMEM columns each from tbuf); da / db describe
+// slice 0 of A / B, A slice i sits kSub bytes further, B slice j kSubB bytes
+// (the descriptor's address field counts 16-byte units).  In the first stage
+// of a chunk the first product into each level, (0, level), overwrites it.
 template <int S, bool FIRST>
-__device__ __forceinline__ void issue_stage(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc) {
+__device__ __forceinline__ void issue_stage(uint32_t tbuf, uint64_t da, uint64_t db, uint32_t idesc) {
 #pragma unroll
   for (int i = 0; i < S; ++i)
 #pragma unroll
     for (int jj = 0; jj < S - i; ++jj) {
       const int lvl = (i + jj) < 3 ? (i + jj) : 3;
       const uint64_t a = da + (uint64_t)(i * (kSub >> 4));
-      const uint64_t b = db + (uint64_t)(jj * (kSub >> 4));
-      if (FIRST && i == 0 && jj == lvl) mma_bf16<false>(tmem + lvl * kRows, a, b, idesc);
-      else mma_bf16<true>(tmem + lvl * kRows, a, b, idesc);
+      const uint64_t b = db + (uint64_t)(jj * (kSubB >> 4));
+      if (FIRST && i == 0 && jj == lvl) mma_bf16<false>(tbuf + lvl * kCols, a, b, idesc);
+      else mma_bf16<true>(tbuf + lvl * kCols, a, b, idesc);
     }
 }
 
@@ -155,10 +181,8 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// four 32x32b.x4 TMEM loads (one per accumulator level) and the wait in one
-// asm statement: tcgen05.ld writes its destination registers asynchronously,
-// so they must not exist as values in the program before tcgen05.wait::ld
-// (a separate wait statement would let the compiler reuse or read them early)
+// four 32x32b.x4 TMEM loads (four columns of each accumulator level) and
+// the wait in one asm statement (see below)
 __device__ __forceinline__ void tmem_ld4x4_wait(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                                 float (&v)[16]) {
   uint32_t r[16];
@@ -176,10 +200,40 @@ __device__ __forceinline__ void tmem_ld4x4_wait(uint32_t a0, uint32_t a1, uint32
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tmem_zero8(uint32_t taddr) {
-  const uint32_t z = 0u;
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr), "r"(z)
-               : "memory");
+// four 32x32b.x8 TMEM loads (eight columns of each accumulator level) and
+// the wait in one asm statement: tcgen05.ld writes its destination registers
+// asynchronously, so they must not exist as values in the program before
+// tcgen05.wait::ld (a separate wait statement would let the compiler reuse or
+// read them early)
+__device__ __forceinline__ void tmem_ld8x4_wait(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                                float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%33];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%34];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%35];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// kG columns of all four accumulator levels (level l at column offset l * kCols)
+template <int kG>
+__device__ __forceinline__ void tmem_ld_levels(uint32_t a, float (&x)[4 * kG]);
+template <>
+__device__ __forceinline__ void tmem_ld_levels<4>(uint32_t a, float (&x)[16]) {
+  tmem_ld4x4_wait(a, a + kCols, a + 2 * kCols, a + 3 * kCols, x);
+}
+template <>
+__device__ __forceinline__ void tmem_ld_levels<8>(uint32_t a, float (&x)[32]) {
+  tmem_ld8x4_wait(a, a + kCols, a + 2 * kCols, a + 3 * kCols, x);
 }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -200,27 +254,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                       int* __restrict__ job_counter, TaskScale ts) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  constexpr int stage_bytes = 2 * S * kSub;
-  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], accf_bar, acce_bar, done_bar;
+  constexpr int stage_bytes = stage_bytes_of(S);
+  constexpr int NS = stages_of(S);
+  __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], accf_bar[2], acce_bar[2], done_bar;
   __shared__ __align__(8) uint64_t jq_full[kRing], jq_empty[kRing];
   __shared__ int job_ring[kRing];
+  __shared__ uint32_t stage_meta[kMaxStages];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
-  __shared__ int issued[kStages];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < NS; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[s])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty_bar[s])));
-      issued[s] = 0;
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf_bar)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 512;" ::"r"(smem_u32(&acce_bar)));
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf_bar[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce_bar[b])), "r"(kDrainWarps));
+    }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done_bar)));
     for (int r = 0; r < kRing; ++r) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&jq_full[r])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 513;" ::"r"(smem_u32(&jq_empty[r])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&jq_empty[r])), "r"(kDrainWarps));
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_flag = 0;
@@ -233,12 +289,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const int nlev = S < 4 ? S : 4;
+  constexpr int nlev = S < 4 ? S : 4;
   if (warp == 0) {
     // ------------------------------------------------------------ producer
+    // fetches jobs for the drain warps (job ring) and fills the stage ring
+    // for the MMA issuer, with one metadata word per stage
     if (lane == 0) {
       int st = 0;
-      uint32_t use[kStages] = {0, 0, 0, 0};
+      uint32_t ph = 0;  // phase of the current use of slot st (flips when st wraps)
+      int nissued = 0;
       bool ok = true;
       for (int k = 0; ok; ++k) {
         const int slot = k % kRing;
@@ -252,94 +311,121 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&jq_full[slot])) : "memory");
         if (j < 0) break;
         const Job jb = jobs[j];
-        const int bbytes = jb.nmma * 32;  // first nmma rows of each B slice sub-tile
-        const int tx = S * kSub + S * bbytes;
+        const int bbytes = jb.nmma * 32;  // the job's nmma rows of each B slice sub-tile (<= kSubB)
+        const uint32_t nmeta = (uint32_t)(jb.nmma >> 4) << 8;
         for (int it = jb.i0; it < jb.i1 && ok; ++it) {
           const Item item = items[it];
-          for (int ks = 0; ks < item.nst; ++ks) {
-            if (!mbar_wait(smem_u32(&empty_bar[st]), (use[st] & 1) ^ 1, &abort_flag)) {
+          const int nstage = (item.nst + kStepK - 1) / kStepK;
+          for (int ks = 0; ks < nstage; ++ks) {
+            if (!mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1, &abort_flag)) {
               ok = false;
               break;
             }
+            const int k16 = ks * kStepK;  // first 16-K step of the stage within the item
+            const int nk = min(kStepK, item.nst - k16);
+            uint32_t m = nmeta | (nk == 2 ? kMetaTwo : 0u);
+            if (k16 % kChunkSteps == 0) m |= kMetaFirst;
+            if ((k16 + kStepK) % kChunkSteps == 0 || ks == nstage - 1) m |= kMetaLast;
+            stage_meta[st] = m;
             const uint32_t fb = smem_u32(&full_bar[st]);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(tx) : "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(nk * S * (kSub + bbytes))
+                         : "memory");
             const uint32_t dst = smem_u32(smem + st * stage_bytes);
-            const unsigned char* srcA = Aslab + item.a_off + (int64_t)ks * S * kSub;
-            const unsigned char* srcB = Bslab + item.b_off + (int64_t)ks * S * kSub;
+            const unsigned char* srcA = Aslab + item.a_off + (int64_t)k16 * S * kSub;
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                "l"(srcA), "r"(S * kSub), "r"(fb)
+                "l"(srcA), "r"(nk * S * kSub), "r"(fb)
                 : "memory");
-            for (int jj = 0; jj < S; ++jj)
-              asm volatile(
-                  "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                      dst + S * kSub + jj * kSub),
-                  "l"(srcB + jj * kSub), "r"(bbytes), "r"(fb)
-                  : "memory");
-            issued[st] = (int)use[st] + 1;
-            use[st] += 1;
-            st = (st + 1) % kStages;
+            for (int kk = 0; kk < nk; ++kk) {
+              const unsigned char* srcB = Bslab + item.b_off + (int64_t)(k16 + kk) * S * kSub;
+#pragma unroll
+              for (int jj = 0; jj < S; ++jj)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        dst + kStepK * S * kSub + (kk * S + jj) * kSubB),
+                    "l"(srcB + jj * kSub), "r"(bbytes), "r"(fb)
+                    : "memory");
+            }
+            ++nissued;
+            if (++st == NS) {
+              st = 0;
+              ph ^= 1;
+            }
           }
+        }
+      }
+      // end marker for the MMA issuer: a stage without data
+      if (ok) {
+        if (mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1, &abort_flag)) {
+          stage_meta[st] = kMetaEnd;
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[st])) : "memory");
+          ++nissued;
+          if (++st == NS) {
+            st = 0;
+            ph ^= 1;
+          }
+        } else {
+          ok = false;
         }
       }
       if (!ok) {
         abort_flag = 1;
         atomicExch(status, 4);
       }
-      // wait (bounded) for every copy this CTA issued
-      for (int s = 0; s < kStages; ++s)
-        if (issued[s] > 0) {
-          bool fin = false;
-          for (long it = 0; it < kSpinLimit && !fin; ++it) fin = mbar_try(smem_u32(&full_bar[s]), (issued[s] - 1) & 1);
-          if (!fin) atomicExch(status, 4);
+      // wait (bounded) for the last use of every slot: all copies this CTA issued have landed
+      for (int b = 0; b < NS && b < nissued; ++b) {
+        int s2 = st - 1 - b;
+        uint32_t p2 = ph;
+        if (s2 < 0) {
+          s2 += NS;
+          p2 ^= 1;
         }
+        bool fin = false;
+        for (long it = 0; it < kSpinLimit && !fin; ++it) fin = mbar_try(smem_u32(&full_bar[s2]), p2);
+        if (!fin) atomicExch(status, 4);
+      }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
+    // reads only shared memory: the stage ring and its metadata words
     if (lane == 0) {
       int st = 0;
-      uint32_t use[kStages] = {0, 0, 0, 0};
-      uint32_t chunk = 0;
+      uint32_t ph = 0;
+      uint32_t chunk = 0;  // chunk c accumulates in TMEM buffer c % kNumBuf
       bool ok = true;
-      for (int k = 0; ok; ++k) {
-        const int slot = k % kRing;
-        if (!mbar_wait(smem_u32(&jq_full[slot]), (k / kRing) & 1, &abort_flag)) {
+      const uint32_t sbase = smem_u32(smem);
+      for (;;) {
+        if (!mbar_wait(smem_u32(&full_bar[st]), ph, &abort_flag)) {
           ok = false;
           break;
         }
-        const int j = job_ring[slot];
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&jq_empty[slot])) : "memory");
-        if (j < 0) break;
-        const Job jb = jobs[j];
-        const uint32_t idesc = idesc_n(jb.nmma);
-        for (int it = jb.i0; it < jb.i1 && ok; ++it) {
-          const int nst = items[it].nst;
-          for (int ks = 0; ks < nst; ++ks) {
-            const int cpos = ks % kChunkStages;  // a chunk = up to kChunkStages stages of one item
-            if (cpos == 0) {
-              if (!mbar_wait(smem_u32(&acce_bar), (chunk & 1) ^ 1, &abort_flag)) {
-                ok = false;
-                break;
-              }
-              asm volatile("tcgen05.fence::after_thread_sync;");
-            }
-            if (!mbar_wait(smem_u32(&full_bar[st]), use[st] & 1, &abort_flag)) {
-              ok = false;
-              break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t sa = smem_u32(smem + st * stage_bytes);
-            const uint64_t da = make_desc(sa), db = make_desc(sa + S * kSub);
-            if (cpos == 0) issue_stage<S, true>(tmem, da, db, idesc);
-            else issue_stage<S, false>(tmem, da, db, idesc);
-            mma_commit(smem_u32(&empty_bar[st]));
-            use[st] += 1;
-            st = (st + 1) % kStages;
-            if (cpos == kChunkStages - 1 || ks == nst - 1) {
-              mma_commit(smem_u32(&accf_bar));
-              chunk += 1;
-            }
+        const uint32_t m = *(volatile uint32_t*)&stage_meta[st];
+        if (m & kMetaEnd) break;
+        const uint32_t buf = chunk % kNumBuf;
+        if (m & kMetaFirst) {
+          // the buffer's previous chunk (c - kNumBuf) must have been read by the drain
+          if (!mbar_wait(smem_u32(&acce_bar[buf]), ((chunk / kNumBuf) & 1) ^ 1, &abort_flag)) {
+            ok = false;
+            break;
           }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+        }
+        const uint32_t idesc = idesc_n((int)((m >> 8) & 0xff) * 16);
+        const uint32_t sa = sbase + st * stage_bytes;
+        const uint64_t da = make_desc(sa), db = make_desc(sa + kStepK * S * kSub);
+        const uint32_t tb = tmem + buf * kBufCols;
+        if (m & kMetaFirst) issue_stage<S, true>(tb, da, db, idesc);
+        else issue_stage<S, false>(tb, da, db, idesc);
+        if (m & kMetaTwo)
+          issue_stage<S, false>(tb, da + (uint64_t)(S * (kSub >> 4)), db + (uint64_t)(S * (kSubB >> 4)), idesc);
+        mma_commit(smem_u32(&empty_bar[st]));
+        if (m & kMetaLast) {
+          mma_commit(smem_u32(&accf_bar[buf]));
+          chunk += 1;
+        }
+        if (++st == NS) {
+          st = 0;
+          ph ^= 1;
         }
       }
       if (!ok) {
@@ -355,9 +441,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ------------------------------------------------------------ drain / epilogue
     const int q = warp & 3;             // TMEM lane quarter
-    const int cgrp = (warp - 2) >> 2;   // 32-column group
+    const int cgrp = (warp - 2) >> 2;   // column group of kDrainCols
     const int row = q * 32 + lane;
-    const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+    const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + cgrp * kDrainCols;
     uint32_t chunk = 0;
     bool ok = true;
     for (int k = 0; ok; ++k) {
@@ -367,71 +453,69 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       const int j = job_ring[slot];
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&jq_empty[slot])) : "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&jq_empty[slot])) : "memory");
       if (j < 0) break;
       const Job jb = jobs[j];
-      float hi[32], lo[32];
+      float hi[kDrainCols], lo[kDrainCols];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
+      for (int c = 0; c < kDrainCols; ++c) {
         hi[c] = 0.f;
         lo[c] = 0.f;
       }
-      const int ncg4 = min(8, max(0, (jb.nmma - cgrp * 32 + 3) / 4));
-      const int c0 = jb.tc * kRows + cgrp * 32;
+      constexpr int kNG = kDrainCols / kGroup;
+      const int ng = min(kNG, max(0, (jb.nmma - cgrp * kDrainCols + kGroup - 1) / kGroup));  // valid column groups
+      const int c0 = jb.tc * kCols + cgrp * kDrainCols;
       for (int it = jb.i0; it < jb.i1 && ok; ++it) {
         const Item item = items[it];
-        // MODE_F: this thread's 32 drain exponents of the item, fetched before
-        // the chunk wait (two 16-byte loads; byte k of word w = column 4w + k)
-        uint32_t dx[8];
+        // MODE_F: this thread's drain exponents of the item, fetched before
+        // the chunk wait (16-byte loads; byte k of word w = column 4w + k)
+        uint32_t dx[kDrainCols / 4];
         if (MODE == MODE_F) {
-          const int4* p = reinterpret_cast<const int4*>(ts.dexp + item.sc_off + c0);
-          const int4 u0 = __ldg(p), u1 = __ldg(p + 1);
-          dx[0] = u0.x, dx[1] = u0.y, dx[2] = u0.z, dx[3] = u0.w;
-          dx[4] = u1.x, dx[5] = u1.y, dx[6] = u1.z, dx[7] = u1.w;
+#pragma unroll
+          for (int v = 0; v < kDrainCols / 16; ++v) {
+            const int4 u = __ldg(reinterpret_cast<const int4*>(ts.dexp + item.sc_off + c0) + v);
+            dx[4 * v] = u.x, dx[4 * v + 1] = u.y, dx[4 * v + 2] = u.z, dx[4 * v + 3] = u.w;
+          }
         }
-        const int nch = (item.nst + kChunkStages - 1) / kChunkStages;
+        const int nch = (item.nst + kChunkSteps - 1) / kChunkSteps;
         for (int ch = 0; ch < nch; ++ch) {
-          if (!warp_wait(smem_u32(&accf_bar), chunk & 1, &abort_flag)) {
+          const uint32_t buf = chunk % kNumBuf;
+          if (!warp_wait(smem_u32(&accf_bar[buf]), (chunk / kNumBuf) & 1, &abort_flag)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-          for (int cg = 0; cg < 8; ++cg) {
-            if (cg >= ncg4) break;
-            const uint32_t col = cgrp * 32 + cg * 4;
-            float xx[16];  // levels 0..3, four columns each
-            tmem_ld4x4_wait(lane_addr + col, lane_addr + 128 + col, lane_addr + 256 + col, lane_addr + 384 + col,
-                            xx);
-            float x0[4], x1[4], x2[4], x3[4];
+          for (int g = 0; g < kNG; ++g) {
+            if (g >= ng) break;
+            const uint32_t a = lane_addr + buf * kBufCols + g * kGroup;
+            float x[4 * kGroup];  // levels 0..3, kGroup columns each
+            tmem_ld_levels<kGroup>(a, x);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              x0[c] = xx[c];
-              x1[c] = xx[4 + c];
-              x2[c] = xx[8 + c];
-              x3[c] = xx[12 + c];
-            }
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const float y1 = nlev > 1 ? x1[c] : 0.f;
-              const float y2 = nlev > 2 ? x2[c] : 0.f;
-              const float y3 = nlev > 3 ? x3[c] : 0.f;
+            for (int c = 0; c < kGroup; ++c) {
+              const int k = g * kGroup + c;  // column within this thread's group
+              const float y1 = nlev > 1 ? x[kGroup + c] : 0.f;
+              const float y2 = nlev > 2 ? x[2 * kGroup + c] : 0.f;
+              const float y3 = nlev > 3 ? x[3 * kGroup + c] : 0.f;
               float f = 1.f;
               if (MODE == MODE_F) {
-                const int d = (int)(int8_t)(dx[cg] >> (8 * c));
+                const int d = (int)(int8_t)(dx[k >> 2] >> (8 * (k & 3)));
                 f = __int_as_float((127 + d) << 23);  // 2^d; d = -127 gives 0
               }
               float s, e, h, e2;
-              two_sum(x0[c] * f, y1 * f, s, e);
-              two_sum(hi[cg * 4 + c], s, h, e2);
-              const float l = lo[cg * 4 + c] + (e2 + (e + (y2 * f + y3 * f)));
+              two_sum(x[c] * f, y1 * f, s, e);
+              two_sum(hi[k], s, h, e2);
+              const float l = lo[k] + (e2 + (e + (y2 * f + y3 * f)));
               const float hs = h + l;
-              lo[cg * 4 + c] = l - (hs - h);
-              hi[cg * 4 + c] = hs;
+              lo[k] = l - (hs - h);
+              hi[k] = hs;
             }
           }
           asm volatile("tcgen05.fence::before_thread_sync;");
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar)) : "memory");
+          __syncwarp();
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[buf])) : "memory");
           chunk += 1;
         }
       }
@@ -441,22 +525,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (r < jb.rows) {
         const int er = rexp[jb.rsc + r];
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          int ce[8];
-#pragma unroll
-          for (int c = 0; c < 8; ++c) ce[c] = (c0 + g * 8 + c < jb.cols) ? cexp[jb.csc + c0 + g * 8 + c] : 0;
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const int cc = c0 + g * 8 + c;
-            if (cc < jb.cols) {
-              const int ex = er + ce[c] - shift;
-              const int64_t o = jb.out_off + r + (int64_t)cc * jb.ld;
-              if (MODE == MODE_T) {
-                Th[o] = ldexp_f(hi[g * 8 + c], ex);
-                Tl[o] = ldexp_f(lo[g * 8 + c], ex);
-              } else {
-                F[o] += ldexp((double)hi[g * 8 + c] + (double)lo[g * 8 + c], ex);
-              }
+        for (int c = 0; c < kDrainCols; ++c) {
+          const int cc = c0 + c;
+          if (cc < jb.cols) {
+            const int ex = er + cexp[jb.csc + cc] - shift;
+            const int64_t o = jb.out_off + r + (int64_t)cc * jb.ld;
+            if (MODE == MODE_T) {
+              Th[o] = ldexp_f(hi[c], ex);
+              Tl[o] = ldexp_f(lo[c], ex);
+            } else {
+              F[o] += ldexp((double)hi[c] + (double)lo[c], ex);
             }
           }
         }
