@@ -171,8 +171,9 @@ __global__ void delta_fix_kernel(int* __restrict__ delta, int n) {
   if (i < n && delta[i] == INT_MAX) delta[i] = 0;
 }
 
-// slab of FP64 matrices: one CTA of 128 threads per (desc, row tile, K stage);
-// thread = one slab row, 16 K elements = 2 core-matrix columns
+// slab of FP64 matrices (compact layout, split_gemm.cuh): one CTA of 128
+// threads per (desc, row tile, K step); thread = one slab row, 16 K elements =
+// 2 core-matrix columns; rows past the stored ones write nothing
 __global__ void slab_fp64_kernel(const SlabDesc* __restrict__ descs, const Unit* __restrict__ units,
                                  const double* __restrict__ src, const int* __restrict__ rexp,
                                  const int* __restrict__ delta, unsigned char* __restrict__ slab, int S) {
@@ -181,7 +182,9 @@ __global__ void slab_fp64_kernel(const SlabDesc* __restrict__ descs, const Unit*
   const int t = threadIdx.x;
   const int r = u.tr * 128 + t;
   const int kst = (d.cols + sp::kKS - 1) / sp::kKS;
-  unsigned char* base = slab + d.slab_off + (int64_t(u.tr) * kst + u.ks) * S * kSub;
+  const int trows = sp::tile_rows(d.rows, u.tr);
+  if (t >= trows) return;
+  unsigned char* base = slab + d.slab_off + sp::slab_pos(d.rows, kst, S, u.tr, u.ks, 0);
   int sigma = 0;
   if (r < d.rows) {
     sigma = rexp[d.exp_off + r];
@@ -210,7 +213,7 @@ __global__ void slab_fp64_kernel(const SlabDesc* __restrict__ descs, const Unit*
         y[q] = (y[q] - qi) * 256.0;
         v[q] = __float2bfloat16_rn(ldexpf((float)qi, -8 * i));
       }
-      *(uint4*)(base + i * kSub + (mi * 2 + kg) * 128 + rr * 16) = *(const uint4*)v;
+      *(uint4*)(base + int64_t(i) * trows * 32 + (mi * 2 + kg) * 128 + rr * 16) = *(const uint4*)v;
     }
   }
 }
@@ -311,7 +314,9 @@ __global__ void slab_tprime_kernel(const TPTask* __restrict__ tasks, const TPUni
   const int tt = threadIdx.x;
   const int c = u.tr * 128 + tt;  // slab row = source column
   const int kst = (s.rows + sp::kKS - 1) / sp::kKS;
-  unsigned char* base = slab + t.tp_off + (int64_t(u.tr) * kst + u.ks) * S * kSub;
+  const int trows = sp::tile_rows(s.cols, u.tr);
+  if (tt >= trows) return;
+  unsigned char* base = slab + t.tp_off + sp::slab_pos(s.cols, kst, S, u.tr, u.ks, 0);
   const float* H = s.sel ? Ph : Th;
   const float* Lo = s.sel ? Pl : Tl;
   int sc = 0;  // the task's own column exponent: |v 2^-delta T[:, c]| < 2^sc
@@ -354,7 +359,7 @@ __global__ void slab_tprime_kernel(const TPTask* __restrict__ tasks, const TPUni
         ph[q] = hs * 256.f;
         v[q] = __float2bfloat16_rn(ldexpf(qi, -8 * i));
       }
-      *(uint4*)(base + i * kSub + (mi * 2 + kg) * 128 + rr * 16) = *(const uint4*)v;
+      *(uint4*)(base + int64_t(i) * trows * 32 + (mi * 2 + kg) * 128 + rr * 16) = *(const uint4*)v;
     }
   }
 }
@@ -387,8 +392,11 @@ int dput(T** p, const std::vector<T>& h, std::string& err) {
   return SU2_OK;
 }
 
+// bytes of a compact slab (split_gemm.cuh): full 128-row tiles and a last tile of its rows rounded up to 16
 int64_t slab_bytes(int rows, int cols, int S) {
-  return int64_t((rows + 127) / 128) * ((cols + sp::kKS - 1) / sp::kKS) * S * kSub;
+  const int nt = (rows + 127) / 128;
+  if (nt == 0) return 0;
+  return (int64_t(nt - 1) * kSub + sp::tile_rows(rows, nt - 1) * 32) * ((cols + sp::kKS - 1) / sp::kKS) * S;
 }
 
 void add_units(std::vector<Unit>& u, int desc, int rows, int cols) {
@@ -402,13 +410,8 @@ int32_t nmma_of(int cols, int tc) {
   return int32_t((rem + 15) / 16 * 16);
 }
 
-// byte offset of job column tile tc (kCols wide) inside a B slab whose row
-// tiles span 128 rows: its 128-row tile, plus the tile's first row inside it
-// (32 bytes per row in the core-matrix layout)
-int64_t btile_off(int tc, int kst, int S) {
-  const int c0 = tc * sp::kCols;
-  return int64_t(c0 / 128) * kst * S * kSub + (c0 % 128) * 32;
-}
+// byte offset of job column tile tc (kCols = 128 wide) in a compact B slab: its row tile
+int64_t btile_off(int tc, int kst, int S) { return int64_t(tc) * kst * S * kSub; }
 
 int exp_host(double x) {
   if (x == 0.0) return kSentinel;

@@ -46,12 +46,12 @@ namespace su2 {
 namespace sp {
 
 constexpr int kRows = 128;           // M tile; slab row tile
-// TMEM accumulator buffers: 1 = 128-column job tiles, the drain of a chunk
-// stalls the MMAs; 2 = 64-column tiles, the drain overlaps the next chunk.
-// Each MMA costs about the same time for N = 64 and 128 (measured in place),
-// so the wide single buffer wins.
+// One TMEM accumulator buffer of 128-column job tiles: the drain of a chunk
+// stalls the MMAs.  Two buffers of 64-column tiles (drain overlapped) were
+// measured slower: in place an MMA costs about the same time for N = 64 and
+// N = 128, so the wide tile does twice the work per MMA.
 constexpr int kNumBuf = 1;
-constexpr int kCols = 128 / kNumBuf;  // N tile of a job
+constexpr int kCols = 128;  // N tile of a job
 constexpr int kKS = 16;              // K per pipeline stage (one MMA K step)
 constexpr int kSub = kRows * kKS * 2;  // bytes of one 128 x 16 BF16 sub-tile (slabs, A stage)
 constexpr int kSubB = kCols * kKS * 2;  // bytes of the B part of a stage slice (kCols rows)
@@ -71,14 +71,28 @@ __host__ __device__ constexpr int stages_of(int S) {
   return (225280 / stage_bytes_of(S)) < kMaxStages ? (225280 / stage_bytes_of(S)) : kMaxStages;
 }
 __host__ __device__ constexpr int smem_bytes_of(int S) { return stages_of(S) * stage_bytes_of(S) + 1024; }
-// per-stage word the producer leaves for the MMA issuer (no global loads on the issue path)
-enum : uint32_t { kMetaFirst = 1, kMetaLast = 2, kMetaTwo = 4, kMetaEnd = 8 };  // bits 8..15: MMA N / 16
+// per-stage word the producer leaves for the MMA issuer (no global loads on
+// the issue path); bits 8..11: MMA N / 16, bits 12..15: stored A rows / 16
+enum : uint32_t { kMetaFirst = 1, kMetaLast = 2, kMetaTwo = 4, kMetaEnd = 8 };
+
+// Compact slab layout: row tile tr of an R-row operand stores only its rows,
+// rounded up to 16; its (16-K step k, slice i) sub-tile sits at
+// tr * kst * S * kSub + (k * S + i) * tile_rows * 32 (core matrices of 8 rows x
+// 16 bytes, (mi * 2 + ki) * 128 within the sub-tile).  All tiles but the last
+// hold 128 rows.
+__host__ __device__ inline int tile_rows(int R, int tr) {
+  const int r = R - tr * kRows;
+  return ((r < kRows ? r : kRows) + 15) & ~15;
+}
+__host__ __device__ inline int64_t slab_pos(int R, int kst, int S, int tr, int k, int i) {
+  return int64_t(tr) * kst * S * kSub + (int64_t(k) * S + i) * tile_rows(R, tr) * 32;
+}
 constexpr int kDrainWarps = 16;
 constexpr int kThreads = 64 + 32 * kDrainWarps;  // producer + MMA + drain warps
 constexpr long kSpinLimit = 1L << 26;
 
 struct Item {
-  int64_t a_off, b_off;  // byte offsets of the first (row tile, K stage) group (b_off: + the job's row offset inside a 128-row slab tile)
+  int64_t a_off, b_off;  // byte offsets of the item's A / B row tiles in their compact slabs
   int32_t nst;           // K stages of 16
   int32_t pad;
   int64_t sc_off;        // MODE_F: offset of the item's per-column drain exponents (a multiple of 128), -1 otherwise
@@ -158,20 +172,23 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, 
     asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 0;" ::"r"(tmem), "l"(a), "l"(b), "r"(idesc));
 }
 
-// the S(S+1)/2 slice products of one 16-K stage, unrolled: pair (i, j) goes to
+// the S(S+1)/2 slice products of one 16-K step, unrolled: pair (i, j) goes to
 // level min(i + j, 3) (kCols TMEM columns each from tbuf); da / db describe
-// slice 0 of A / B, A slice i sits kSub bytes further, B slice j kSubB bytes
-// (the descriptor's address field counts 16-byte units).  In the first stage
-// of a chunk the first product into each level, (0, level), overwrites it.
+// slice 0 of A / B, slice i sits as16 / bs16 16-byte units further (the
+// descriptor's address field counts 16-byte units; an A slice stored with
+// fewer than 128 rows lets the MMA read the next slice's bytes as rows past
+// the tile, whose outputs are never used).  In the first step of a chunk the
+// first product into each level, (0, level), overwrites it.
 template <int S, bool FIRST>
-__device__ __forceinline__ void issue_stage(uint32_t tbuf, uint64_t da, uint64_t db, uint32_t idesc) {
+__device__ __forceinline__ void issue_stage(uint32_t tbuf, uint64_t da, uint64_t db, uint32_t as16, uint32_t bs16,
+                                            uint32_t idesc) {
 #pragma unroll
   for (int i = 0; i < S; ++i)
 #pragma unroll
     for (int jj = 0; jj < S - i; ++jj) {
       const int lvl = (i + jj) < 3 ? (i + jj) : 3;
-      const uint64_t a = da + (uint64_t)(i * (kSub >> 4));
-      const uint64_t b = db + (uint64_t)(jj * (kSubB >> 4));
+      const uint64_t a = da + (uint64_t)(i * as16);
+      const uint64_t b = db + (uint64_t)(jj * bs16);
       if (FIRST && i == 0 && jj == lvl) mma_bf16<false>(tbuf + lvl * kCols, a, b, idesc);
       else mma_bf16<true>(tbuf + lvl * kCols, a, b, idesc);
     }
@@ -311,8 +328,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&jq_full[slot])) : "memory");
         if (j < 0) break;
         const Job jb = jobs[j];
-        const int bbytes = jb.nmma * 32;  // the job's nmma rows of each B slice sub-tile (<= kSubB)
-        const uint32_t nmeta = (uint32_t)(jb.nmma >> 4) << 8;
+        const int arows = tile_rows(jb.rows, jb.tr);
+        const int abytes = arows * 32, bbytes = jb.nmma * 32;  // stored bytes of one A / B sub-tile
+        const uint32_t nmeta = ((uint32_t)(jb.nmma >> 4) << 8) | ((uint32_t)(arows >> 4) << 12);
         for (int it = jb.i0; it < jb.i1 && ok; ++it) {
           const Item item = items[it];
           const int nstage = (item.nst + kStepK - 1) / kStepK;
@@ -328,24 +346,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             if ((k16 + kStepK) % kChunkSteps == 0 || ks == nstage - 1) m |= kMetaLast;
             stage_meta[st] = m;
             const uint32_t fb = smem_u32(&full_bar[st]);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(nk * S * (kSub + bbytes))
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                         "r"(nk * S * (abytes + bbytes))
                          : "memory");
+            // the nk steps x S slices of A, then of B, are contiguous in their slabs
             const uint32_t dst = smem_u32(smem + st * stage_bytes);
-            const unsigned char* srcA = Aslab + item.a_off + (int64_t)k16 * S * kSub;
+            const unsigned char* srcA = Aslab + item.a_off + (int64_t)k16 * S * abytes;
+            const unsigned char* srcB = Bslab + item.b_off + (int64_t)k16 * S * bbytes;
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                "l"(srcA), "r"(nk * S * kSub), "r"(fb)
+                "l"(srcA), "r"(nk * S * abytes), "r"(fb)
                 : "memory");
-            for (int kk = 0; kk < nk; ++kk) {
-              const unsigned char* srcB = Bslab + item.b_off + (int64_t)(k16 + kk) * S * kSub;
-#pragma unroll
-              for (int jj = 0; jj < S; ++jj)
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        dst + kStepK * S * kSub + (kk * S + jj) * kSubB),
-                    "l"(srcB + jj * kSub), "r"(bbytes), "r"(fb)
-                    : "memory");
-            }
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    dst + kStepK * S * kSub),
+                "l"(srcB), "r"(nk * S * bbytes), "r"(fb)
+                : "memory");
             ++nissued;
             if (++st == NS) {
               st = 0;
@@ -410,14 +426,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
         }
-        const uint32_t idesc = idesc_n((int)((m >> 8) & 0xff) * 16);
+        const uint32_t n16 = (m >> 8) & 0xf, a16 = (m >> 12) & 0xf;
+        const uint32_t idesc = idesc_n((int)n16 * 16);
+        const uint32_t bs16 = n16 * 32, as16 = a16 * 32;  // sub-tile strides in 16-byte units (rows * 32 / 16)
         const uint32_t sa = sbase + st * stage_bytes;
         const uint64_t da = make_desc(sa), db = make_desc(sa + kStepK * S * kSub);
         const uint32_t tb = tmem + buf * kBufCols;
-        if (m & kMetaFirst) issue_stage<S, true>(tb, da, db, idesc);
-        else issue_stage<S, false>(tb, da, db, idesc);
+        if (m & kMetaFirst) issue_stage<S, true>(tb, da, db, as16, bs16, idesc);
+        else issue_stage<S, false>(tb, da, db, as16, bs16, idesc);
         if (m & kMetaTwo)
-          issue_stage<S, false>(tb, da + (uint64_t)(S * (kSub >> 4)), db + (uint64_t)(S * (kSubB >> 4)), idesc);
+          issue_stage<S, false>(tb, da + (uint64_t)(S * as16), db + (uint64_t)(S * bs16), as16, bs16, idesc);
         mma_commit(smem_u32(&empty_bar[st]));
         if (m & kMetaLast) {
           mma_commit(smem_u32(&accf_bar[buf]));
