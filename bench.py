@@ -308,7 +308,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": cfg.name, "L": cfg.L, "N": cfg.N, "twoS": cfg.twoS, "D": cfg.D,
                        "prec": "fp64" if prec == P.SU2_FP64 else
-                       "bf16 slices on tcgen05, fp32 accumulate (exact per 128-K chunk), float-float/fp64 recombine",
+                       "bf16 slices on tcgen05, fp32 accumulate (exact per 192-K chunk), float-float/fp64 recombine",
                        "psi_len": n, "terms": info["n_terms"], "tasks": info["n_tasks"],
                        "l2": "flushed between steps (256 MB write)"},
             "value_u1_equiv": value * info["r_d"],
