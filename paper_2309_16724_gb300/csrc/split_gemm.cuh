@@ -253,12 +253,15 @@ __device__ __forceinline__ void tmem_ld_levels<8>(uint32_t a, float (&x)[32]) {
   tmem_ld8x4_wait(a, a + kCols, a + 2 * kCols, a + 3 * kCols, x);
 }
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+// packed FP32 pairs (two drain columns per instruction); every step is the
+// same IEEE operation on each half, so TwoSum stays error-free
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = add2(a, b);
+  const float2 bb = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
 }
-
 // x * 2^k for float, exact while the result stays normal
 __device__ __forceinline__ float ldexp_f(float x, int k) { return ldexpf(x, k); }
 
@@ -475,11 +478,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&jq_empty[slot])) : "memory");
       if (j < 0) break;
       const Job jb = jobs[j];
-      float hi[kDrainCols], lo[kDrainCols];
+      float2 hi2[kDrainCols / 2], lo2[kDrainCols / 2];
 #pragma unroll
-      for (int c = 0; c < kDrainCols; ++c) {
-        hi[c] = 0.f;
-        lo[c] = 0.f;
+      for (int c = 0; c < kDrainCols / 2; ++c) {
+        hi2[c] = make_float2(0.f, 0.f);
+        lo2[c] = make_float2(0.f, 0.f);
       }
       constexpr int kNG = kDrainCols / kGroup;
       const int ng = min(kNG, max(0, (jb.nmma - cgrp * kDrainCols + kGroup - 1) / kGroup));  // valid column groups
@@ -511,23 +514,32 @@ __global__ void __launch_bounds__(kThreads, 1)
             float x[4 * kGroup];  // levels 0..3, kGroup columns each
             tmem_ld_levels<kGroup>(a, x);
 #pragma unroll
-            for (int c = 0; c < kGroup; ++c) {
-              const int k = g * kGroup + c;  // column within this thread's group
-              const float y1 = nlev > 1 ? x[kGroup + c] : 0.f;
-              const float y2 = nlev > 2 ? x[2 * kGroup + c] : 0.f;
-              const float y3 = nlev > 3 ? x[3 * kGroup + c] : 0.f;
-              float f = 1.f;
+            for (int c = 0; c < kGroup; c += 2) {
+              const int k = g * kGroup + c;  // column within this thread's group (even)
+              const float2 z = make_float2(0.f, 0.f);
+              const float2 x0 = make_float2(x[c], x[c + 1]);
+              const float2 y1 = nlev > 1 ? make_float2(x[kGroup + c], x[kGroup + c + 1]) : z;
+              const float2 y2 = nlev > 2 ? make_float2(x[2 * kGroup + c], x[2 * kGroup + c + 1]) : z;
+              const float2 y3 = nlev > 3 ? make_float2(x[3 * kGroup + c], x[3 * kGroup + c + 1]) : z;
+              float2 s, e, h, e2;
               if (MODE == MODE_F) {
-                const int d = (int)(int8_t)(dx[k >> 2] >> (8 * (k & 3)));
-                f = __int_as_float((127 + d) << 23);  // 2^d; d = -127 gives 0
+                const int d0 = (int)(int8_t)(dx[k >> 2] >> (8 * (k & 3)));
+                const int d1 = (int)(int8_t)(dx[(k + 1) >> 2] >> (8 * ((k + 1) & 3)));
+                const float2 f2 = make_float2(__int_as_float((127 + d0) << 23), __int_as_float((127 + d1) << 23));
+                two_sum2(__fmul2_rn(x0, f2), __fmul2_rn(y1, f2), s, e);
+                two_sum2(hi2[k >> 1], s, h, e2);
+                const float2 l = add2(lo2[k >> 1], add2(e2, add2(e, __ffma2_rn(y2, f2, __fmul2_rn(y3, f2)))));
+                const float2 hs = add2(h, l);
+                lo2[k >> 1] = sub2(l, sub2(hs, h));
+                hi2[k >> 1] = hs;
+              } else {
+                two_sum2(x0, y1, s, e);
+                two_sum2(hi2[k >> 1], s, h, e2);
+                const float2 l = add2(lo2[k >> 1], add2(e2, add2(e, add2(y2, y3))));
+                const float2 hs = add2(h, l);
+                lo2[k >> 1] = sub2(l, sub2(hs, h));
+                hi2[k >> 1] = hs;
               }
-              float s, e, h, e2;
-              two_sum(x[c] * f, y1 * f, s, e);
-              two_sum(hi[k], s, h, e2);
-              const float l = lo[k] + (e2 + (e + (y2 * f + y3 * f)));
-              const float hs = h + l;
-              lo[k] = l - (hs - h);
-              hi[k] = hs;
             }
           }
           asm volatile("tcgen05.fence::before_thread_sync;");
@@ -549,10 +561,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int ex = er + cexp[jb.csc + cc] - shift;
             const int64_t o = jb.out_off + r + (int64_t)cc * jb.ld;
             if (MODE == MODE_T) {
-              Th[o] = ldexp_f(hi[c], ex);
-              Tl[o] = ldexp_f(lo[c], ex);
+              Th[o] = ldexp_f((c & 1) ? hi2[c >> 1].y : hi2[c >> 1].x, ex);
+              Tl[o] = ldexp_f((c & 1) ? lo2[c >> 1].y : lo2[c >> 1].x, ex);
             } else {
-              F[o] += ldexp((double)hi[c] + (double)lo[c], ex);
+              F[o] += ldexp((double)((c & 1) ? hi2[c >> 1].y : hi2[c >> 1].x) +
+                                (double)((c & 1) ? lo2[c >> 1].y : lo2[c >> 1].x),
+                            ex);
             }
           }
         }
