@@ -184,7 +184,9 @@ def main():
     ap.add_argument("--prec", default="split", choices=["fp64", "split"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--slices", type=int, default=0, help="BF16 slices per operand (0: library default)")
+    ap.add_argument("--slices", type=int, default=0,
+                    help="BF16 slices per operand (0: picked by the library's autotuner)")
+    ap.add_argument("--split-tol", type=float, default=3e-11, help="autotuner tolerance vs six slices")
     ap.add_argument("--t-budget-mb", type=int, default=0, help="device MB for one term chunk (0: default)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -210,8 +212,10 @@ def main():
     prec = P.SU2_SPLIT_BF16 if args.prec == "split" else P.SU2_FP64
     ctx = P.Context(local, stream=stream)
     t0 = time.time()
-    sec, env = workload.build(ctx, cfg, prepare_split=(prec == P.SU2_SPLIT_BF16), n_slices=args.slices,
-                              t_budget_bytes=args.t_budget_mb << 20)
+    split = prec == P.SU2_SPLIT_BF16
+    tune = split and args.slices == 0
+    sec, env = workload.build(ctx, cfg, prepare_split=split, n_slices=args.slices,
+                              t_budget_bytes=args.t_budget_mb << 20, autotune=tune, split_tol=args.split_tol)
     build_s = time.time() - t0
     n = sec.psi_len
     psi = torch.from_numpy(synth.gaussian_psi(n, synth.psi_seed(cfg))).to(dev)
@@ -310,6 +314,9 @@ def main():
                        "prec": "fp64" if prec == P.SU2_FP64 else
                        "bf16 slices on tcgen05, fp32 accumulate (exact per 192-K chunk), float-float/fp64 recombine",
                        "psi_len": n, "terms": info["n_terms"], "tasks": info["n_tasks"],
+                       "slices": info["split_slices"] if split else None,
+                       "stage_k16": info["split_stage_k"] if split else None,
+                       "autotuned": tune,
                        "l2": "flushed between steps (256 MB write)"},
             "value_u1_equiv": value * info["r_d"],
             "flops_su2_per_step": flops,

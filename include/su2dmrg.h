@@ -93,6 +93,15 @@ typedef struct {
                               one term chunk (0: library default)           */
   int32_t n_slices;        /* BF16 slices per operand, 2..6 (0: default 5)  */
   int32_t prepare_split;   /* 1: also build the split-precision arenas      */
+  int32_t autotune;        /* 1: build the split arenas with the slice count
+                              and stage depth picked by measurement on this
+                              environment (n_slices is ignored): the
+                              smallest S whose H.psi on a seeded vector
+                              differs from the S = 6 result by <= split_tol
+                              (relative 2-norm), then the fastest valid
+                              stage depth.  Costs about a dozen split H.psi
+                              and five slab builds.  Not in the paper.     */
+  double split_tol;        /* autotune tolerance (0: 3e-11)                 */
 } su2_env_opts;
 
 typedef struct {
@@ -103,6 +112,11 @@ typedef struct {
   double flops_u1_equiv;   /* flops_su2 * R_D, R_D = D_U(1)^eff / D        */
   double r_d;              /* D_U(1)^eff / D of the left bond              */
   double env_bytes;        /* FP64 bytes of all operator blocks            */
+  int32_t split_slices;    /* slices of the prepared split path (0: none)  */
+  int32_t split_stage_k;   /* 16-K steps per pipeline stage of the split GEMM */
+  double split_err_est;    /* autotune: relative difference of the chosen
+                              S to S = 6 on the test vector (-1: not
+                              measured)                                    */
 } su2_env_info;
 
 typedef struct {

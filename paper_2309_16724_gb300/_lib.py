@@ -49,14 +49,16 @@ class Hamiltonian(C.Structure):
 
 
 class EnvOpts(C.Structure):
-    _fields_ = [("t_budget_bytes", C.c_int64), ("n_slices", C.c_int32), ("prepare_split", C.c_int32)]
+    _fields_ = [("t_budget_bytes", C.c_int64), ("n_slices", C.c_int32), ("prepare_split", C.c_int32),
+                ("autotune", C.c_int32), ("split_tol", C.c_double)]
 
 
 class EnvInfo(C.Structure):
     _fields_ = [("psi_len", C.c_int64), ("n_blocks", C.c_int64), ("n_terms", C.c_int64),
                 ("n_tasks", C.c_int64), ("n_k1", C.c_int64), ("n_chunks", C.c_int64),
                 ("flops_su2", C.c_double), ("flops_u1_equiv", C.c_double), ("r_d", C.c_double),
-                ("env_bytes", C.c_double)]
+                ("env_bytes", C.c_double), ("split_slices", C.c_int32), ("split_stage_k", C.c_int32),
+                ("split_err_est", C.c_double)]
 
 
 class DavOpts(C.Structure):
@@ -220,12 +222,13 @@ class Environment:
     """su2_build_environment: operator-table, block operators, C~ table, tasks."""
 
     def __init__(self, ctx: Context, sectors: Sectors, model, left_chain, right_chain, n_left=0, n_right=0,
-                 J=1.0, seed=0, t_budget_bytes=0, n_slices=0, prepare_split=False):
+                 J=1.0, seed=0, t_budget_bytes=0, n_slices=0, prepare_split=False, autotune=False,
+                 split_tol=0.0):
         self.ctx = ctx
         H = Hamiltonian(model, n_left, n_right, J, seed)
         lc, keep1 = _chain(left_chain)
         rc_, keep2 = _chain(right_chain)
-        opts = EnvOpts(t_budget_bytes, n_slices, 1 if prepare_split else 0)
+        opts = EnvOpts(t_budget_bytes, n_slices, 1 if prepare_split else 0, 1 if autotune else 0, split_tol)
         h = C.c_void_p()
         ctx.check(lib().su2_build_environment(ctx.h, C.byref(H), C.byref(lc), C.byref(rc_), sectors.h,
                                               C.byref(opts), C.byref(h)))

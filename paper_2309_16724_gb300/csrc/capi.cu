@@ -31,6 +31,7 @@ void dav_restart(cudaStream_t, double*, double*, int64_t, const double*, int, do
 void dav_append(cudaStream_t, double*, int64_t, int*, const double*, const double*);
 // split-precision path (heff_split.cu)
 int split_prepare(su2_env* env, int n_slices, std::string& err);
+int split_autotune(su2_env* env, double tol, std::string& err);
 int generate_side(const SideOps& so, double* d_arena, cudaStream_t s);
 int split_apply(su2_env* env, const double* psi, double* F, std::string& err);
 void split_free(su2_env* env);
@@ -440,9 +441,10 @@ int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond
     if (!rc) rc = upload(ctx, &env->dk2t, env->k2t);
     if (!rc) rc = upload(ctx, &env->ddj, env->dj);
     if (!rc) rc = upload(ctx, &env->ddt, env->dt);
-    if (!rc && opts && opts->prepare_split) {
+    if (!rc && opts && (opts->prepare_split || opts->autotune)) {
       std::string err;
-      rc = split_prepare(env, opts->n_slices > 0 ? opts->n_slices : 5, err);
+      if (opts->autotune) rc = split_autotune(env, opts->split_tol > 0 ? opts->split_tol : 3e-11, err);
+      else rc = split_prepare(env, opts->n_slices > 0 ? opts->n_slices : 5, err);
       if (rc) fail(ctx, rc, err);
     }
     if (rc) {

@@ -72,6 +72,7 @@ struct SChunk {
 
 struct SplitState {
   int S = 5;
+  int sk = 2;  // 16-K steps per pipeline stage (a tile-shape parameter of the split GEMM)
   // slabs
   unsigned char *dA = nullptr, *dD = nullptr, *dE = nullptr, *dTP = nullptr;
   int64_t a_bytes = 0, d_bytes = 0, e_bytes = 0, tp_bytes = 0;
@@ -422,7 +423,7 @@ int exp_host(double x) {
 
 // the stripe GEMM instantiated for each mode and slice count
 using GemmFn = void (*)(const sp::Job*, int, const sp::Item*, const unsigned char*, const unsigned char*, const int*,
-                        const int*, int, float*, float*, double*, int*, int*, sp::TaskScale);
+                        const int*, int, float*, float*, double*, int*, int*, sp::TaskScale, int);
 GemmFn gemm_fn(int mode, int S) {
   static const GemmFn t[2][sp::kMaxS - 1] = {
       {sp::split_gemm_kernel<sp::MODE_T, 2>, sp::split_gemm_kernel<sp::MODE_T, 3>, sp::split_gemm_kernel<sp::MODE_T, 4>,
@@ -436,17 +437,23 @@ void launch_gemm(int mode, cudaStream_t s, SplitState* st, const Job* jobs, int 
                  const unsigned char* A, const unsigned char* B, const int* rexp, const int* cexp, float* Th,
                  float* Tl, double* F, sp::TaskScale ts) {
   if (njobs <= 0) return;
-  const int smem = sp::smem_bytes_of(st->S);
+  // only the stages in use: the rest of the SM's 256 KB stays L1 (the drain's
+  // spills and the job / item / exponent loads; launching with the maximum
+  // measured 17 % slower K2)
+  const int smem = sp::stages_of(st->S, st->sk) * sp::stage_bytes_of(st->S, st->sk) + 1024;
   const int grid = std::min(njobs, st->n_sms);
   cudaMemsetAsync(st->d_counter, 0, sizeof(int), s);
   gemm_fn(mode, st->S)<<<grid, sp::kThreads, smem, s>>>(jobs, njobs, items, A, B, rexp, cexp, 2 * sp::kLead, Th, Tl, F,
-                                                        st->d_status, st->d_counter, ts);
+                                                        st->d_status, st->d_counter, ts, st->sk);
 }
 
 }  // namespace
 
 
 int split_prepare(su2_env* env, int S, std::string& err) {
+  env->info.split_slices = S;
+  env->info.split_stage_k = 2;
+  env->info.split_err_est = -1.0;
   if (S < 2 || S > sp::kMaxS) {
     err = "n_slices must be in [2, 6]";
     return SU2_EINVAL;
@@ -457,7 +464,7 @@ int split_prepare(su2_env* env, int S, std::string& err) {
   cudaDeviceProp prop;
   cudaGetDeviceProperties(&prop, env->ctx->device);
   st->n_sms = prop.multiProcessorCount;
-  const int smem = sp::smem_bytes_of(S);
+  const int smem = sp::kSmemMax;
   if (cudaFuncSetAttribute((const void*)gemm_fn(sp::MODE_T, S), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
           cudaSuccess ||
       cudaFuncSetAttribute((const void*)gemm_fn(sp::MODE_F, S), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
@@ -848,6 +855,107 @@ int split_apply(su2_env* env, const double* psi, double* F, std::string& err) {
     return SU2_ECUDA;
   }
   return SU2_OK;
+}
+
+void split_free(su2_env* env);
+
+// Autotuner of the split path.  The reference is H.psi with S = 6 slices on a
+// seeded test vector (its error, ~1e-12, is far below any useful tolerance);
+// the slice count is the smallest S in 2..5 whose relative difference to it is
+// <= tol (else 6); the stage depth is then the fastest valid sk in
+// {1, 2, 3, 4, 6} (min of two timed applies after one warm-up).  Leaves the
+// environment prepared with the choice and records it in env->info.
+int split_autotune(su2_env* env, double tol, std::string& err) {
+  const int64_t n = env->psi_len;
+  cudaStream_t s = env->ctx->stream;
+  std::vector<double> hpsi(size_t(std::max<int64_t>(n, 1))), href(hpsi.size()), hout(hpsi.size());
+  uint64_t x = 0x5eed5eedULL;
+  for (auto& v : hpsi) {  // SplitMix64, uniform in [-1, 1)
+    uint64_t z = (x += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    v = double(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+  double *dpsi = nullptr, *dout = nullptr;
+  int rc = dalloc(&dpsi, hpsi.size(), err);
+  if (!rc) rc = dalloc(&dout, hpsi.size(), err);
+  auto run = [&](std::vector<double>* host) -> int {
+    int r = split_apply(env, dpsi, dout, err);
+    if (!r && host && cudaMemcpyAsync(host->data(), dout, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      r = SU2_ECUDA;
+    if (!r && cudaStreamSynchronize(s) != cudaSuccess) r = SU2_ECUDA;
+    if (r && err.empty()) err = "autotune: H.psi failed";
+    return r;
+  };
+  auto reprep = [&](int S) -> int {
+    split_free(env);
+    return split_prepare(env, S, err);
+  };
+  if (!rc && cudaMemcpy(dpsi, hpsi.data(), size_t(n) * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    err = "autotune: upload failed";
+    rc = SU2_ECUDA;
+  }
+  if (!rc) rc = reprep(6);
+  if (!rc) rc = run(&href);
+  double nref = 0.0;
+  for (int64_t i = 0; i < n; ++i) nref += href[i] * href[i];
+  nref = std::sqrt(nref);
+  int chosen = 6;
+  double chosen_err = 0.0;
+  for (int S = 2; S <= 5 && !rc; ++S) {
+    rc = reprep(S);
+    if (!rc) rc = run(&hout);
+    if (rc) break;
+    double d = 0.0;
+    for (int64_t i = 0; i < n; ++i) d += (hout[i] - href[i]) * (hout[i] - href[i]);
+    const double e = nref > 0 ? std::sqrt(d) / nref : 0.0;
+    if (e <= tol) {
+      chosen = S;
+      chosen_err = e;
+      break;
+    }
+  }
+  if (!rc && chosen == 6) rc = reprep(6);
+  int best_sk = 2;
+  float best_ms = 1e30f;
+  if (!rc) {
+    auto* st = static_cast<SplitState*>(env->split);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int sk : {1, 2, 3, 4, 6}) {
+      if (!sp::stage_k_valid(chosen, sk)) continue;
+      st->sk = sk;
+      if ((rc = run(nullptr))) break;
+      float ms = 1e30f;
+      for (int rep = 0; rep < 2 && !rc; ++rep) {
+        cudaEventRecord(e0, s);
+        rc = split_apply(env, dpsi, dout, err);
+        cudaEventRecord(e1, s);
+        if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = SU2_ECUDA;
+        float t = 0.f;
+        if (!rc) cudaEventElapsedTime(&t, e0, e1);
+        ms = std::min(ms, t);
+      }
+      if (rc) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_sk = sk;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    st->sk = best_sk;
+  }
+  cudaFree(dpsi);
+  cudaFree(dout);
+  if (!rc) {
+    env->info.split_slices = chosen;
+    env->info.split_stage_k = best_sk;
+    env->info.split_err_est = chosen == 6 ? -1.0 : chosen_err;
+  }
+  return rc;
 }
 
 void split_free(su2_env* env) {

@@ -59,21 +59,26 @@ constexpr int kBufCols = 4 * kCols;  // TMEM columns of one accumulator buffer (
 constexpr int kDrainCols = kCols / 4;  // columns per drain thread (16 drain warps: 4 lane quarters x 4 groups)
 constexpr int kGroup = kDrainCols >= 32 ? 4 : 8;  // columns per TMEM load group
 constexpr int kMaxS = 6;
-constexpr int kStepK = 2;            // 16-K steps per pipeline stage (one barrier wait per 2 S(S+1)/2 MMAs)
-constexpr int kChunkSteps = 12;      // 16-K steps per exact drain chunk (192 K), a multiple of kStepK
+constexpr int kChunkSteps = 12;      // 16-K steps per exact drain chunk (192 K)
 constexpr int kLead = 8;             // leading slice |q_0| <= 2^kLead, the others |q_i| <= 128
 constexpr int kRing = 4;             // job ring slots
 constexpr int kMaxStages = 8;
-// bytes of one pipeline stage: kStepK x (S A slices of 128 rows + S B slices of 64 rows)
-__host__ __device__ constexpr int stage_bytes_of(int S) { return kStepK * S * (kSub + kSubB); }
+// A pipeline stage holds sk consecutive 16-K steps (sk divides kChunkSteps;
+// a tile-shape parameter chosen by the autotuner): S A slices of up to 128
+// rows and S B slices of up to kCols rows per step
+__host__ __device__ constexpr int stage_bytes_of(int S, int sk) { return sk * S * (kSub + kSubB); }
 // stages that fit in 220 KB of shared memory (at most kMaxStages)
-__host__ __device__ constexpr int stages_of(int S) {
-  return (225280 / stage_bytes_of(S)) < kMaxStages ? (225280 / stage_bytes_of(S)) : kMaxStages;
+__host__ __device__ constexpr int stages_of(int S, int sk) {
+  return (225280 / stage_bytes_of(S, sk)) < kMaxStages ? (225280 / stage_bytes_of(S, sk)) : kMaxStages;
 }
-__host__ __device__ constexpr int smem_bytes_of(int S) { return stages_of(S) * stage_bytes_of(S) + 1024; }
+constexpr int kSmemMax = 225280 + 1024;  // largest dynamic shared memory of a launch (+ 1 KB for alignment)
+__host__ __device__ constexpr bool stage_k_valid(int S, int sk) {
+  return sk >= 1 && sk <= 6 && kChunkSteps % sk == 0 && stages_of(S, sk) >= 2;
+}
 // per-stage word the producer leaves for the MMA issuer (no global loads on
-// the issue path); bits 8..11: MMA N / 16, bits 12..15: stored A rows / 16
-enum : uint32_t { kMetaFirst = 1, kMetaLast = 2, kMetaTwo = 4, kMetaEnd = 8 };
+// the issue path); bits 4..7: 16-K steps in the stage, bits 8..11: MMA N / 16,
+// bits 12..15: stored A rows / 16
+enum : uint32_t { kMetaFirst = 1, kMetaLast = 2, kMetaEnd = 8 };
 
 // Compact slab layout: row tile tr of an R-row operand stores only its rows,
 // rounded up to 16; its (16-K step k, slice i) sub-tile sits at
@@ -271,11 +276,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                       const unsigned char* __restrict__ Aslab, const unsigned char* __restrict__ Bslab,
                       const int* __restrict__ rexp, const int* __restrict__ cexp, int shift,
                       float* __restrict__ Th, float* __restrict__ Tl, double* __restrict__ F, int* __restrict__ status,
-                      int* __restrict__ job_counter, TaskScale ts) {
+                      int* __restrict__ job_counter, TaskScale ts, int sk) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  constexpr int stage_bytes = stage_bytes_of(S);
-  constexpr int NS = stages_of(S);
+  const int stage_bytes = stage_bytes_of(S, sk);
+  const int NS = stages_of(S, sk);
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], accf_bar[2], acce_bar[2], done_bar;
   __shared__ __align__(8) uint64_t jq_full[kRing], jq_empty[kRing];
   __shared__ int job_ring[kRing];
@@ -336,17 +341,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t nmeta = ((uint32_t)(jb.nmma >> 4) << 8) | ((uint32_t)(arows >> 4) << 12);
         for (int it = jb.i0; it < jb.i1 && ok; ++it) {
           const Item item = items[it];
-          const int nstage = (item.nst + kStepK - 1) / kStepK;
+          const int nstage = (item.nst + sk - 1) / sk;
           for (int ks = 0; ks < nstage; ++ks) {
             if (!mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1, &abort_flag)) {
               ok = false;
               break;
             }
-            const int k16 = ks * kStepK;  // first 16-K step of the stage within the item
-            const int nk = min(kStepK, item.nst - k16);
-            uint32_t m = nmeta | (nk == 2 ? kMetaTwo : 0u);
+            const int k16 = ks * sk;  // first 16-K step of the stage within the item
+            const int nk = min(sk, item.nst - k16);
+            uint32_t m = nmeta | ((uint32_t)nk << 4);
             if (k16 % kChunkSteps == 0) m |= kMetaFirst;
-            if ((k16 + kStepK) % kChunkSteps == 0 || ks == nstage - 1) m |= kMetaLast;
+            if ((k16 + sk) % kChunkSteps == 0 || ks == nstage - 1) m |= kMetaLast;
             stage_meta[st] = m;
             const uint32_t fb = smem_u32(&full_bar[st]);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
@@ -362,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 : "memory");
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    dst + kStepK * S * kSub),
+                    dst + sk * S * kSub),
                 "l"(srcB), "r"(nk * S * bbytes), "r"(fb)
                 : "memory");
             ++nissued;
@@ -433,12 +438,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t idesc = idesc_n((int)n16 * 16);
         const uint32_t bs16 = n16 * 32, as16 = a16 * 32;  // sub-tile strides in 16-byte units (rows * 32 / 16)
         const uint32_t sa = sbase + st * stage_bytes;
-        const uint64_t da = make_desc(sa), db = make_desc(sa + kStepK * S * kSub);
+        const uint64_t da = make_desc(sa), db = make_desc(sa + sk * S * kSub);
         const uint32_t tb = tmem + buf * kBufCols;
+        const int nk = (int)((m >> 4) & 0xf);
         if (m & kMetaFirst) issue_stage<S, true>(tb, da, db, as16, bs16, idesc);
         else issue_stage<S, false>(tb, da, db, as16, bs16, idesc);
-        if (m & kMetaTwo)
-          issue_stage<S, false>(tb, da + (uint64_t)(S * as16), db + (uint64_t)(S * bs16), as16, bs16, idesc);
+        for (int kk = 1; kk < nk; ++kk)
+          issue_stage<S, false>(tb, da + (uint64_t)(kk * S * as16), db + (uint64_t)(kk * S * bs16), as16, bs16, idesc);
         mma_commit(smem_u32(&empty_bar[st]));
         if (m & kMetaLast) {
           mma_commit(smem_u32(&accf_bar[buf]));

@@ -81,3 +81,29 @@ def test_slice_count_controls_error(ctx, S, tol):
     G = run(ctx, env, psi, P.SU2_SPLIT_BF16)
     H = run(ctx, env, psi, P.SU2_FP64)
     assert rel_err(G, H) <= tol
+
+
+@pytest.mark.parametrize("tol", [1e-5, 3e-11, 1e-14])
+def test_autotune_picks_slices_and_stage_depth(ctx, tol):
+    """The autotuner's slice count is the smallest whose H.psi differs from the
+    six-slice one by <= tol; the prepared path then meets that bound against
+    the FP64 path (up to the six-slice error itself), and its stage depth is a
+    valid one."""
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    cfg = CASES[2]
+    sec, env = workload.build(ctx, cfg, autotune=True, split_tol=tol)
+    S, sk, est = env.info["split_slices"], env.info["split_stage_k"], env.info["split_err_est"]
+    assert 2 <= S <= 6 and sk in (1, 2, 3, 4, 6)
+    if S < 6:
+        assert 0.0 <= est <= tol
+    else:
+        assert est == -1.0
+    if tol >= 1e-5:
+        assert S <= 4
+    if tol <= 1e-14:
+        assert S == 6
+    psi = synth.gaussian_psi(sec.psi_len, 6)
+    G = run(ctx, env, psi, P.SU2_SPLIT_BF16)
+    H = run(ctx, env, psi, P.SU2_FP64)
+    assert rel_err(G, H) <= max(10 * tol, 1e-11)
