@@ -97,7 +97,6 @@ struct SplitState {
   Job *d_k1j = nullptr, *d_k2j = nullptr;
   Item *d_k1i = nullptr, *d_k2i = nullptr;
   Source* d_src = nullptr;
-  int64_t* d_colbase = nullptr;
   TPTask* d_tpt = nullptr;
   TPUnit* d_tpu = nullptr;
   int* d_status = nullptr;
@@ -229,29 +228,22 @@ __global__ void psi_ff_kernel(const double* __restrict__ x, float* __restrict__ 
   }
 }
 
-// column exponents of the float-float sources: one warp per (source, column);
-// colbase[i] = first column of source i (chunk-local, = its cexp offset)
-__global__ void cexp_kernel(const Source* __restrict__ src, int nsrc, const int64_t* __restrict__ colbase,
-                            const float* __restrict__ Th, const float* __restrict__ Ph, int* __restrict__ cexp,
-                            int64_t total_cols) {
-  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= total_cols) return;
-  // locate the source by binary search over colbase
-  int lo = 0, hi = nsrc - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (colbase[mid] <= w) lo = mid;
-    else hi = mid - 1;
-  }
-  const Source s = src[lo];
-  const int c = int(w - colbase[lo]);
-  const float* h = (s.sel ? Ph : Th) + s.off + int64_t(c) * s.rows;
-  float m = 0.f;
-  for (int r = lane; r < s.rows; r += 32) m = fmaxf(m, fabsf(h[r]));
+// column exponents of the float-float sources: one CTA per source, its warps
+// take the columns in turn and their lanes the rows (contiguous in the
+// column-major block)
+__global__ void cexp_kernel(const Source* __restrict__ src, const float* __restrict__ Th,
+                            const float* __restrict__ Ph, int* __restrict__ cexp) {
+  const Source s = src[blockIdx.x];
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const float* base = (s.sel ? Ph : Th) + s.off;
+  for (int c = threadIdx.x >> 5; c < s.cols; c += nw) {
+    const float* h = base + int64_t(c) * s.rows;
+    float m = 0.f;
+    for (int r = lane; r < s.rows; r += 32) m = fmaxf(m, fabsf(h[r]));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) cexp[s.cexp_off + c] = exp_of_f(m);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) cexp[s.cexp_off + c] = exp_of_f(m);
+  }
 }
 
 __global__ void fill_kernel(int* __restrict__ p, int64_t n, int v) {
@@ -746,11 +738,6 @@ int split_prepare(su2_env* env, int S, std::string& err) {
   if (!rc2) rc2 = dalloc(&st->d_scale, size_t(std::max<int64_t>(st->n_scale, 1)), err);
   if (!rc2) rc2 = dput(&st->d_scoff, st->scoff, err);
   if (rc2) return rc2;
-  std::vector<int64_t> colbase(st->src.size());
-  for (size_t q = 0; q < st->src.size(); ++q) colbase[q] = st->src[q].cexp_off;
-  int64_t* d_colbase = nullptr;
-  if ((rc2 = dput(&d_colbase, colbase, err))) return rc2;
-  st->d_colbase = d_colbase;
   // ---------------------------------------------------------- operator slabs (once per site)
   cudaStream_t s = env->ctx->stream;
   const int na = int(st->aunit.size()), nd = int(st->dunit.size());
@@ -818,13 +805,7 @@ int split_apply(su2_env* env, const double* psi, double* F, std::string& err) {
     SPLIT_CHECK("K1 split GEMM");
     slot = pf.begin(s, 2, 0.0);
     const int nsrc = int(c.src1 - c.src0);
-    int64_t cols = 0;
-    if (nsrc) cols = st->src[c.src1 - 1].cexp_off + st->src[c.src1 - 1].cols;
-    if (cols > 0) {
-      const int64_t threads = cols * 32;
-      cexp_kernel<<<unsigned((threads + 255) / 256), 256, 0, s>>>(st->d_src + c.src0, nsrc, st->d_colbase + c.src0,
-                                                                  st->dTh, st->dPh, st->d_cexp, cols);
-    }
+    if (nsrc > 0) cexp_kernel<<<unsigned(nsrc), 256, 0, s>>>(st->d_src + c.src0, st->dTh, st->dPh, st->d_cexp);
     SPLIT_CHECK("column exponents");
     fill_kernel<<<256, 256, 0, s>>>(st->d_gamma, st->n_gamma, kSentinel);
     const int ntp = int(c.tp1 - c.tp0);
@@ -964,7 +945,7 @@ void split_free(su2_env* env) {
   void* ps[] = {st->dA, st->dD, st->dE, st->dTP, st->d_adesc, st->d_ddesc, st->d_edesc, st->d_aunit, st->d_dunit,
                 st->d_eunit, st->d_rho, st->d_aown, st->d_delta, st->d_zeta, st->d_eps, st->d_gamma, st->d_cexp,
                 st->dTh, st->dTl, st->dPh, st->dPl, st->d_k1j, st->d_k2j, st->d_k1i, st->d_k2i, st->d_src,
-                st->d_tpt, st->d_tpu, st->d_colbase, st->d_counter, st->d_phi,
+                st->d_tpt, st->d_tpu, st->d_counter, st->d_phi,
                 st->d_scale, st->d_scoff};
   for (void* p : ps) cudaFree(p);
   delete st;
