@@ -65,6 +65,25 @@ struct TPTask {
 };
 struct TPUnit { int32_t task, tr, ks, pad; };
 
+// Small-task class: tasks whose four dimensions (m, k1, k2, n) are all at
+// most kSmallDim run in FP64 on CUDA cores instead of the split tensor path
+// (no slabs, no MMA tile padding, no drain chunk).  One warp per segment of
+// up to kSmallSeg tasks of one output block writes a partial block; a second
+// pass adds each block's partials into F in segment order (deterministic).
+constexpr int kSmallDim = 16;
+constexpr int kSmallSeg = 32;
+struct SmallTask {
+  int64_t e_off, a_off, d_off;  // psi block, left / right operator block (-1: identity)
+  int32_t m, k1, k2, n;
+  double v;
+};
+struct SmallOut {               // an output block with small tasks
+  int64_t f_off;
+  int32_t m, n;
+  int32_t s0, s1;               // its segments
+};
+struct SmallSeg { int32_t t0, t1; };  // a segment's tasks (one output block)
+
 struct SChunk {
   int64_t k1_j0, k1_j1, src0, src1, tp0, tp1, tpu0, tpu1, k2_j0, k2_j1;
   double k1_flops, k2_flops;
@@ -72,6 +91,13 @@ struct SChunk {
 
 struct SplitState {
   int S = 5;
+  std::vector<SmallTask> small;
+  std::vector<SmallOut> small_out;
+  std::vector<SmallSeg> small_seg;
+  SmallTask* d_small = nullptr;
+  SmallOut* d_small_out = nullptr;
+  SmallSeg* d_small_seg = nullptr;
+  double* d_small_part = nullptr;  // kSmallDim^2 doubles per segment
   int sk = 2;  // 16-K steps per pipeline stage (a tile-shape parameter of the split GEMM)
   // slabs
   unsigned char *dA = nullptr, *dD = nullptr, *dE = nullptr, *dTP = nullptr;
@@ -357,6 +383,84 @@ __global__ void slab_tprime_kernel(const TPTask* __restrict__ tasks, const TPUni
   }
 }
 
+// FP64 partials of the small-task class: warp w sums v A E D^T over the
+// tasks of segment w, in task order (T = E D^T, k1 x n, then A T, m x n; the
+// operands staged in shared memory), and writes the m x n partial to
+// part[w * kSmallDim^2 ...]; lane l owns the elements l, l + 32, ...
+__global__ void __launch_bounds__(128) small_tasks_kernel(const SmallSeg* __restrict__ segs, int nseg,
+                                                          const SmallTask* __restrict__ tasks,
+                                                          const double* __restrict__ psi,
+                                                          const double* __restrict__ Lop,
+                                                          const double* __restrict__ Rop, double* __restrict__ part) {
+  constexpr int kD = kSmallDim * kSmallDim;
+  __shared__ double sm[4][4][kD];  // per warp: E, D, A, T
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = blockIdx.x * 4 + wl;
+  if (w >= nseg) return;
+  double* E = sm[wl][0];
+  double* D = sm[wl][1];
+  double* A = sm[wl][2];
+  double* T = sm[wl][3];
+  const SmallSeg g = segs[w];
+  double acc[kD / 32];
+#pragma unroll
+  for (int q = 0; q < kD / 32; ++q) acc[q] = 0.0;
+  for (int ti = g.t0; ti < g.t1; ++ti) {
+    const SmallTask t = tasks[ti];
+    for (int i = lane; i < t.k1 * t.k2; i += 32) E[i] = psi[t.e_off + i];
+    if (t.d_off >= 0)
+      for (int i = lane; i < t.n * t.k2; i += 32) D[i] = Rop[t.d_off + i];
+    if (t.a_off >= 0)
+      for (int i = lane; i < t.m * t.k1; i += 32) A[i] = Lop[t.a_off + i];
+    __syncwarp();
+    // T = E D^T (identity D: T = E)
+    for (int i = lane; i < t.k1 * t.n; i += 32) {
+      const int r = i % t.k1, c = i / t.k1;
+      double x = 0.0;
+      if (t.d_off >= 0) {
+        for (int k = 0; k < t.k2; ++k) x = fma(E[r + k * t.k1], D[c + k * t.n], x);
+      } else {
+        x = E[i];
+      }
+      T[i] = x;
+    }
+    __syncwarp();
+    // += v A T (identity A: += v T)
+#pragma unroll
+    for (int q = 0; q < kD / 32; ++q) {
+      const int i = lane + 32 * q;
+      if (i < t.m * t.n) {
+        const int r = i % t.m, c = i / t.m;
+        double x = 0.0;
+        if (t.a_off >= 0) {
+          for (int k = 0; k < t.k1; ++k) x = fma(A[r + k * t.m], T[k + c * t.k1], x);
+        } else {
+          x = T[r + c * t.k1];
+        }
+        acc[q] = fma(t.v, x, acc[q]);
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int q = 0; q < kD / 32; ++q) part[int64_t(w) * kD + lane + 32 * q] = acc[q];
+}
+
+// F += the partials of each output block's segments, in segment order: one
+// warp per output block
+__global__ void small_reduce_kernel(const SmallOut* __restrict__ outs, int nout, const double* __restrict__ part,
+                                    double* __restrict__ F) {
+  constexpr int kD = kSmallDim * kSmallDim;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= nout) return;
+  const SmallOut o = outs[w];
+  for (int i = lane; i < o.m * o.n; i += 32) {
+    double x = 0.0;
+    for (int sg = o.s0; sg < o.s1; ++sg) x += part[int64_t(sg) * kD + i];
+    F[o.f_off + i] += x;
+  }
+}
+
 template <class T>
 int dalloc(T** p, size_t n, std::string& err) {
   *p = nullptr;
@@ -537,7 +641,33 @@ int split_prepare(su2_env* env, int S, std::string& err) {
   // ---------------------------------------------------------- chunk plan
   const int nterms = int(env->table.terms.size());
   std::vector<std::vector<int64_t>> by_term(nterms);
-  for (int64_t i = 0; i < int64_t(env->tasks.size()); ++i) by_term[env->tasks[i].term].push_back(i);
+  // small-task class, in task order (sorted by output block)
+  auto is_small = [&](const Task& t) {
+    const Block& Fb = B[t.f];
+    const Block& Eb = B[t.e];
+    return std::max(std::max(Fb.rows, Fb.cols), std::max(Eb.rows, Eb.cols)) <= kSmallDim;
+  };
+  for (int64_t i = 0; i < int64_t(env->tasks.size()); ++i) {
+    const Task& t = env->tasks[i];
+    if (!is_small(t)) continue;
+    const Block& Fb = B[t.f];
+    const Block& Eb = B[t.e];
+    const int32_t ti = int32_t(st->small.size());
+    if (st->small_out.empty() || st->small_out.back().f_off != Fb.offset) {
+      const int32_t sg = int32_t(st->small_seg.size());
+      st->small_out.push_back(SmallOut{Fb.offset, Fb.rows, Fb.cols, sg, sg});
+    }
+    SmallOut& so = st->small_out.back();
+    if (so.s1 == so.s0 || st->small_seg.back().t1 - st->small_seg.back().t0 == kSmallSeg) {
+      st->small_seg.push_back(SmallSeg{ti, ti});
+      so.s1 += 1;
+    }
+    st->small.push_back(SmallTask{Eb.offset, t.ablk >= 0 ? L.blocks[t.ablk].off : -1,
+                                  t.dblk >= 0 ? R.blocks[t.dblk].off : -1, Fb.rows, Eb.rows, Eb.cols, Fb.cols, t.v});
+    st->small_seg.back().t1 = ti + 1;
+  }
+  for (int64_t i = 0; i < int64_t(env->tasks.size()); ++i)
+    if (!is_small(env->tasks[i])) by_term[env->tasks[i].term].push_back(i);
   int64_t budget = env->split_budget;
   if (budget <= 0) {  // default: a quarter of the free device memory, at most 16 GiB
     size_t fr = 0, tot = 0;
@@ -634,7 +764,7 @@ int split_prepare(su2_env* env, int S, std::string& err) {
       std::vector<int64_t> mine;
       for (; j < nt && env->tasks[j].f == f; ++j) {
         const Task& t = env->tasks[j];
-        if (t.term >= t0 && t.term < t1) mine.push_back(j);
+        if (t.term >= t0 && t.term < t1 && !is_small(t)) mine.push_back(j);
       }
       i = j;
       if (mine.empty()) continue;
@@ -737,6 +867,10 @@ int split_prepare(su2_env* env, int S, std::string& err) {
   if (!rc2) rc2 = dalloc(&st->d_phi, std::max<size_t>(st->tpt.size(), 1), err);
   if (!rc2) rc2 = dalloc(&st->d_scale, size_t(std::max<int64_t>(st->n_scale, 1)), err);
   if (!rc2) rc2 = dput(&st->d_scoff, st->scoff, err);
+  if (!rc2) rc2 = dput(&st->d_small, st->small, err);
+  if (!rc2) rc2 = dput(&st->d_small_out, st->small_out, err);
+  if (!rc2) rc2 = dput(&st->d_small_seg, st->small_seg, err);
+  if (!rc2) rc2 = dalloc(&st->d_small_part, std::max<size_t>(st->small_seg.size(), 1) * kSmallDim * kSmallDim, err);
   if (rc2) return rc2;
   // ---------------------------------------------------------- operator slabs (once per site)
   cudaStream_t s = env->ctx->stream;
@@ -830,6 +964,17 @@ int split_apply(su2_env* env, const double* psi, double* F, std::string& err) {
                 sp::TaskScale{st->d_scale});
     pf.end(s, slot);
     SPLIT_CHECK("K2 split GEMM");
+  }
+  // the small-task class, added after the tensor-core contributions
+  if (!st->small_out.empty()) {
+    pf.count(2);
+    slot = pf.begin(s, 2, 0.0);
+    const int nseg = int(st->small_seg.size()), nout = int(st->small_out.size());
+    small_tasks_kernel<<<unsigned((nseg + 3) / 4), 128, 0, s>>>(st->d_small_seg, nseg, st->d_small, psi, env->dL,
+                                                                 env->dR, st->d_small_part);
+    small_reduce_kernel<<<unsigned((nout + 3) / 4), 128, 0, s>>>(st->d_small_out, nout, st->d_small_part, F);
+    pf.end(s, slot);
+    SPLIT_CHECK("small tasks");
   }
   if (cudaGetLastError() != cudaSuccess) {
     err = "split-precision launch failed";
@@ -946,7 +1091,7 @@ void split_free(su2_env* env) {
                 st->d_eunit, st->d_rho, st->d_aown, st->d_delta, st->d_zeta, st->d_eps, st->d_gamma, st->d_cexp,
                 st->dTh, st->dTl, st->dPh, st->dPl, st->d_k1j, st->d_k2j, st->d_k1i, st->d_k2i, st->d_src,
                 st->d_tpt, st->d_tpu, st->d_counter, st->d_phi,
-                st->d_scale, st->d_scoff};
+                st->d_scale, st->d_scoff, st->d_small, st->d_small_out, st->d_small_seg, st->d_small_part};
   for (void* p : ps) cudaFree(p);
   delete st;
   env->split = nullptr;
