@@ -13,6 +13,7 @@ all ranks / max time over ranks ("weak" scaling).
 from __future__ import annotations
 
 import argparse
+import re
 import json
 import os
 import statistics
@@ -29,6 +30,27 @@ import synth  # noqa: E402
 METRIC = "H·ψ TFLOPS/GB300 (SU(2), U(1)-equiv): split-prec vs FP64 at ≤1e-10 rel err"
 DEFAULT_CONFIG = "qc32"
 FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal FP64 rate)
+
+
+def k2_traffic(workload, slices, stage_k):
+    """DRAM bytes per K2 launch from the committed ncu capture, or None when the
+    split sources changed since it was taken or the workload differs."""
+    import hashlib
+    root = os.path.dirname(os.path.abspath(__file__))
+    src = os.path.join(root, "paper_2309_16724_gb300", "csrc")
+    try:
+        txt = open(os.path.join(root, "profiles", "split_gemm_traffic_qc32.md")).read()
+        h = hashlib.sha256()
+        for f in ("split_gemm.cuh", "heff_split.cu"):
+            h.update(open(os.path.join(src, f), "rb").read())
+    except OSError:
+        return None
+    kv = dict(re.findall(r"(\w+): (\S+)", txt.split("Machine-readable", 1)[-1]))
+    if kv.get("sources_sha256_16") != h.hexdigest()[:16]:
+        return None
+    if (kv.get("workload"), kv.get("slices"), kv.get("stage_k16")) != (workload, str(slices), str(stage_k)):
+        return None
+    return float(kv["k2_split_traffic_bytes_per_launch"])
 
 
 def peaks():
@@ -323,7 +345,9 @@ def main():
             "rel_err_vs_fp64": rel_err_fp64,
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
             "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                         "frac": achieved / peak if peak else None, "traffic": None,
+                         "frac": achieved / peak if peak else None,
+                         "traffic": (k2_traffic(cfg.name, info["split_slices"], info["split_stage_k"])
+                                     if name == "k2_split" else None),
                          "kernel": name, "peak_source": peak_note},
             "kernels": {k: {"launches": v[0], "ms": v[1], "flops": v[2]} for k, v in prof.items() if v[0]},
             "gpu_launches": gpu_launches,
