@@ -102,6 +102,16 @@ typedef struct {
                               stage depth.  Costs about a dozen split H.psi
                               and five slab builds.  Not in the paper.     */
   double split_tol;        /* autotune tolerance (0: 3e-11)                 */
+  int32_t shard_rank;      /* term sharding (shard_count > 1): this shard  */
+  int32_t shard_count;     /* keeps the tasks of its share of the operator
+                              terms (longest-processing-time order of their
+                              flops), so its H.psi is a partial F and the
+                              shards' results sum to H.psi.  For a
+                              multi-rank run with one shard per GPU and a
+                              sum-reduction of F.  0 / 0: all terms.  The
+                              paper's own distribution is by GPU task
+                              queues (Sec. III); this is a data-parallel
+                              split of Eq. 2's sum over i.                 */
 } su2_env_opts;
 
 typedef struct {

@@ -50,7 +50,8 @@ class Hamiltonian(C.Structure):
 
 class EnvOpts(C.Structure):
     _fields_ = [("t_budget_bytes", C.c_int64), ("n_slices", C.c_int32), ("prepare_split", C.c_int32),
-                ("autotune", C.c_int32), ("split_tol", C.c_double)]
+                ("autotune", C.c_int32), ("split_tol", C.c_double), ("shard_rank", C.c_int32),
+                ("shard_count", C.c_int32)]
 
 
 class EnvInfo(C.Structure):
@@ -223,12 +224,13 @@ class Environment:
 
     def __init__(self, ctx: Context, sectors: Sectors, model, left_chain, right_chain, n_left=0, n_right=0,
                  J=1.0, seed=0, t_budget_bytes=0, n_slices=0, prepare_split=False, autotune=False,
-                 split_tol=0.0):
+                 split_tol=0.0, shard=(0, 0)):
         self.ctx = ctx
         H = Hamiltonian(model, n_left, n_right, J, seed)
         lc, keep1 = _chain(left_chain)
         rc_, keep2 = _chain(right_chain)
-        opts = EnvOpts(t_budget_bytes, n_slices, 1 if prepare_split else 0, 1 if autotune else 0, split_tol)
+        opts = EnvOpts(t_budget_bytes, n_slices, 1 if prepare_split else 0, 1 if autotune else 0, split_tol,
+                       shard[0], shard[1])
         h = C.c_void_p()
         ctx.check(lib().su2_build_environment(ctx.h, C.byref(H), C.byref(lc), C.byref(rc_), sectors.h,
                                               C.byref(opts), C.byref(h)))

@@ -346,6 +346,35 @@ static void env_free_device(su2_env* e) {
   cudaFree(e->d_out_scratch);
 }
 
+// Term sharding: terms go to shards by longest-processing-time order of
+// their task flops (2(m k1 k2 + m k2 n) per task; ties by term index, then by
+// the lower shard), and shard `rank` keeps the tasks of its terms.  The
+// shards' H.psi sum to the full H.psi.
+void shard_terms(std::vector<Task>& tasks, const std::vector<Block>& blocks, int nterms, int rank, int count) {
+  std::vector<double> cost(size_t(nterms), 0.0);
+  for (const Task& t : tasks) {
+    const Block& F = blocks[t.f];
+    const Block& E = blocks[t.e];
+    cost[t.term] += 2.0 * (double(F.rows) * E.rows * E.cols + double(F.rows) * E.cols * F.cols);
+  }
+  std::vector<int> order(static_cast<size_t>(nterms));
+  for (int i = 0; i < nterms; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<double> load(size_t(count), 0.0);
+  std::vector<int> owner(size_t(nterms), 0);
+  for (int term : order) {
+    int best = 0;
+    for (int r = 1; r < count; ++r)
+      if (load[r] < load[best]) best = r;
+    owner[term] = best;
+    load[best] += cost[term];
+  }
+  std::vector<Task> kept;
+  for (const Task& t : tasks)
+    if (owner[t.term] == rank) kept.push_back(t);
+  tasks.swap(kept);
+}
+
 int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond_chain* lc, const su2_bond_chain* rc,
                           const su2_sectors* S, const su2_env_opts* opts, su2_env** out) {
   if (!ctx || !H || !lc || !rc || !S || !out) return fail(ctx, SU2_EINVAL, "null argument");
@@ -389,6 +418,10 @@ int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond
     std::string err = build_side_ops(env->table, true, lch, *H, env->L, host_values);
     if (err.empty()) err = build_side_ops(env->table, false, rch, *H, env->R, host_values);
     if (err.empty()) err = build_tasks(env->table, S->left, S->right, S->blocks, S->twoS, env->L, env->R, env->tasks);
+    if (err.empty() && opts && opts->shard_count > 1) {
+      if (opts->shard_rank < 0 || opts->shard_rank >= opts->shard_count) err = "shard_rank outside [0, shard_count)";
+      else shard_terms(env->tasks, S->blocks, int(env->table.terms.size()), opts->shard_rank, opts->shard_count);
+    }
     if (!err.empty()) {
       delete env;
       return fail(ctx, SU2_EINVAL, err);
