@@ -106,35 +106,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_cpu_baseline(cfg_name: str, repeats: int, max_seconds: float, flop_budget: float = 4e10):
-    """Times the FP64 oracle (as it stands) on the host in a child process with
-    one BLAS thread.  Small configs: the full H.psi.  Larger ones: a bounded
-    sample of output blocks (whole blocks, every task into them), chosen
-    deterministically across the size range.  Returns (TFLOP/s, cores,
-    sample description, seconds per repeat).  Flops follow the library's
-    definition (K1 counted once per distinct (right block, input block))."""
-    code = f"""
+_ORACLE_WORKER = r"""
 import os, sys, time, json
-sys.path.insert(0, {ROOT!r})
+sys.path.insert(0, ROOT)
 import numpy as np, synth
 from oracle import model, sectors, heff, env
-cfg = synth.CONFIGS[{cfg_name!r}]
+w, W, cfg_name, repeats, budget, warm = (int(sys.argv[1]), int(sys.argv[2]), sys.argv[3], int(sys.argv[4]),
+                                        float(sys.argv[5]), int(sys.argv[6]))
+cfg = synth.CONFIGS[cfg_name]
 left, right = synth.middle_bond_sectors(cfg)
 blocks, n = sectors.build_blocks(left, right, cfg.site_kind, cfg.N, cfg.twoS)
 tab = model.heisenberg_table() if cfg.site_kind == synth.SPIN_HALF else model.qc_skeleton_table(cfg.n_left, cfg.n_right)
-full = n < 1_000_000
-if full:
-    sel = None
-    e = env.build_env(tab, cfg, left, right)
-else:
-    order = sorted(range(len(blocks)), key=lambda f: -blocks[f].rows * blocks[f].cols)
-    sel = set(order[:: max(1, len(order) // 12)][:12])
-    e = env.LazySyntheticEnv(tab, cfg, left, right)
-tasks = heff.build_tasks(tab, left, right, blocks, cfg.twoS, only_f=sel)
-# trim the sample to the flop budget (whole output blocks)
 def work(ts):
-    k1 = {{}}
-    k2 = 0
+    k1, k2 = {}, 0
     for t in ts:
         E, F = blocks[t.e], blocks[t.f]
         if t.D is not None:
@@ -142,36 +126,96 @@ def work(ts):
         if t.A is not None:
             k2 += 2 * F.rows * E.rows * F.cols
     return sum(k1.values()) + k2
-if sel is not None:
-    by_f = {{}}
-    for t in tasks:
+# the same deterministic sample in every worker: the full H.psi of a small
+# config, else whole output blocks spread over the size range, up to W x budget
+# flops; its tasks are shared among the workers, longest first
+if n < 1_000_000:
+    e = env.build_env(tab, cfg, left, right)
+    sample_tasks = heff.build_tasks(tab, left, right, blocks, cfg.twoS)
+    sample = f"full H.psi of {cfg_name} (all tasks) on {W} processes"
+else:
+    order = sorted(range(len(blocks)), key=lambda f: -blocks[f].rows * blocks[f].cols)
+    cand = order[:: max(1, len(order) // (12 * W))][: 12 * W]
+    e = env.LazySyntheticEnv(tab, cfg, left, right)
+    ts_all = heff.build_tasks(tab, left, right, blocks, cfg.twoS, only_f=set(cand))
+    by_f = {}
+    for t in ts_all:
         by_f.setdefault(t.f, []).append(t)
     keep, acc = [], 0
-    for f in sorted(by_f, key=lambda f: -blocks[f].rows * blocks[f].cols):
-        w = work(by_f[f])
-        if keep and acc + w > {flop_budget}:
+    for f in cand:
+        if f not in by_f:
             continue
-        keep.append(f); acc += w
-    tasks = [t for t in tasks if t.f in set(keep)]
-    sample = f"{{len(keep)}} of {{len(blocks)}} output blocks of {cfg_name} (all tasks into them)"
-else:
-    sample = f"full H.psi of {cfg_name} (all tasks)"
-flops = work(tasks)
+        wf = work(by_f[f])
+        if keep and acc + wf > W * budget:
+            continue
+        keep.append(f); acc += wf
+    sample_tasks = [t for f in keep for t in by_f[f]]
+    sample = f"{len(keep)} of {len(blocks)} output blocks of {cfg_name} (all tasks into them) on {W} processes"
+flops = work(sample_tasks)  # the sample's flops (library definition), reported by worker 0 only
+def cost(t):
+    E, F = blocks[t.e], blocks[t.f]
+    return 2 * (F.rows * E.rows * E.cols + F.rows * E.cols * F.cols)
+load = [0] * W
+tasks = []
+for i in sorted(range(len(sample_tasks)), key=lambda i: (-cost(sample_tasks[i]), i)):
+    r = min(range(W), key=lambda k: (load[k], k))
+    load[r] += cost(sample_tasks[i])
+    if r == w:
+        tasks.append(sample_tasks[i])
+if w != 0:
+    flops = 0
 psi = synth.gaussian_psi(n, synth.psi_seed(cfg))
+print("ready", flush=True)
+sys.stdin.readline()  # start together
+for r in range(warm):
+    heff.apply_heff(tab, e, tasks, blocks, n, psi)
 times = []
-t_end = time.time() + {max_seconds}
-for r in range({repeats}):
+for r in range(repeats):
     t0 = time.perf_counter(); heff.apply_heff(tab, e, tasks, blocks, n, psi); times.append(time.perf_counter() - t0)
-    if time.time() > t_end: break
-print(json.dumps({{"flops": flops, "times": times, "sample": sample}}))
+print(json.dumps({"flops": flops, "times": times, "sample": sample}), flush=True)
 """
+
+
+def oracle_cpu_baseline(cfg_name: str, repeats: int, flop_budget: float = 3e10, workers: int = 0, warmup: int = 0):
+    """Times the FP64 oracle (as it stands) on the host cores: `workers`
+    processes (default: one per core), one BLAS thread each, `warmup`
+    untimed repeats first.  Small configs
+    on one worker: the full H.psi.  Otherwise a bounded, deterministic sample
+    of whole output blocks (every task into them) shared among the workers,
+    which start their timed repeats together.  Returns (TFLOP/s, cores,
+    sample description, seconds per repeat): the flops of the sample over the
+    slowest worker's time, median over the repeats.  Flops follow the
+    library's definition (K1 counted once per distinct (right block, input
+    block))."""
+    W = workers or (os.cpu_count() or 1)
     envv = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=envv)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    t = statistics.median(d["times"])
-    return d["flops"] / t / 1e12, 1, f"{d['sample']}, median of {len(d['times'])}", t
+    code = _ORACLE_WORKER.replace("sys.path.insert(0, ROOT)", f"sys.path.insert(0, {ROOT!r})")
+    procs = [subprocess.Popen([sys.executable, "-c", code, str(w), str(W), cfg_name, str(repeats), str(flop_budget),
+                               str(warmup)],
+                              stdin=subprocess.PIPE, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=envv)
+             for w in range(W)]
+    try:
+        for p in procs:
+            line = p.stdout.readline()
+            if not line.startswith("ready"):
+                raise RuntimeError(p.stderr.read()[-2000:])
+        for p in procs:
+            p.stdin.write("go\n")
+            p.stdin.flush()
+        outs = []
+        for p in procs:
+            out, err = p.communicate(timeout=600)
+            if p.returncode != 0:
+                raise RuntimeError(err[-2000:])
+            outs.append(json.loads(out.strip().splitlines()[-1]))
+    finally:
+        for p in procs:
+            if p.poll() is None:
+                p.kill()
+    flops = sum(d["flops"] for d in outs)
+    per_rep = [max(d["times"][r] for d in outs) for r in range(repeats)]
+    t = statistics.median(per_rep)
+    return flops / t / 1e12, W, f"{outs[0]['sample']}, median of {repeats}", t
 
 
 def run_reference(args):
@@ -179,12 +223,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     cfg = synth.CONFIGS[args.config]
-    ts = []
-    value = None
-    for _ in range(args.warmup):
-        pass
-    v, cores, sample, t = oracle_cpu_baseline(args.config, max(1, args.steps), 150.0,
-                                              flop_budget=1.5e10)
+    v, cores, sample, t = oracle_cpu_baseline(args.config, max(1, args.steps), warmup=args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
@@ -303,6 +342,21 @@ def main():
         e2e_tot = float(t.item())
     e2e_value = world * args.steps * flops / e2e_tot / 1e12
 
+    # one Davidson iteration (H.psi + FP64 Gram-Schmidt, Rayleigh-Ritz, residual,
+    # correction), eager and as a CUDA-graph replay; host-timed (each step
+    # returns theta and the residual norm to the host)
+    dav_ms = {}
+    for graph in (False, True):
+        d = P.Davidson(ctx, env, psi, tol=1e-14, max_sub=24, keep=2, max_iter=1000, prec=prec, use_graph=graph)
+        d.step()
+        d.step()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(3):
+            d.step()
+        dav_ms["iter_ms_graph" if graph else "iter_ms_eager"] = (time.perf_counter() - t1) / 3 * 1e3
+        d.close()
+
     # roofline of the dominant kernel
     launch_count = prof.pop("kernel_launches")[0]
     dom = max(prof.items(), key=lambda kv: kv[1][1])
@@ -321,7 +375,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            v, cores, sample, _ = oracle_cpu_baseline(cfg.name, 2, 30.0, flop_budget=1.5e10)
+            v, cores, sample, _ = oracle_cpu_baseline(cfg.name, 2)
             cpu = {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample}
         except Exception as ex:  # reported, not fatal
             cpu = {"value": None, "unit": "TFLOP/s", "cores": 0, "kind": "oracle", "sample": f"failed: {ex}"}
@@ -351,6 +405,7 @@ def main():
                          "kernel": name, "peak_source": peak_note},
             "kernels": {k: {"launches": v[0], "ms": v[1], "flops": v[2]} for k, v in prof.items() if v[0]},
             "gpu_launches": gpu_launches,
+            "davidson": dav_ms,
             "clocks": clk,
             "cpu_baseline": cpu,
             "build_s": build_s,
