@@ -1,6 +1,6 @@
 """GPU parity of the split-precision (BF16 slices on tcgen05) path.
 
-Bar (the benchmark spec): relative 2-norm error of H.psi <= 1e-10 against the FP64
+Bar: relative 2-norm error of H.psi <= 1e-10 against the FP64
 oracle and against the GPU FP64 path on the same inputs; the device status
 word stays clear (no bounded wait gave up).
 """
