@@ -107,3 +107,23 @@ def test_autotune_picks_slices_and_stage_depth(ctx, tol):
     G = run(ctx, env, psi, P.SU2_SPLIT_BF16)
     H = run(ctx, env, psi, P.SU2_FP64)
     assert rel_err(G, H) <= max(10 * tol, 1e-11)
+
+
+def test_degenerate_inputs(ctx):
+    """psi = 0 gives F = 0 exactly on both paths (zero rows and columns take
+    the sentinel exponents); psi non-zero in one block only still matches the
+    oracle."""
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    cfg = CASES[2]
+    p = oracle_problem(cfg)
+    sec, env = workload.build(ctx, cfg, prepare_split=True)
+    z = np.zeros(sec.psi_len)
+    for prec in (P.SU2_FP64, P.SU2_SPLIT_BF16):
+        assert not np.any(run(ctx, env, z, prec))
+    blk = max(p["blocks"], key=lambda b: b.rows * b.cols)
+    one = np.zeros(p["n"])
+    one[blk.offset:blk.offset + blk.rows * blk.cols] = synth.gaussian_psi(blk.rows * blk.cols, 11)
+    F = oracle_apply(p, one)
+    assert rel_err(run(ctx, env, one, P.SU2_SPLIT_BF16), F) <= TOL_SPLIT
+    assert rel_err(run(ctx, env, one, P.SU2_FP64), F) <= 1e-12
