@@ -127,3 +127,18 @@ def test_degenerate_inputs(ctx):
     F = oracle_apply(p, one)
     assert rel_err(run(ctx, env, one, P.SU2_SPLIT_BF16), F) <= TOL_SPLIT
     assert rel_err(run(ctx, env, one, P.SU2_FP64), F) <= 1e-12
+
+
+@pytest.mark.parametrize("which", ["S2", "N"])
+def test_split_casimir(ctx, which):
+    """Total spin squared (as a sum of S_i.S_j) and particle number through the
+    whole split machinery: S(S+1) psi and N psi."""
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    cfg = synth.Config("c", synth.SPATIAL_ORBITAL, 12, 11, 3, 120, 4)
+    model = P.SU2_MODEL_CASIMIR_S2 if which == "S2" else P.SU2_MODEL_CASIMIR_N
+    sec, env = workload.build(ctx, cfg, model=model, prepare_split=True)
+    psi = synth.gaussian_psi(sec.psi_len, 1)
+    G = run(ctx, env, psi, P.SU2_SPLIT_BF16)
+    want = 1.5 * 2.5 if which == "S2" else 11.0
+    assert rel_err(G, want * psi) <= TOL_SPLIT
