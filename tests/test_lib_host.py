@@ -157,3 +157,26 @@ def test_flop_count_matches_oracle_dedup(hctx):
     D = sum(d for (_, _, d) in left)
     Deff = sum(d * (s + 1) for (_, s, d) in left)
     assert env.info["r_d"] == pytest.approx(Deff / D)
+
+
+def test_shard_options(hctx):
+    """A shard rank outside [0, count) is rejected; the shards of a count
+    partition the task list (each task in exactly one shard)."""
+    cfg = synth.Config("qc8", synth.SPATIAL_ORBITAL, 8, 8, 0, 12, 5)
+    lch, rch = workload.chains(cfg)
+    sec = L.Sectors(hctx, lch[-1], rch[-1], cfg.site_kind, cfg.N, cfg.twoS)
+    kw = dict(n_left=cfg.n_left, n_right=cfg.n_right, seed=cfg.seed)
+    with pytest.raises(L.Su2Error) as ei:
+        L.Environment(hctx, sec, L.SU2_MODEL_QC_SKELETON, lch, rch, shard=(3, 3), **kw)
+    assert ei.value.code == L.SU2_EINVAL
+    full = L.Environment(hctx, sec, L.SU2_MODEL_QC_SKELETON, lch, rch, **kw)
+    rows, v = full.tasks()
+    key = lambda r: tuple(int(x) for x in r[:7])
+    want = sorted(key(r) for r in rows)
+    got = []
+    for r in range(3):
+        part = L.Environment(hctx, sec, L.SU2_MODEL_QC_SKELETON, lch, rch, shard=(r, 3), **kw)
+        prow, _ = part.tasks()
+        assert len(prow) > 0
+        got += [key(x) for x in prow]
+    assert sorted(got) == want
