@@ -816,6 +816,14 @@ int split_prepare(su2_env* env, int S, std::string& err) {
     for (size_t q = 0; q < o2.size(); ++q) o2[q] = int(q);
     std::stable_sort(o2.begin(), o2.end(), [&](int a, int b) { return k2cost[a] > k2cost[b]; });
     for (int q : o2) st->k2j.push_back(k2jobs[q]);
+    // T' units of the tasks that read the same source tile run next to each
+    // other (the second read of the T tile then hits L2)
+    std::stable_sort(st->tpu.begin() + ch.tpu0, st->tpu.end(), [&](const TPUnit& x, const TPUnit& y) {
+      const int sx = st->tpt[ch.tp0 + x.task].src, sy = st->tpt[ch.tp0 + y.task].src;
+      if (sx != sy) return sx < sy;
+      if (x.tr != y.tr) return x.tr < y.tr;
+      return x.ks < y.ks;
+    });
     ch.k1_j1 = int64_t(st->k1j.size());
     ch.src1 = int64_t(st->src.size());
     ch.tp1 = int64_t(st->tpt.size());
