@@ -468,9 +468,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ------------------------------------------------------------ drain / epilogue
     const int q = warp & 3;             // TMEM lane quarter
-    const int cgrp = (warp - 2) >> 2;   // column group of kDrainCols
+    const int cgrp = (warp - 2) >> 2;   // column group: a quarter of the job's MMA columns
     const int row = q * 32 + lane;
-    const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + cgrp * kDrainCols;
+    const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     uint32_t chunk = 0;
     bool ok = true;
     for (int k = 0; ok; ++k) {
@@ -490,20 +490,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         hi2[c] = make_float2(0.f, 0.f);
         lo2[c] = make_float2(0.f, 0.f);
       }
+      // the 16 drain warps split the job's nmma columns evenly: nmma / 4 (a
+      // multiple of 4, at most kDrainCols) per lane-quarter warp, so a narrow
+      // tile drains in proportionally less time
       constexpr int kNG = kDrainCols / kGroup;
-      const int ng = min(kNG, max(0, (jb.nmma - cgrp * kDrainCols + kGroup - 1) / kGroup));  // valid column groups
-      const int c0 = jb.tc * kCols + cgrp * kDrainCols;
+      const int w = jb.nmma >> 2;
+      const int ng = w / kGroup;  // column groups of this warp
+      const int c0 = jb.tc * kCols + cgrp * w;
+      const uint32_t lane_addr = lane_base + cgrp * w;
       for (int it = jb.i0; it < jb.i1 && ok; ++it) {
         const Item item = items[it];
         // MODE_F: this thread's drain exponents of the item, fetched before
-        // the chunk wait (16-byte loads; byte k of word w = column 4w + k)
+        // the chunk wait (4-byte loads; byte k of word v = column 4v + k)
         uint32_t dx[kDrainCols / 4];
         if (MODE == MODE_F) {
+          const uint32_t* dw = reinterpret_cast<const uint32_t*>(ts.dexp + item.sc_off + c0);
 #pragma unroll
-          for (int v = 0; v < kDrainCols / 16; ++v) {
-            const int4 u = __ldg(reinterpret_cast<const int4*>(ts.dexp + item.sc_off + c0) + v);
-            dx[4 * v] = u.x, dx[4 * v + 1] = u.y, dx[4 * v + 2] = u.z, dx[4 * v + 3] = u.w;
-          }
+          for (int v = 0; v < kDrainCols / 4; ++v) dx[v] = v < ng ? __ldg(dw + v) : 0u;
         }
         const int nch = (item.nst + kChunkSteps - 1) / kChunkSteps;
         for (int ch = 0; ch < nch; ++ch) {
@@ -562,6 +565,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int er = rexp[jb.rsc + r];
 #pragma unroll
         for (int c = 0; c < kDrainCols; ++c) {
+          if (c >= w) break;
           const int cc = c0 + c;
           if (cc < jb.cols) {
             const int ex = er + cexp[jb.csc + cc] - shift;
