@@ -54,6 +54,8 @@ struct Unit { int32_t desc, tr, ks, pad; };
 struct Source {          // float-float matrix whose columns feed T' (K2 B operand)
   int64_t off;           // element offset in Th/Tl (sel 0) or psi_ff (sel 1)
   int32_t rows, cols, sel, cexp_off;
+  int32_t ld;            // column stride: T rows rounded up to 4 (16-byte aligned columns), psi block rows
+  int32_t pad;
 };
 struct TPTask {
   int32_t src;           // Source index (chunk-local)
@@ -263,7 +265,7 @@ __global__ void cexp_kernel(const Source* __restrict__ src, const float* __restr
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const float* base = (s.sel ? Ph : Th) + s.off;
   for (int c = threadIdx.x >> 5; c < s.cols; c += nw) {
-    const float* h = base + int64_t(c) * s.rows;
+    const float* h = base + int64_t(c) * s.ld;
     float m = 0.f;
     for (int r = lane; r < s.rows; r += 32) m = fmaxf(m, fabsf(h[r]));
 #pragma unroll
@@ -343,18 +345,42 @@ __global__ void slab_tprime_kernel(const TPTask* __restrict__ tasks, const TPUni
     const int ce = cexp[s.cexp_off + c];
     sc = (ce < -1000 || ph_t < -1000) ? 0 : ph_t + ce;
   }
+  // the 16 K values of column c: T columns are 16-byte aligned (stride a
+  // multiple of 4), so four 16-byte loads per array; rows past the column's
+  // end read padding or the next column and are set to zero
+  float av[16], bv[16];
+  const int k0 = u.ks * sp::kKS;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) av[q] = bv[q] = 0.f;
+  if (c < s.cols) {
+    const int64_t o = s.off + k0 + int64_t(c) * s.ld;
+    if (!s.sel) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const float4 x = reinterpret_cast<const float4*>(H + o)[v];
+        const float4 y = reinterpret_cast<const float4*>(Lo + o)[v];
+        av[4 * v] = x.x, av[4 * v + 1] = x.y, av[4 * v + 2] = x.z, av[4 * v + 3] = x.w;
+        bv[4 * v] = y.x, bv[4 * v + 1] = y.y, bv[4 * v + 2] = y.z, bv[4 * v + 3] = y.w;
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        if (k0 + q >= s.rows) av[q] = bv[q] = 0.f;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        if (k0 + q < s.rows) {
+          av[q] = H[o + q];
+          bv[q] = Lo[o + q];
+        }
+    }
+  }
   const int mi = tt >> 3, rr = tt & 7;
 #pragma unroll
   for (int kg = 0; kg < 2; ++kg) {
     float ph[8], pl[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int k = u.ks * sp::kKS + kg * 8 + q;
-      float a = 0.f, b = 0.f;
-      if (c < s.cols && k < s.rows) {
-        a = H[s.off + k + int64_t(c) * s.rows];
-        b = Lo[s.off + k + int64_t(c) * s.rows];
-      }
+      const float a = av[kg * 8 + q], b = bv[kg * 8 + q];
       // (a + b) * (vh + vl) in float-float
       const float p = a * vh;
       float e = fmaf(a, vh, -p);
@@ -725,7 +751,7 @@ int split_prepare(su2_env* env, int S, std::string& err) {
         auto it = pmap.find(t.e);
         if (it != pmap.end()) return it->second;
         const int id = int(st->src.size() - ch.src0);
-        st->src.push_back(Source{E.offset, E.rows, E.cols, 1, int32_t(csz)});
+        st->src.push_back(Source{E.offset, E.rows, E.cols, 1, int32_t(csz), E.rows, 0});
         csz += E.cols;
         pmap[t.e] = id;
         return id;
@@ -736,7 +762,8 @@ int split_prepare(su2_env* env, int S, std::string& err) {
       const OpBlock& Db = R.blocks[t.dblk];
       const int k1 = E.rows, k2 = E.cols, n = Db.rows;
       const int id = int(st->src.size() - ch.src0);
-      st->src.push_back(Source{tsz, k1, n, 0, int32_t(csz)});
+      const int ldT = (k1 + 3) & ~3;
+      st->src.push_back(Source{tsz, k1, n, 0, int32_t(csz), ldT, 0});
       csz += n;
       umap[key] = id;
       const int kst2 = (k2 + sp::kKS - 1) / sp::kKS;
@@ -746,12 +773,12 @@ int split_prepare(su2_env* env, int S, std::string& err) {
           const int ii = int(st->k1i.size());
           st->k1i.push_back(Item{st->edesc[t.e].slab_off + int64_t(tr) * kst2 * S * kSub,
                                  st->ddesc[t.dblk].slab_off + btile_off(tc, kst2, S), kst2, 0, -1});
-          k1jobs.push_back(Job{tsz, k1, n, k1, tr, tc, ii, ii + 1, int32_t(eps_off[t.e]),
+          k1jobs.push_back(Job{tsz, k1, n, ldT, tr, tc, ii, ii + 1, int32_t(eps_off[t.e]),
                                int32_t(zeta_off[t.dblk]), kst2, nmma_of(n, tc), 0});
           k1cost.push_back(kst2);
         }
       ch.k1_flops += 2.0 * k1 * k2 * n;
-      tsz += (int64_t(k1) * n + 3) & ~int64_t(3);
+      tsz += int64_t(ldT) * n;
       return id;
     };
     // K2 jobs grouped by output block
@@ -848,8 +875,9 @@ int split_prepare(su2_env* env, int S, std::string& err) {
   if (!rc2) rc2 = dalloc(&st->dD, size_t(st->d_bytes), err);
   if (!rc2) rc2 = dalloc(&st->dE, size_t(st->e_bytes), err);
   if (!rc2) rc2 = dalloc(&st->dTP, size_t(std::max<int64_t>(st->tp_bytes, 16)), err);
-  if (!rc2) rc2 = dalloc(&st->dTh, size_t(std::max<int64_t>(st->t_elems, 4)), err);
-  if (!rc2) rc2 = dalloc(&st->dTl, size_t(std::max<int64_t>(st->t_elems, 4)), err);
+  // + 16: the 16-byte loads of a T' unit may run up to 16 K past its source's last column
+  if (!rc2) rc2 = dalloc(&st->dTh, size_t(st->t_elems + 16), err);
+  if (!rc2) rc2 = dalloc(&st->dTl, size_t(st->t_elems + 16), err);
   if (!rc2) rc2 = dalloc(&st->dPh, size_t(env->psi_len), err);
   if (!rc2) rc2 = dalloc(&st->dPl, size_t(env->psi_len), err);
   if (!rc2) rc2 = dalloc(&st->d_rho, size_t(st->n_rho), err);
