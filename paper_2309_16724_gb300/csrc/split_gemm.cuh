@@ -1,39 +1,40 @@
 // Persistent split-precision stripe GEMM on tcgen05 (sm_103a).
 //
 // Operands are pre-tiled "slabs": an R x K FP64 matrix (R = M or N side,
-// K-major) cut into S BF16 slices, stored as 128-row x 16-K sub-tiles of
-// 4 KB in the UMMA no-swizzle K-major core-matrix layout (core matrix
-// (mi, ki) at (mi*2 + ki)*128 bytes, row r%8 at 16*(r%8)); for each
-// (row tile, K stage) the S slices follow each other (S*4 KB, one bulk
-// copy).  Slice i holds q_i * 2^-8i where q_i are the integers peeled from
-// x * 2^(8 - sigma_row) (|x| < 2^sigma_row): |q_0| <= 256, |q_i| <= 128.
+// K-major) cut into S BF16 slices, stored as sub-tiles of up to 128 rows x
+// 16 K in the UMMA no-swizzle K-major core-matrix layout (core matrix
+// (mi, ki) at (mi*2 + ki)*128 bytes, row r%8 at 16*(r%8)); the compact layout
+// (tile_rows / slab_pos below) stores a last row tile with only its rows,
+// and the S slices of consecutive 16-K steps of a row tile follow each other,
+// so one bulk copy per operand fills a pipeline stage.  Slice i holds
+// q_i * 2^-8i where q_i are the integers peeled from x * 2^(8 - sigma_row)
+// (|x| < 2^sigma_row): |q_0| <= 256, |q_i| <= 128.
 //
-// One job = one 128 x 64 output tile (rows of a slab row tile x half of a
-// B slab row tile) and a list of items (A slab, B slab, K stages); all items
-// of a job share the row and column scales, so the K-concatenated stripe
-// sum_items A_item . B_item^T accumulates in TMEM without a separate
-// reduction (the stripe product of Sec. III.A).  Slice pairs (i, j), i + j < S,
-// go to four FP32 TMEM accumulators of 64 columns by level l = min(i + j, 3);
-// TMEM (512 columns) holds two such buffers, so the MMAs of chunk c + 1 run
-// while the drain reads chunk c.  Levels 0, 1 and 2 hold integer multiples of
-// their unit 2^-8l below 2^24 for K chunks of 192 (level 2 grows by at most
-// 2*256*128 + 128^2 = 2^16.3 per K, 192 K give 2^23.9), hence are exact whatever
-// rounding the tensor core applies when it adds into the accumulator
-// (it truncates: a shared tail accumulator of many pairs would collect a
-// biased error of order #adds * 2^-23 of its size); level 3 carries the
-// 2^-24-weighted tail.  A chunk is up to 192 K of one item; after it the
+// One job = one 128 x 128 output tile and a list of items (A slab, B slab,
+// K steps); all items of a job share the row and column scales, so the
+// K-concatenated stripe sum_items A_item . B_item^T accumulates in TMEM
+// without a separate reduction (the stripe product of Sec. III.A).  Slice
+// pairs (i, j), i + j < S, go to four FP32 TMEM accumulators of 128 columns
+// (all 512) by level l = min(i + j, 3).  Levels 0, 1 and 2 hold integer
+// multiples of their unit 2^-8l below 2^24 for K chunks of 192 (level 2 grows
+// by at most 2*256*128 + 128^2 = 2^16.3 per K, 192 K give 2^23.9), hence are
+// exact whatever rounding the tensor core applies when it adds into the
+// accumulator (it truncates: a shared tail accumulator of many pairs would
+// collect a biased error of order #adds * 2^-23 of its size); level 3 carries
+// the 2^-24-weighted tail.  A chunk is up to 192 K of one item; after it the
 // drain warps fold the four levels into a float-float register accumulator
 // (K2: scaled by the item's per-column factor, so every task keeps its own
-// S*8 bits); the first MMA into each level of the buffer's next chunk
-// overwrites it.  At the end of the job they write the tile (K1: float-float
-// T; K2: F += FP64).  The two 64-column halves of a 128-column slab tile are
-// neighbouring jobs, so the second read of their common A tiles mostly hits L2.
+// S*8 bits), and the first MMA of the next chunk into each level overwrites
+// it.  At the end of the job they write the tile (K1: float-float T; K2:
+// F += FP64).
 //
-// Warp roles (576 threads): warp 0 bulk-copy producer and job fetcher
-// (dynamic schedule: an atomic job counter, handed to the other roles through
-// a shared-memory ring), warp 1 MMA issuer, warps 2..17 drain/epilogue (TMEM
-// lane quarter w%4, 16-column group (w-2)/4).  The drain warps arrive on
-// barriers with one lane each.
+// Warp roles (576 threads): warp 0, one lane: job fetcher (dynamic schedule:
+// an atomic job counter, handed to the drain warps through a shared-memory
+// ring) and bulk-copy producer, which leaves one metadata word per stage for
+// the MMA issuer; warp 1, one lane: MMA issuer, reading shared memory only;
+// warps 2..17: drain and epilogue (TMEM lane quarter w%4; the job's columns
+// are split evenly among the four warps of a quarter).  The drain warps
+// arrive on barriers with one lane each.
 // Every mbarrier wait is bounded; on timeout the CTA records a status,
 // stops issuing, waits (bounded) for its own copies and MMAs, frees TMEM and
 // returns.
@@ -56,7 +57,7 @@ constexpr int kKS = 16;              // K per pipeline stage (one MMA K step)
 constexpr int kSub = kRows * kKS * 2;  // bytes of one 128 x 16 BF16 sub-tile (slabs, A stage)
 constexpr int kSubB = kCols * kKS * 2;  // bytes of the B part of a stage slice (kCols rows)
 constexpr int kBufCols = 4 * kCols;  // TMEM columns of one accumulator buffer (4 levels)
-constexpr int kDrainCols = kCols / 4;  // columns per drain thread (16 drain warps: 4 lane quarters x 4 groups)
+constexpr int kDrainCols = kCols / 4;  // most columns per drain thread (16 drain warps: 4 lane quarters x 4 groups)
 constexpr int kGroup = kDrainCols >= 32 ? 4 : 8;  // columns per TMEM load group
 constexpr int kMaxS = 6;
 constexpr int kChunkSteps = 12;      // 16-K steps per exact drain chunk (192 K)
