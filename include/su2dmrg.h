@@ -233,7 +233,8 @@ int su2_davidson_destroy(su2_dav* dav);
  * every kernel launch of the hot path is bracketed by CUDA events on the
  * context stream.  su2_profile_read synchronises on the recorded events and
  * returns, for kernel kind `kind` (0: FP64 K1, 1: FP64 K2, 2: split-path
- * slice kernel, 3: split-path K1, 4: split-path K2), the launches, total
+ * kernels other than the GEMMs: slices, exponents, T' slabs and the
+ * small-task class, 3: split-path K1, 4: split-path K2), the launches, total
  * device milliseconds and algorithmic flops since the last reset, and the
  * kind's name.  Kind 5 counts every kernel the hot path launched (also with
  * profiling off; no timing).  SU2_EINVAL for an unknown kind. */

@@ -19,6 +19,15 @@
 //    with the largest task of the column, and thousands of tasks add up.
 //  * K1 (T = E D^T): per-row exponents of the psi blocks and of the right
 //    operator blocks.
+//
+// Per H.psi: psi is copied to float-float and sliced (psi slabs); per term
+// chunk (whose intermediates fit the T budget): K1 writes T in float-float
+// (columns padded to a multiple of 4), column exponents of T and of psi
+// blocks, gamma and the int8 drain exponents, T' slabs, then K2 adds into
+// F.  Tasks whose four dimensions are all <= kSmallDim run afterwards in
+// FP64 on CUDA cores (small-task class).  The operator slabs are built once
+// per site by split_prepare; split_autotune picks the slice count and the
+// stage depth.
 #include <algorithm>
 #include <climits>
 #include <cmath>
