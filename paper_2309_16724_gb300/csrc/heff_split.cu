@@ -160,6 +160,15 @@ __device__ __forceinline__ int exp_of_f(float x) {
   return be == 0 ? -126 : be - 126;
 }
 
+// x * 2^e: one multiply by the power of two when that is a normal number (the
+// same correctly rounded result as ldexp), ldexp otherwise
+__device__ __forceinline__ float scale2f(float x, int e) {
+  return (e >= -126 && e <= 127) ? x * __int_as_float((127 + e) << 23) : ldexpf(x, e);
+}
+__device__ __forceinline__ double scale2(double x, int e) {
+  return (e >= -1022 && e <= 1023) ? x * __longlong_as_double((long long)(1023 + e) << 52) : ldexp(x, e);
+}
+
 // row exponents of FP64 source matrices: one CTA (128 threads) per (desc, row tile)
 __global__ void rowexp_kernel(const SlabDesc* __restrict__ descs, const Unit* __restrict__ units,
                               const double* __restrict__ src, int* __restrict__ out, int use_own) {
@@ -240,15 +249,16 @@ __global__ void slab_fp64_kernel(const SlabDesc* __restrict__ descs, const Unit*
         if (d.src_off < 0) x = (r == k) ? 1.0 : 0.0;
         else x = src[d.src_off + r + int64_t(k) * d.ld];
       }
-      y[q] = ldexp(x, sp::kLead - sigma);  // |y| < 2^kLead
+      y[q] = scale2(x, sp::kLead - sigma);  // |y| < 2^kLead
     }
-    for (int i = 0; i < S; ++i) {
+    float si = 1.f;  // 2^-8i
+    for (int i = 0; i < S; ++i, si *= 0x1p-8f) {
       __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const double qi = rint(y[q]);
         y[q] = (y[q] - qi) * 256.0;
-        v[q] = __float2bfloat16_rn(ldexpf((float)qi, -8 * i));
+        v[q] = __float2bfloat16_rn((float)qi * si);
       }
       *(uint4*)(base + int64_t(i) * trows * 32 + (mi * 2 + kg) * 128 + rr * 16) = *(const uint4*)v;
     }
@@ -396,13 +406,14 @@ __global__ void slab_tprime_kernel(const TPTask* __restrict__ tasks, const TPUni
       e = fmaf(a, vl, e);
       e = fmaf(b, vh, e);
       // scale to |x| < 2^kLead (exact power of two)
-      ph[q] = ldexpf(p, sp::kLead - sc);
-      pl[q] = ldexpf(e, sp::kLead - sc);
+      ph[q] = scale2f(p, sp::kLead - sc);
+      pl[q] = scale2f(e, sp::kLead - sc);
       const float hs = ph[q] + pl[q];
       pl[q] = pl[q] - (hs - ph[q]);
       ph[q] = hs;
     }
-    for (int i = 0; i < S; ++i) {
+    float si = 1.f;  // 2^-8i
+    for (int i = 0; i < S; ++i, si *= 0x1p-8f) {
       __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -411,7 +422,7 @@ __global__ void slab_tprime_kernel(const TPTask* __restrict__ tasks, const TPUni
         const float hs = rh + pl[q];
         pl[q] = (pl[q] - (hs - rh)) * 256.f;
         ph[q] = hs * 256.f;
-        v[q] = __float2bfloat16_rn(ldexpf(qi, -8 * i));
+        v[q] = __float2bfloat16_rn(qi * si);
       }
       *(uint4*)(base + int64_t(i) * trows * 32 + (mi * 2 + kg) * 128 + rr * 16) = *(const uint4*)v;
     }
