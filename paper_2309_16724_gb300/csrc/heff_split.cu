@@ -139,7 +139,7 @@ struct SplitState {
   int* d_status = nullptr;
   int* d_counter = nullptr;
   int* d_phi = nullptr;          // per TP task: phi_t
-  int8_t* d_scale = nullptr;     // per (task, column) drain exponents of one chunk
+  uint8_t* d_scale = nullptr;    // per (task, column) biased drain exponents of one chunk
   int64_t* d_scoff = nullptr;    // per TP task: offset into d_scale (chunk-local)
   std::vector<int64_t> scoff;
   int64_t n_scale = 0;
@@ -317,15 +317,16 @@ __global__ void gamma_kernel(const TPTask* __restrict__ tasks, const Source* __r
 }
 
 // per-(task, column) drain exponents d = phi_t + cexp(c) - gamma(c) <= 0 (the
-// factor is 2^d); -127 (factor 0) for empty columns, for d below -126 and for
-// the padding up to the next multiple of 128 columns
+// factor is 2^d), stored biased as 127 + d (the FP32 exponent field of 2^d);
+// 0 (factor 0) for empty columns, for d below -126 and for the padding up to
+// the next multiple of 128 columns
 __global__ void scale_kernel(const TPTask* __restrict__ tasks, const Source* __restrict__ src,
                              const int* __restrict__ cexp, const int* __restrict__ gamma,
-                             const int* __restrict__ phi, const int64_t* __restrict__ sc_off, int8_t* __restrict__ scale) {
+                             const int* __restrict__ phi, const int64_t* __restrict__ sc_off, uint8_t* __restrict__ scale) {
   const TPTask t = tasks[blockIdx.x];
   const Source s = src[t.src];
   const int ph = phi[blockIdx.x];
-  int8_t* out = scale + sc_off[blockIdx.x];
+  uint8_t* out = scale + sc_off[blockIdx.x];
   const int padded = (s.cols + 127) & ~127;
   for (int c = threadIdx.x; c < padded; c += blockDim.x) {
     int d = -127;
@@ -333,7 +334,7 @@ __global__ void scale_kernel(const TPTask* __restrict__ tasks, const Source* __r
       const int ce = cexp[s.cexp_off + c];
       if (ce > -1000) d = max(-127, ph + ce - gamma[t.gcol + c]);
     }
-    out[c] = (int8_t)d;
+    out[c] = d <= -127 ? 0 : (uint8_t)(127 + d);
   }
 }
 

@@ -25,8 +25,12 @@
 // drain warps fold the four levels into a float-float register accumulator
 // (K2: scaled by the item's per-column factor, so every task keeps its own
 // S*8 bits), and the first MMA of the next chunk into each level overwrites
-// it.  At the end of the job they write the tile (K1: float-float T; K2:
-// F += FP64).
+// it.  The chunk enters as the exact pair (x0 + r, (y1 - r) + y2 + y3), with
+// r = rint(y1): level 0 is an integer of at most 192 * 2^16 and level 1 stays
+// below 2^16, so x0 + r is an integer below 2^24 and y1 - r is at most 1/2.
+// The job's first chunk becomes the accumulator; later ones are added with
+// TwoSum and renormalised.  At the end of the job they write the tile (K1:
+// normalised float-float T; K2: F += FP64).
 //
 // Warp roles (576 threads): warp 0, one lane: job fetcher (dynamic schedule:
 // an atomic job counter, handed to the drain warps through a shared-memory
@@ -104,12 +108,13 @@ struct Item {
   int64_t sc_off;        // MODE_F: offset of the item's per-column drain exponents (a multiple of 128), -1 otherwise
 };
 // MODE_F: task t's B slab is cut relative to its own column exponents; the
-// drain multiplies each chunk of t by 2^d, d = dexp[sc_off + col] =
-// own(col) - gamma(col) in [-126, 0], or -127 for a column that is zero (an
-// exact power of two, <= 1) before adding it to the tile accumulator.  The
-// per-task vector is padded to whole 128-column tiles.
+// drain multiplies each chunk of t by 2^d, d = own(col) - gamma(col) in
+// [-126, 0] (an exact power of two, <= 1), before adding it to the tile
+// accumulator.  dexp[sc_off + col] holds the biased exponent 127 + d, the
+// exponent field of the FP32 number 2^d, or 0 (the factor 0) for a column
+// that is zero.  The per-task vector is padded to whole 128-column tiles.
 struct TaskScale {
-  const int8_t* dexp;
+  const uint8_t* dexp;
 };
 struct Job {
   int64_t out_off;       // element offset of the output block
@@ -260,16 +265,28 @@ __device__ __forceinline__ void tmem_ld_levels<8>(uint32_t a, float (&x)[32]) {
 }
 
 // packed FP32 pairs (two drain columns per instruction); every step is the
-// same IEEE operation on each half, so TwoSum stays error-free
+// same IEEE operation on each half, so TwoSum stays error-free.  a - b is
+// fma(b, -1, a): b * -1 is exact, so the one rounding gives RN(a - b) in a
+// single packed instruction with no separate negation
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
   s = add2(a, b);
   const float2 bb = sub2(s, a);
   e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
 }
-// x * 2^k for float, exact while the result stays normal
-__device__ __forceinline__ float ldexp_f(float x, int k) { return ldexpf(x, k); }
+// x * 2^k: one multiply by the power of two built from its exponent field
+// while 2^k is a normal number (the correctly rounded product, as ldexp
+// gives), ldexp otherwise
+__device__ __forceinline__ float ldexp_f(float x, int k) {
+  return (k >= -126 && k <= 127) ? x * __int_as_float((127 + k) << 23) : ldexpf(x, k);
+}
+__device__ __forceinline__ double ldexp_d(double x, int k) {
+  if (k >= -1022 && k <= 1023) return x * __longlong_as_double((long long)(1023 + k) << 52);
+  k = max(-2044, min(2046, k));
+  const int k1 = k / 2;
+  return x * __longlong_as_double((long long)(1023 + k1) << 52) * __longlong_as_double((long long)(1023 + k - k1) << 52);
+}
 
 template <int MODE, int S>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -285,6 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], accf_bar[2], acce_bar[2], done_bar;
   __shared__ __align__(8) uint64_t jq_full[kRing], jq_empty[kRing];
   __shared__ int job_ring[kRing];
+  __shared__ Job job_slot[kRing];  // the job itself: the drain reads its fields here when it needs them
   __shared__ uint32_t stage_meta[kMaxStages];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
@@ -333,10 +351,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         const int jnext = atomicAdd(job_counter, 1);
         const int j = jnext < njobs ? jnext : -1;
+        Job jb{};
+        if (j >= 0) {
+          jb = jobs[j];
+          job_slot[slot] = jb;
+        }
         job_ring[slot] = j;
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&jq_full[slot])) : "memory");
         if (j < 0) break;
-        const Job jb = jobs[j];
         const int arows = tile_rows(jb.rows, jb.tr);
         const int abytes = arows * 32, bbytes = jb.nmma * 32;  // stored bytes of one A / B sub-tile
         const uint32_t nmeta = ((uint32_t)(jb.nmma >> 4) << 8) | ((uint32_t)(arows >> 4) << 12);
@@ -481,33 +503,44 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       const int j = job_ring[slot];
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&jq_empty[slot])) : "memory");
-      if (j < 0) break;
-      const Job jb = jobs[j];
+      if (j < 0) {
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&jq_empty[slot])) : "memory");
+        break;
+      }
+      // the job stays in its ring slot until this warp's epilogue is done; its
+      // fields are read from shared memory where they are used, so that they
+      // hold no registers across the chunk loop
+      const volatile Job& jb = job_slot[slot];
+      // float-float tile accumulator (leading, trailing part), set by the
+      // job's first chunk
       float2 hi2[kDrainCols / 2], lo2[kDrainCols / 2];
 #pragma unroll
       for (int c = 0; c < kDrainCols / 2; ++c) {
         hi2[c] = make_float2(0.f, 0.f);
         lo2[c] = make_float2(0.f, 0.f);
       }
+      bool first = true;
       // the 16 drain warps split the job's nmma columns evenly: nmma / 4 (a
       // multiple of 4, at most kDrainCols) per lane-quarter warp, so a narrow
       // tile drains in proportionally less time
       constexpr int kNG = kDrainCols / kGroup;
+      static_assert(kGroup == 4, "the drain exponent of column 4g + c is byte c of word g");
       const int w = jb.nmma >> 2;
       const int ng = w / kGroup;  // column groups of this warp
       const int c0 = jb.tc * kCols + cgrp * w;
       const uint32_t lane_addr = lane_base + cgrp * w;
-      for (int it = jb.i0; it < jb.i1 && ok; ++it) {
+      const int i1 = jb.i1;
+      for (int it = jb.i0; it < i1 && ok; ++it) {
         const Item item = items[it];
-        // MODE_F: this thread's drain exponents of the item, fetched before
-        // the chunk wait (4-byte loads; byte k of word v = column 4v + k)
-        uint32_t dx[kDrainCols / 4];
+        // MODE_F: the item's drain exponents of this warp's columns, fetched
+        // before the chunk wait; they are the same for every lane (row), so
+        // lane v holds word v (bytes = columns 4v .. 4v + 3) and the group
+        // loop broadcasts it
+        uint32_t dxl = 0u;
         if (MODE == MODE_F) {
           const uint32_t* dw = reinterpret_cast<const uint32_t*>(ts.dexp + item.sc_off + c0);
-#pragma unroll
-          for (int v = 0; v < kDrainCols / 4; ++v) dx[v] = v < ng ? __ldg(dw + v) : 0u;
+          if (lane < ng) dxl = __ldg(dw + lane);
         }
         const int nch = (item.nst + kChunkSteps - 1) / kChunkSteps;
         for (int ch = 0; ch < nch; ++ch) {
@@ -523,6 +556,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t a = lane_addr + buf * kBufCols + g * kGroup;
             float x[4 * kGroup];  // levels 0..3, kGroup columns each
             tmem_ld_levels<kGroup>(a, x);
+            const uint32_t dxg = MODE == MODE_F ? __shfl_sync(0xffffffffu, dxl, g) : 0u;
+            if (g == ng - 1) {
+              // the warp's last TMEM read of this chunk has completed: hand
+              // the buffer back before the arithmetic on the last group
+              asm volatile("tcgen05.fence::before_thread_sync;");
+              __syncwarp();
+              if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[buf])) : "memory");
+            }
 #pragma unroll
             for (int c = 0; c < kGroup; c += 2) {
               const int k = g * kGroup + c;  // column within this thread's group (even)
@@ -531,57 +573,84 @@ __global__ void __launch_bounds__(kThreads, 1)
               const float2 y1 = nlev > 1 ? make_float2(x[kGroup + c], x[kGroup + c + 1]) : z;
               const float2 y2 = nlev > 2 ? make_float2(x[2 * kGroup + c], x[2 * kGroup + c + 1]) : z;
               const float2 y3 = nlev > 3 ? make_float2(x[3 * kGroup + c], x[3 * kGroup + c + 1]) : z;
-              float2 s, e, h, e2;
+              // x0 + y1 split exactly without TwoSum: level 0 is an integer
+              // with |x0| <= 192 * 256 * 256 (slice 0 of each operand is an
+              // integer of magnitude <= 256), level 1 a multiple of 2^-8 with
+              // |y1| <= 192 * 2 * 256 * 128 * 2^-8 < 2^22, so r = rint(y1) (by
+              // the 1.5 * 2^23 shift), s = x0 + r (an integer < 2^24) and
+              // e = y1 - r (|e| <= 1/2) are all exact and s + e = x0 + y1
+              const float2 mg = make_float2(12582912.f, 12582912.f);
+              const float2 r = sub2(add2(y1, mg), mg);
+              float2 sc = add2(x0, r);
+              float2 t = add2(sub2(y1, r), add2(y2, y3));
               if (MODE == MODE_F) {
-                const int d0 = (int)(int8_t)(dx[k >> 2] >> (8 * (k & 3)));
-                const int d1 = (int)(int8_t)(dx[(k + 1) >> 2] >> (8 * ((k + 1) & 3)));
-                const float2 f2 = make_float2(__int_as_float((127 + d0) << 23), __int_as_float((127 + d1) << 23));
-                two_sum2(__fmul2_rn(x0, f2), __fmul2_rn(y1, f2), s, e);
-                two_sum2(hi2[k >> 1], s, h, e2);
-                const float2 l = add2(lo2[k >> 1], add2(e2, add2(e, __ffma2_rn(y2, f2, __fmul2_rn(y3, f2)))));
-                const float2 hs = add2(h, l);
-                lo2[k >> 1] = sub2(l, sub2(hs, h));
-                hi2[k >> 1] = hs;
-              } else {
-                two_sum2(x0, y1, s, e);
-                two_sum2(hi2[k >> 1], s, h, e2);
-                const float2 l = add2(lo2[k >> 1], add2(e2, add2(e, add2(y2, y3))));
+                // 2^d of columns k and k + 1: the biased exponent byte moved
+                // to the FP32 exponent field (byte 3 of a word, shifted right
+                // once); the scaling of both parts is exact
+                const uint32_t b0 = __byte_perm(dxg, 0u, 0x0444u | ((uint32_t)c << 12)) >> 1;
+                const uint32_t b1 = __byte_perm(dxg, 0u, 0x0444u | ((uint32_t)(c + 1) << 12)) >> 1;
+                const float2 f2 = make_float2(__uint_as_float(b0), __uint_as_float(b1));
+                sc = __fmul2_rn(sc, f2);
+                t = __fmul2_rn(t, f2);
+              }
+              if (first) {  // the accumulator is zero: it becomes the chunk (sc, t)
+                hi2[k >> 1] = sc;
+                lo2[k >> 1] = t;
+              } else {  // TwoSum into the leading part, the rest into the trailing part, renormalise
+                float2 h, e2;
+                two_sum2(hi2[k >> 1], sc, h, e2);
+                const float2 l = add2(lo2[k >> 1], add2(e2, t));
                 const float2 hs = add2(h, l);
                 lo2[k >> 1] = sub2(l, sub2(hs, h));
                 hi2[k >> 1] = hs;
               }
             }
           }
-          asm volatile("tcgen05.fence::before_thread_sync;");
-          __syncwarp();
-          if (lane == 0)
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[buf])) : "memory");
+          if (ng <= 0) {  // (nmma >= 16 gives ng >= 1; kept so that the barrier always completes)
+            __syncwarp();
+            if (lane == 0)
+              asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce_bar[buf])) : "memory");
+          }
+          first = false;
           chunk += 1;
         }
       }
       if (!ok) break;
       // epilogue: scale by 2^(rexp + cexp - shift) and write
       const int r = jb.tr * kRows + row;
-      if (r < jb.rows) {
+      const int jrows = jb.rows, jcols = jb.cols, jld = jb.ld;
+      const int* const ce_j = cexp + jb.csc;
+      const int64_t jout = jb.out_off;
+      if (r < jrows) {
         const int er = rexp[jb.rsc + r];
 #pragma unroll
         for (int c = 0; c < kDrainCols; ++c) {
           if (c >= w) break;
           const int cc = c0 + c;
-          if (cc < jb.cols) {
-            const int ex = er + cexp[jb.csc + cc] - shift;
-            const int64_t o = jb.out_off + r + (int64_t)cc * jb.ld;
+          if (cc < jcols) {
+            const int ex = er + ce_j[cc] - shift;
+            const int64_t o = jout + r + (int64_t)cc * jld;
             if (MODE == MODE_T) {
-              Th[o] = ldexp_f((c & 1) ? hi2[c >> 1].y : hi2[c >> 1].x, ex);
-              Tl[o] = ldexp_f((c & 1) ? lo2[c >> 1].y : lo2[c >> 1].x, ex);
+              // a job whose only chunk was its first leaves (hi, lo) not
+              // normalised; T goes out normalised (TwoSum), since the column
+              // exponents of T are taken from its leading part alone
+              const float ha = (c & 1) ? hi2[c >> 1].y : hi2[c >> 1].x;
+              const float la = (c & 1) ? lo2[c >> 1].y : lo2[c >> 1].x;
+              const float hs = __fadd_rn(ha, la), bb = __fsub_rn(hs, ha);
+              const float ls = __fadd_rn(__fsub_rn(ha, __fsub_rn(hs, bb)), __fsub_rn(la, bb));
+              Th[o] = ldexp_f(hs, ex);
+              Tl[o] = ldexp_f(ls, ex);
             } else {
-              F[o] += ldexp((double)((c & 1) ? hi2[c >> 1].y : hi2[c >> 1].x) +
+              F[o] += ldexp_d((double)((c & 1) ? hi2[c >> 1].y : hi2[c >> 1].x) +
                                 (double)((c & 1) ? lo2[c >> 1].y : lo2[c >> 1].x),
                             ex);
             }
           }
         }
       }
+      // the job's ring slot may now take the next job
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&jq_empty[slot])) : "memory");
     }
     if (!ok) {
       abort_flag = 1;
