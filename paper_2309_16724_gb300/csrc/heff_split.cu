@@ -395,37 +395,56 @@ __global__ void slab_tprime_kernel(const TPTask* __restrict__ tasks, const TPUni
     }
   }
   const int mi = tt >> 3, rr = tt & 7;
+  // the same IEEE operations as the scalar form, on packed FP32 pairs (two
+  // K values per instruction): rint by the 1.5 * 2^23 shift (|x| <= 2^8 + 1
+  // here), the power-of-two scaling as one multiply while the factor is a
+  // normal number, differences as fma(b, -1, a)
+  const int es = sp::kLead - sc;
+  const bool fast = es >= -126 && es <= 127;
+  const float fac = fast ? __int_as_float((127 + es) << 23) : 1.f;
+  const float2 nvh = make_float2(-vh, -vh), vh2 = make_float2(vh, vh), vl2 = make_float2(vl, vl);
+  const float2 nf2 = make_float2(-fac, -fac), f2 = make_float2(fac, fac), m1 = make_float2(-1.f, -1.f);
+  const float2 mg = make_float2(12582912.f, 12582912.f), c256 = make_float2(256.f, 256.f);
 #pragma unroll
   for (int kg = 0; kg < 2; ++kg) {
-    float ph[8], pl[8];
+    float2 ph[4], pl[4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float a = av[kg * 8 + q], b = bv[kg * 8 + q];
-      // (a + b) * (vh + vl) in float-float
-      const float p = a * vh;
-      float e = fmaf(a, vh, -p);
-      e = fmaf(a, vl, e);
-      e = fmaf(b, vh, e);
+    for (int j = 0; j < 4; ++j) {
+      const int q = kg * 8 + 2 * j;
+      const float2 a = make_float2(av[q], av[q + 1]), b = make_float2(bv[q], bv[q + 1]);
+      // (a + b) * (vh + vl) in float-float: pn = -RN(a vh), e = a vh - RN(a vh) + a vl + b vh
+      const float2 pn = __fmul2_rn(a, nvh);
+      float2 e = __ffma2_rn(a, vh2, pn);
+      e = __ffma2_rn(a, vl2, e);
+      e = __ffma2_rn(b, vh2, e);
       // scale to |x| < 2^kLead (exact power of two)
-      ph[q] = scale2f(p, sp::kLead - sc);
-      pl[q] = scale2f(e, sp::kLead - sc);
-      const float hs = ph[q] + pl[q];
-      pl[q] = pl[q] - (hs - ph[q]);
-      ph[q] = hs;
-    }
-    float si = 1.f;  // 2^-8i
-    for (int i = 0; i < S; ++i, si *= 0x1p-8f) {
-      __align__(16) __nv_bfloat16 v[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float qi = rintf(ph[q]);
-        const float rh = ph[q] - qi;           // exact
-        const float hs = rh + pl[q];
-        pl[q] = (pl[q] - (hs - rh)) * 256.f;
-        ph[q] = hs * 256.f;
-        v[q] = __float2bfloat16_rn(qi * si);
+      float2 h, l;
+      if (fast) {
+        h = __fmul2_rn(pn, nf2);
+        l = __fmul2_rn(e, f2);
+      } else {
+        h = make_float2(ldexpf(-pn.x, es), ldexpf(-pn.y, es));
+        l = make_float2(ldexpf(e.x, es), ldexpf(e.y, es));
       }
-      *(uint4*)(base + int64_t(i) * trows * 32 + (mi * 2 + kg) * 128 + rr * 16) = *(const uint4*)v;
+      const float2 hs = __fadd2_rn(h, l);
+      pl[j] = __ffma2_rn(__ffma2_rn(h, m1, hs), m1, l);  // l - (hs - h)
+      ph[j] = hs;
+    }
+    float2 si = make_float2(1.f, 1.f);  // 2^-8i
+    for (int i = 0; i < S; ++i, si = __fmul2_rn(si, make_float2(0x1p-8f, 0x1p-8f))) {
+      uint4 w;
+      uint32_t* wv = &w.x;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 qi = __ffma2_rn(mg, m1, __fadd2_rn(ph[j], mg));  // rint(ph)
+        const float2 rh = __ffma2_rn(qi, m1, ph[j]);                 // ph - qi, exact
+        const float2 hs = __fadd2_rn(rh, pl[j]);
+        pl[j] = __fmul2_rn(__ffma2_rn(__ffma2_rn(rh, m1, hs), m1, pl[j]), c256);  // (pl - (hs - rh)) * 256
+        ph[j] = __fmul2_rn(hs, c256);
+        const __nv_bfloat162 v2 = __float22bfloat162_rn(__fmul2_rn(qi, si));
+        wv[j] = *reinterpret_cast<const uint32_t*>(&v2);
+      }
+      *(uint4*)(base + int64_t(i) * trows * 32 + (mi * 2 + kg) * 128 + rr * 16) = w;
     }
   }
 }
@@ -556,6 +575,22 @@ int32_t nmma_of(int cols, int tc) {
 
 // byte offset of job column tile tc (kCols = 128 wide) in a compact B slab: its row tile
 int64_t btile_off(int tc, int kst, int S) { return int64_t(tc) * kst * S * kSub; }
+
+// Modelled cost of one orientation of a tile product: the M side has Mr rows
+// (128-row tiles, every MMA has M = 128), the N side Nr rows (tiles of kCols,
+// MMA N = the valid extent rounded up to 16); steps / chunks are the 16-K
+// steps and drain chunks summed over the items.  Measured on GB300: an MMA
+// (M = 128, K = 16) takes about max(N / 2, 32 + N / 4) cycles (48 at N = 64,
+// 64 at N = 128), and a drain exposes about 23 cycles per column.
+double orient_cost(int Mr, int Nr, double steps, double chunks, int S) {
+  const double pairs = S * (S + 1) / 2.0;
+  double per = 0.0;
+  for (int tc = 0; tc < (Nr + sp::kCols - 1) / sp::kCols; ++tc) {
+    const double nm = nmma_of(Nr, tc);
+    per += pairs * std::max(nm / 2.0, 32.0 + nm / 4.0) * steps + 23.0 * nm * chunks;
+  }
+  return per * ((Mr + 127) / 128);
+}
 
 int exp_host(double x) {
   if (x == 0.0) return kSentinel;
@@ -788,7 +823,10 @@ int split_prepare(su2_env* env, int S, std::string& err) {
       csz += n;
       umap[key] = id;
       const int kst2 = (k2 + sp::kKS - 1) / sp::kKS;
-      // the column tiles of one row tile are neighbouring jobs (they share the E tile)
+      // T = E D^T with M along the rows of T.  (The transposed orientation
+      // writes T with the lanes of a warp a column apart; measured on qc32 it
+      // cost more in the epilogue than it saved in MMA and drain work.)
+      // The column tiles of one row tile are neighbouring jobs (they share the E tile).
       for (int tr = 0; tr < (k1 + 127) / 128; ++tr)
         for (int tc = 0; tc < (n + sp::kCols - 1) / sp::kCols; ++tc) {
           const int ii = int(st->k1i.size());
@@ -840,18 +878,30 @@ int split_prepare(su2_env* env, int S, std::string& err) {
         tpsz += slab_bytes(Fb.cols, E.rows, S);
         if (t.ablk >= 0) ch.k2_flops += 2.0 * Fb.rows * E.rows * Fb.cols;
       }
-      // the column tiles of one row tile are neighbouring jobs (they share the A tiles)
-      for (int tr = 0; tr < (Fb.rows + 127) / 128; ++tr)
-        for (int tc = 0; tc < (Fb.cols + sp::kCols - 1) / sp::kCols; ++tc) {
+      // F_f += A T' with M along the rows of F_f (A rows) or, transposed,
+      // along its columns (T' rows), whichever the cost model prefers for the
+      // block's items
+      double steps = 0.0, chunks = 0.0;
+      for (size_t q = 0; q < mine.size(); ++q) {
+        steps += kst[q];
+        chunks += (kst[q] + sp::kChunkSteps - 1) / sp::kChunkSteps;
+      }
+      const bool trans = orient_cost(Fb.cols, Fb.rows, steps, chunks, S) < orient_cost(Fb.rows, Fb.cols, steps, chunks, S);
+      const int mr = trans ? Fb.cols : Fb.rows, nr = trans ? Fb.rows : Fb.cols;
+      // the N tiles of one M tile are neighbouring jobs (they share the M-side tiles)
+      for (int tr = 0; tr < (mr + 127) / 128; ++tr)
+        for (int tc = 0; tc < (nr + sp::kCols - 1) / sp::kCols; ++tc) {
           const int i0 = int(st->k2i.size());
           int tot = 0;
           for (size_t q = 0; q < mine.size(); ++q) {
-            st->k2i.push_back(Item{st->adesc[aid[q]].slab_off + int64_t(tr) * kst[q] * S * kSub,
-                                   tp[q] + btile_off(tc, kst[q], S), kst[q], 0, sco[q]});
+            const int64_t aoff = st->adesc[aid[q]].slab_off + int64_t(trans ? tc : tr) * kst[q] * S * kSub;
+            const int64_t toff = tp[q] + btile_off(trans ? tr : tc, kst[q], S);
+            st->k2i.push_back(Item{trans ? toff : aoff, trans ? aoff : toff, kst[q], 0, sco[q]});
             tot += kst[q];
           }
-          k2jobs.push_back(Job{Fb.offset, Fb.rows, Fb.cols, Fb.rows, tr, tc, i0, int(st->k2i.size()),
-                               int32_t(rho_off[Fb.a]), int32_t(goff[f]), tot, nmma_of(Fb.cols, tc), 0});
+          k2jobs.push_back(Job{Fb.offset, mr, nr, Fb.rows, tr, tc, i0, int(st->k2i.size()),
+                               int32_t(rho_off[Fb.a]), int32_t(goff[f]), tot, nmma_of(nr, tc),
+                               trans ? sp::kJobTrans : 0});
           k2cost.push_back(tot);
         }
     }

@@ -116,15 +116,24 @@ struct Item {
 struct TaskScale {
   const uint8_t* dexp;
 };
+// A job computes an M x N tile of the product; the MMA's M side (TMEM
+// lanes) comes from the items' a_off slabs and its N side (TMEM columns) from
+// the b_off slabs.  Without kJobTrans the M side runs along the output
+// block's rows; with it the tile is computed transposed (M along the output
+// columns, N along its rows), the A and B slab arrays swap roles, and the
+// epilogue writes the transpose.  The host picks per output block the
+// orientation with the smaller padded MMA work (M is always 128 rows; N is
+// the valid extent rounded up to 16).
+constexpr int32_t kJobTrans = 1;
 struct Job {
-  int64_t out_off;       // element offset of the output block
-  int32_t rows, cols;    // valid extent of the output block
-  int32_t ld, tr, tc;    // leading dimension (rows of the block), tile indices (tc counts kCols columns)
+  int64_t out_off;       // element offset of the output block (column-major, leading dimension ld)
+  int32_t rows, cols;    // valid extent along M and along N (the block's rows and columns, swapped if transposed)
+  int32_t ld, tr, tc;    // leading dimension of the block; tile indices along M (kRows) and N (kCols)
   int32_t i0, i1;        // items
-  int32_t rsc, csc;      // offsets of the row / column exponent arrays
+  int32_t rsc, csc;      // offsets of the exponent arrays of the block's rows / columns
   int32_t nst;           // total K stages of all items
-  int32_t nmma;          // MMA N of this tile: the valid columns rounded up to 16 (<= kCols)
-  int32_t pad2;
+  int32_t nmma;          // MMA N of this tile: the valid N extent rounded up to 16 (<= kCols)
+  int32_t flags;         // kJobTrans
 };
 
 enum { MODE_T = 0, MODE_F = 1 };
@@ -359,6 +368,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         job_ring[slot] = j;
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&jq_full[slot])) : "memory");
         if (j < 0) break;
+        const bool jtrans = (jb.flags & kJobTrans) != 0;
+        const unsigned char* mslab = jtrans ? Bslab : Aslab;  // M side (TMEM lanes)
+        const unsigned char* nslab = jtrans ? Aslab : Bslab;  // N side (TMEM columns)
         const int arows = tile_rows(jb.rows, jb.tr);
         const int abytes = arows * 32, bbytes = jb.nmma * 32;  // stored bytes of one A / B sub-tile
         const uint32_t nmeta = ((uint32_t)(jb.nmma >> 4) << 8) | ((uint32_t)(arows >> 4) << 12);
@@ -382,8 +394,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                          : "memory");
             // the nk steps x S slices of A, then of B, are contiguous in their slabs
             const uint32_t dst = smem_u32(smem + st * stage_bytes);
-            const unsigned char* srcA = Aslab + item.a_off + (int64_t)k16 * S * abytes;
-            const unsigned char* srcB = Bslab + item.b_off + (int64_t)k16 * S * bbytes;
+            const unsigned char* srcA = mslab + item.a_off + (int64_t)k16 * S * abytes;
+            const unsigned char* srcB = nslab + item.b_off + (int64_t)k16 * S * bbytes;
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                 "l"(srcA), "r"(nk * S * abytes), "r"(fb)
@@ -531,16 +543,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int c0 = jb.tc * kCols + cgrp * w;
       const uint32_t lane_addr = lane_base + cgrp * w;
       const int i1 = jb.i1;
+      const bool trans = (jb.flags & kJobTrans) != 0;
+      const int p = jb.tr * kRows + row;  // this lane's index along M
       for (int it = jb.i0; it < i1 && ok; ++it) {
         const Item item = items[it];
-        // MODE_F: the item's drain exponents of this warp's columns, fetched
-        // before the chunk wait; they are the same for every lane (row), so
-        // lane v holds word v (bytes = columns 4v .. 4v + 3) and the group
-        // loop broadcasts it
+        // MODE_F: the item's drain exponents (one per output column), fetched
+        // before the chunk wait.  Output columns along N: the same for every
+        // lane, so lane v holds word v (bytes = columns 4v .. 4v + 3) and the
+        // group loop broadcasts it.  Transposed: the lane's own column, its
+        // byte replicated into all four positions.
         uint32_t dxl = 0u;
         if (MODE == MODE_F) {
-          const uint32_t* dw = reinterpret_cast<const uint32_t*>(ts.dexp + item.sc_off + c0);
-          if (lane < ng) dxl = __ldg(dw + lane);
+          if (trans) {
+            dxl = (uint32_t)__ldg(ts.dexp + item.sc_off + p) * 0x01010101u;
+          } else {
+            const uint32_t* dw = reinterpret_cast<const uint32_t*>(ts.dexp + item.sc_off + c0);
+            if (lane < ng) dxl = __ldg(dw + lane);
+          }
         }
         const int nch = (item.nst + kChunkSteps - 1) / kChunkSteps;
         for (int ch = 0; ch < nch; ++ch) {
@@ -556,7 +575,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t a = lane_addr + buf * kBufCols + g * kGroup;
             float x[4 * kGroup];  // levels 0..3, kGroup columns each
             tmem_ld_levels<kGroup>(a, x);
-            const uint32_t dxg = MODE == MODE_F ? __shfl_sync(0xffffffffu, dxl, g) : 0u;
+            const uint32_t dxg = MODE == MODE_F ? __shfl_sync(0xffffffffu, dxl, trans ? lane : g) : 0u;
             if (g == ng - 1) {
               // the warp's last TMEM read of this chunk has completed: hand
               // the buffer back before the arithmetic on the last group
@@ -616,20 +635,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       if (!ok) break;
-      // epilogue: scale by 2^(rexp + cexp - shift) and write
-      const int r = jb.tr * kRows + row;
+      // epilogue: scale by 2^(rexp(block row) + cexp(block column) - shift)
+      // and write; lane index p along M, column index q along N, the block
+      // element (p, q), or (q, p) when transposed
       const int jrows = jb.rows, jcols = jb.cols, jld = jb.ld;
-      const int* const ce_j = cexp + jb.csc;
-      const int64_t jout = jb.out_off;
-      if (r < jrows) {
-        const int er = rexp[jb.rsc + r];
+      if (p < jrows) {
+        const int ep = trans ? cexp[jb.csc + p] : rexp[jb.rsc + p];
+        const int* const eq = trans ? rexp + jb.rsc : cexp + jb.csc;
+        const int64_t obase = jb.out_off + (trans ? (int64_t)p * jld : (int64_t)p);
+        const int64_t ostep = trans ? 1 : jld;
 #pragma unroll
         for (int c = 0; c < kDrainCols; ++c) {
           if (c >= w) break;
-          const int cc = c0 + c;
-          if (cc < jcols) {
-            const int ex = er + ce_j[cc] - shift;
-            const int64_t o = jout + r + (int64_t)cc * jld;
+          const int q = c0 + c;
+          if (q < jcols) {
+            const int ex = ep + eq[q] - shift;
+            const int64_t o = obase + (int64_t)q * ostep;
             if (MODE == MODE_T) {
               // a job whose only chunk was its first leaves (hi, lo) not
               // normalised; T goes out normalised (TwoSum), since the column
