@@ -22,8 +22,9 @@
 //
 // Per H.psi: psi is copied to float-float and sliced (psi slabs); per term
 // chunk (whose intermediates fit the T budget): K1 writes T in float-float
-// (columns padded to a multiple of 4), column exponents of T and of psi
-// blocks, gamma and the int8 drain exponents, T' slabs, then K2 adds into
+// (column-major with columns padded to a multiple of 4, or row-major where
+// K1 computes the block transposed), column exponents of T and of psi
+// blocks, gamma and the 8-bit drain exponents, T' slabs, then K2 adds into
 // F.  Tasks whose four dimensions are all <= kSmallDim run afterwards in
 // FP64 on CUDA cores (small-task class).  The operator slabs are built once
 // per site by split_prepare; split_autotune picks the slice count and the
@@ -63,8 +64,9 @@ struct Unit { int32_t desc, tr, ks, pad; };
 struct Source {          // float-float matrix whose columns feed T' (K2 B operand)
   int64_t off;           // element offset in Th/Tl (sel 0) or psi_ff (sel 1)
   int32_t rows, cols, sel, cexp_off;
-  int32_t ld;            // column stride: T rows rounded up to 4 (16-byte aligned columns), psi block rows
-  int32_t pad;
+  int32_t ld;            // column stride (T rows rounded up to 4: 16-byte aligned columns; psi block rows),
+                         // or the row stride of a row-major T (its columns rounded up to 4)
+  int32_t rowmajor;      // 1: T stored row-major (written by transposed K1 jobs)
 };
 struct TPTask {
   int32_t src;           // Source index (chunk-local)
@@ -275,14 +277,23 @@ __global__ void psi_ff_kernel(const double* __restrict__ x, float* __restrict__ 
   }
 }
 
-// column exponents of the float-float sources: one CTA per source, its warps
-// take the columns in turn and their lanes the rows (contiguous in the
-// column-major block)
+// column exponents of the float-float sources: one CTA per source; in a
+// column-major block its warps take the columns in turn and their lanes the
+// rows (contiguous), in a row-major one each thread takes a column and walks
+// its rows (the lanes of a warp read neighbouring elements)
 __global__ void cexp_kernel(const Source* __restrict__ src, const float* __restrict__ Th,
                             const float* __restrict__ Ph, int* __restrict__ cexp) {
   const Source s = src[blockIdx.x];
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const float* base = (s.sel ? Ph : Th) + s.off;
+  if (s.rowmajor) {
+    for (int c = threadIdx.x; c < s.cols; c += blockDim.x) {
+      float m = 0.f;
+      for (int r = 0; r < s.rows; ++r) m = fmaxf(m, fabsf(base[int64_t(r) * s.ld + c]));
+      cexp[s.cexp_off + c] = exp_of_f(m);
+    }
+    return;
+  }
   for (int c = threadIdx.x >> 5; c < s.cols; c += nw) {
     const float* h = base + int64_t(c) * s.ld;
     float m = 0.f;
@@ -372,7 +383,17 @@ __global__ void slab_tprime_kernel(const TPTask* __restrict__ tasks, const TPUni
   const int k0 = u.ks * sp::kKS;
 #pragma unroll
   for (int q = 0; q < 16; ++q) av[q] = bv[q] = 0.f;
-  if (c < s.cols) {
+  if (c < s.cols && s.rowmajor) {
+    // row-major T: element (k0 + q, c) at (k0 + q) * ld + c; neighbouring
+    // lanes read neighbouring columns
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+      if (k0 + q < s.rows) {
+        const int64_t o = s.off + int64_t(k0 + q) * s.ld + c;
+        av[q] = H[o];
+        bv[q] = Lo[o];
+      }
+  } else if (c < s.cols) {
     const int64_t o = s.off + k0 + int64_t(c) * s.ld;
     if (!s.sel) {
 #pragma unroll
@@ -818,26 +839,32 @@ int split_prepare(su2_env* env, int S, std::string& err) {
       const OpBlock& Db = R.blocks[t.dblk];
       const int k1 = E.rows, k2 = E.cols, n = Db.rows;
       const int id = int(st->src.size() - ch.src0);
-      const int ldT = (k1 + 3) & ~3;
-      st->src.push_back(Source{tsz, k1, n, 0, int32_t(csz), ldT, 0});
+      const int kst2 = (k2 + sp::kKS - 1) / sp::kKS;
+      const double nch2 = (kst2 + sp::kChunkSteps - 1) / sp::kChunkSteps;
+      // T = E D^T with M along the rows of T (E rows; T column-major) or,
+      // transposed, along its columns (D rows; T row-major, so that the
+      // lanes of a warp still write neighbouring elements), whichever the
+      // cost model prefers
+      const bool trans = orient_cost(n, k1, kst2, nch2, S) < orient_cost(k1, n, kst2, nch2, S);
+      const int ldT = trans ? (n + 3) & ~3 : (k1 + 3) & ~3;
+      st->src.push_back(Source{tsz, k1, n, 0, int32_t(csz), ldT, trans ? 1 : 0});
       csz += n;
       umap[key] = id;
-      const int kst2 = (k2 + sp::kKS - 1) / sp::kKS;
-      // T = E D^T with M along the rows of T.  (The transposed orientation
-      // writes T with the lanes of a warp a column apart; measured on qc32 it
-      // cost more in the epilogue than it saved in MMA and drain work.)
-      // The column tiles of one row tile are neighbouring jobs (they share the E tile).
-      for (int tr = 0; tr < (k1 + 127) / 128; ++tr)
-        for (int tc = 0; tc < (n + sp::kCols - 1) / sp::kCols; ++tc) {
+      const int mr = trans ? n : k1, nr = trans ? k1 : n;
+      const SlabDesc& mdesc = trans ? st->ddesc[t.dblk] : st->edesc[t.e];
+      const SlabDesc& ndesc = trans ? st->edesc[t.e] : st->ddesc[t.dblk];
+      // the N tiles of one M tile are neighbouring jobs (they share the M-side tile)
+      for (int tr = 0; tr < (mr + 127) / 128; ++tr)
+        for (int tc = 0; tc < (nr + sp::kCols - 1) / sp::kCols; ++tc) {
           const int ii = int(st->k1i.size());
-          st->k1i.push_back(Item{st->edesc[t.e].slab_off + int64_t(tr) * kst2 * S * kSub,
-                                 st->ddesc[t.dblk].slab_off + btile_off(tc, kst2, S), kst2, 0, -1});
-          k1jobs.push_back(Job{tsz, k1, n, ldT, tr, tc, ii, ii + 1, int32_t(eps_off[t.e]),
-                               int32_t(zeta_off[t.dblk]), kst2, nmma_of(n, tc), 0});
+          st->k1i.push_back(Item{mdesc.slab_off + int64_t(tr) * kst2 * S * kSub,
+                                 ndesc.slab_off + btile_off(tc, kst2, S), kst2, 0, -1});
+          k1jobs.push_back(Job{tsz, mr, nr, ldT, tr, tc, ii, ii + 1, int32_t(eps_off[t.e]),
+                               int32_t(zeta_off[t.dblk]), kst2, nmma_of(nr, tc), trans ? sp::kJobTrans : 0});
           k1cost.push_back(kst2);
         }
       ch.k1_flops += 2.0 * k1 * k2 * n;
-      tsz += int64_t(ldT) * n;
+      tsz += int64_t(ldT) * (trans ? k1 : n);
       return id;
     };
     // K2 jobs grouped by output block
@@ -901,7 +928,7 @@ int split_prepare(su2_env* env, int S, std::string& err) {
           }
           k2jobs.push_back(Job{Fb.offset, mr, nr, Fb.rows, tr, tc, i0, int(st->k2i.size()),
                                int32_t(rho_off[Fb.a]), int32_t(goff[f]), tot, nmma_of(nr, tc),
-                               trans ? sp::kJobTrans : 0});
+                               trans ? (sp::kJobTrans | sp::kJobLaneStride) : 0});
           k2cost.push_back(tot);
         }
     }

@@ -120,11 +120,14 @@ struct TaskScale {
 // lanes) comes from the items' a_off slabs and its N side (TMEM columns) from
 // the b_off slabs.  Without kJobTrans the M side runs along the output
 // block's rows; with it the tile is computed transposed (M along the output
-// columns, N along its rows), the A and B slab arrays swap roles, and the
-// epilogue writes the transpose.  The host picks per output block the
-// orientation with the smaller padded MMA work (M is always 128 rows; N is
-// the valid extent rounded up to 16).
+// columns, N along its rows) and the A and B slab arrays swap roles.  The
+// host picks per output block the orientation with the smaller modelled cost
+// (M is always 128 rows; N is the valid extent rounded up to 16).  The
+// element of lane p and TMEM column q is written at out_off + p + q * ld, or
+// with kJobLaneStride at out_off + p * ld + q (a transposed tile of a
+// column-major block; a transposed tile of a row-major block needs no flag).
 constexpr int32_t kJobTrans = 1;
+constexpr int32_t kJobLaneStride = 2;
 struct Job {
   int64_t out_off;       // element offset of the output block (column-major, leading dimension ld)
   int32_t rows, cols;    // valid extent along M and along N (the block's rows and columns, swapped if transposed)
@@ -133,7 +136,7 @@ struct Job {
   int32_t rsc, csc;      // offsets of the exponent arrays of the block's rows / columns
   int32_t nst;           // total K stages of all items
   int32_t nmma;          // MMA N of this tile: the valid N extent rounded up to 16 (<= kCols)
-  int32_t flags;         // kJobTrans
+  int32_t flags;         // kJobTrans, kJobLaneStride
 };
 
 enum { MODE_T = 0, MODE_F = 1 };
@@ -642,8 +645,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (p < jrows) {
         const int ep = trans ? cexp[jb.csc + p] : rexp[jb.rsc + p];
         const int* const eq = trans ? rexp + jb.rsc : cexp + jb.csc;
-        const int64_t obase = jb.out_off + (trans ? (int64_t)p * jld : (int64_t)p);
-        const int64_t ostep = trans ? 1 : jld;
+        const bool lstride = (jb.flags & kJobLaneStride) != 0;
+        const int64_t obase = jb.out_off + (lstride ? (int64_t)p * jld : (int64_t)p);
+        const int64_t ostep = lstride ? 1 : jld;
 #pragma unroll
         for (int c = 0; c < kDrainCols; ++c) {
           if (c >= w) break;
