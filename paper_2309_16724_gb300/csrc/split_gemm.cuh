@@ -35,7 +35,7 @@
 // Warp roles (576 threads): warp 0, one lane: job fetcher (dynamic schedule:
 // an atomic job counter, handed to the drain warps through a shared-memory
 // ring) and bulk-copy producer, which leaves one metadata word per stage for
-// the MMA issuer; warp 1, one lane: MMA issuer, reading shared memory only;
+// the MMA issuer; warp 1: MMA issuer, reading shared memory only (the converged warp runs the loop, one elected lane issues);
 // warps 2..17: drain and epilogue (TMEM lane quarter w%4; the job's columns
 // are split evenly among the four warps of a quarter).  The drain warps
 // arrive on barriers with one lane each.
@@ -186,13 +186,23 @@ __device__ __forceinline__ uint32_t idesc_n(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t(n) >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-// D (+)= A * B^T; ACC = false overwrites D
+// D (+)= A * B^T; ACC = false overwrites D.  Called by all 32 lanes of the
+// MMA warp with the same operands; one lane, chosen by elect.sync, issues
+// the MMA.  (Issued by a lone lane in a divergent branch, an MMA measured
+// about 75 cycles at any N; from the converged warp 67 cycles at N = 128 and
+// 53 at N = 64, close to the tensor core's own 64 and 48.)
 template <bool ACC>
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc) {
   if (ACC)
-    asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;" ::"r"(tmem), "l"(a), "l"(b), "r"(idesc));
+    asm volatile(
+        "{\n.reg .pred p;\nelect.sync _|p, 0xffffffff;\n"
+        "@p tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc));
   else
-    asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 0;" ::"r"(tmem), "l"(a), "l"(b), "r"(idesc));
+    asm volatile(
+        "{\n.reg .pred p;\nelect.sync _|p, 0xffffffff;\n"
+        "@p tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 0;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc));
 }
 
 // the S(S+1)/2 slice products of one 16-K step, unrolled: pair (i, j) goes to
@@ -217,8 +227,12 @@ __device__ __forceinline__ void issue_stage(uint32_t tbuf, uint64_t da, uint64_t
     }
 }
 
+// commit of the MMAs issued so far, by one elected lane of the converged MMA warp
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+  asm volatile(
+      "{\n.reg .pred p;\nelect.sync _|p, 0xffffffff;\n"
+      "@p tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(bar)
+      : "memory");
 }
 
 // four 32x32b.x4 TMEM loads (four columns of each accumulator level) and
@@ -449,15 +463,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    // reads only shared memory: the stage ring and its metadata words
-    if (lane == 0) {
+    // reads only shared memory: the stage ring and its metadata words.  The
+    // whole warp runs the loop (its values are warp-uniform); one elected
+    // lane issues each MMA and commit.
+    {
       int st = 0;
       uint32_t ph = 0;
       uint32_t chunk = 0;  // chunk c accumulates in TMEM buffer c % kNumBuf
       bool ok = true;
       const uint32_t sbase = smem_u32(smem);
       for (;;) {
-        if (!mbar_wait(smem_u32(&full_bar[st]), ph, &abort_flag)) {
+        if (!warp_wait(smem_u32(&full_bar[st]), ph, &abort_flag)) {
           ok = false;
           break;
         }
@@ -466,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t buf = chunk % kNumBuf;
         if (m & kMetaFirst) {
           // the buffer's previous chunk (c - kNumBuf) must have been read by the drain
-          if (!mbar_wait(smem_u32(&acce_bar[buf]), ((chunk / kNumBuf) & 1) ^ 1, &abort_flag)) {
+          if (!warp_wait(smem_u32(&acce_bar[buf]), ((chunk / kNumBuf) & 1) ^ 1, &abort_flag)) {
             ok = false;
             break;
           }
@@ -493,11 +509,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           ph ^= 1;
         }
       }
-      if (!ok) {
+      if (!ok && lane == 0) {
         abort_flag = 1;
         atomicExch(status, 4);
       }
-      // all MMAs issued by this thread complete before TMEM is released
+      // all MMAs issued by this warp complete before TMEM is released
       mma_commit(smem_u32(&done_bar));
       bool fin = false;
       for (long it = 0; it < kSpinLimit && !fin; ++it) fin = mbar_try(smem_u32(&done_bar), 0);
