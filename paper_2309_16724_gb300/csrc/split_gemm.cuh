@@ -35,7 +35,8 @@
 // Warp roles (576 threads): warp 0, one lane: job fetcher (dynamic schedule:
 // an atomic job counter, handed to the drain warps through a shared-memory
 // ring) and bulk-copy producer, which leaves one metadata word per stage for
-// the MMA issuer; warp 1: MMA issuer, reading shared memory only (the converged warp runs the loop, one elected lane issues);
+// the MMA issuer; warp 1: MMA issuer, reading shared memory only (the
+// converged warp runs the loop, one elected lane issues each MMA);
 // warps 2..17: drain and epilogue (TMEM lane quarter w%4; the job's columns
 // are split evenly among the four warps of a quarter).  The drain warps
 // arrive on barriers with one lane each.
