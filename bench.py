@@ -2,6 +2,11 @@
 
 One step = one full H.psi (every operator-table row, every task) of the
 seeded synthetic workload, inputs resident in HBM.  Prints one JSON line.
+The default workload is the L = N = 48, D = 4096 ab initio configuration
+(qc48).  Beside the split-precision value the line carries the native-FP64
+path's rate on the same workload (a term shard of it, timed), the split/FP64
+ratio and the split error against the FP64 result on that shard, and the
+oracle timed on the host cores on a flop-weighted sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME]
                   [--prec split|fp64] [--impl ours|reference]
@@ -28,7 +33,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "H·ψ TFLOPS/GB300 (SU(2), U(1)-equiv): split-prec vs FP64 at ≤1e-10 rel err"
-DEFAULT_CONFIG = "qc32"
+DEFAULT_CONFIG = "qc48"   # L = N = 48, D = 4096: the batching configuration the throughput target is set on
 FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal FP64 rate)
 
 
@@ -107,64 +112,15 @@ class ClockSampler:
 
 
 _ORACLE_WORKER = r"""
-import os, sys, time, json
+import os, sys, time, json, pickle
 sys.path.insert(0, ROOT)
 import numpy as np, synth
-from oracle import model, sectors, heff, env
-w, W, cfg_name, repeats, budget, warm = (int(sys.argv[1]), int(sys.argv[2]), sys.argv[3], int(sys.argv[4]),
-                                        float(sys.argv[5]), int(sys.argv[6]))
-cfg = synth.CONFIGS[cfg_name]
-left, right = synth.middle_bond_sectors(cfg)
-blocks, n = sectors.build_blocks(left, right, cfg.site_kind, cfg.N, cfg.twoS)
-tab = model.heisenberg_table() if cfg.site_kind == synth.SPIN_HALF else model.qc_skeleton_table(cfg.n_left, cfg.n_right)
-def work(ts):
-    k1, k2 = {}, 0
-    for t in ts:
-        E, F = blocks[t.e], blocks[t.f]
-        if t.D is not None:
-            k1[(tab.terms[t.term].D, t.D, t.e)] = 2 * E.rows * E.cols * F.cols
-        if t.A is not None:
-            k2 += 2 * F.rows * E.rows * F.cols
-    return sum(k1.values()) + k2
-# the same deterministic sample in every worker: the full H.psi of a small
-# config, else whole output blocks spread over the size range, up to W x budget
-# flops; its tasks are shared among the workers, longest first
-if n < 1_000_000:
-    e = env.build_env(tab, cfg, left, right)
-    sample_tasks = heff.build_tasks(tab, left, right, blocks, cfg.twoS)
-    sample = f"full H.psi of {cfg_name} (all tasks) on {W} processes"
-else:
-    order = sorted(range(len(blocks)), key=lambda f: -blocks[f].rows * blocks[f].cols)
-    cand = order[:: max(1, len(order) // (12 * W))][: 12 * W]
-    e = env.LazySyntheticEnv(tab, cfg, left, right)
-    ts_all = heff.build_tasks(tab, left, right, blocks, cfg.twoS, only_f=set(cand))
-    by_f = {}
-    for t in ts_all:
-        by_f.setdefault(t.f, []).append(t)
-    keep, acc = [], 0
-    for f in cand:
-        if f not in by_f:
-            continue
-        wf = work(by_f[f])
-        if keep and acc + wf > W * budget:
-            continue
-        keep.append(f); acc += wf
-    sample_tasks = [t for f in keep for t in by_f[f]]
-    sample = f"{len(keep)} of {len(blocks)} output blocks of {cfg_name} (all tasks into them) on {W} processes"
-flops = work(sample_tasks)  # the sample's flops (library definition), reported by worker 0 only
-def cost(t):
-    E, F = blocks[t.e], blocks[t.f]
-    return 2 * (F.rows * E.rows * E.cols + F.rows * E.cols * F.cols)
-load = [0] * W
-tasks = []
-for i in sorted(range(len(sample_tasks)), key=lambda i: (-cost(sample_tasks[i]), i)):
-    r = min(range(W), key=lambda k: (load[k], k))
-    load[r] += cost(sample_tasks[i])
-    if r == w:
-        tasks.append(sample_tasks[i])
-if w != 0:
-    flops = 0
-psi = synth.gaussian_psi(n, synth.psi_seed(cfg))
+from oracle import heff
+w, W, path, repeats, warm = int(sys.argv[1]), int(sys.argv[2]), sys.argv[3], int(sys.argv[4]), int(sys.argv[5])
+with open(path, "rb") as f:
+    d = pickle.load(f)
+tab, e, blocks, n, psi, parts = d["table"], d["env"], d["blocks"], d["n"], d["psi"], d["parts"]
+tasks = parts[w]
 print("ready", flush=True)
 sys.stdin.readline()  # start together
 for r in range(warm):
@@ -172,26 +128,99 @@ for r in range(warm):
 times = []
 for r in range(repeats):
     t0 = time.perf_counter(); heff.apply_heff(tab, e, tasks, blocks, n, psi); times.append(time.perf_counter() - t0)
-print(json.dumps({"flops": flops, "times": times, "sample": sample}), flush=True)
+print(json.dumps({"times": times}), flush=True)
 """
 
 
-def oracle_cpu_baseline(cfg_name: str, repeats: int, flop_budget: float = 3e10, workers: int = 0, warmup: int = 0):
+def _oracle_sample(cfg_name: str, W: int, frac: float = 0.02, min_flops: float = 2e10):
+    """The oracle's problem for a config and a bounded sample of its H.psi:
+    the full H.psi when it is small, else output blocks drawn with
+    probability proportional to their flops (seeded, without replacement)
+    until the drawn blocks hold `frac` of the flops (at least `min_flops`);
+    every task into a drawn block is kept.  Tasks are dealt to W workers,
+    longest first.  Returns (pickle path, sample flops, total flops,
+    description)."""
+    import pickle
+    import numpy as np
+    from oracle import env as oenv, heff as oheff, model as omodel, sectors as osec
+    cfg = synth.CONFIGS[cfg_name]
+    left, right = synth.middle_bond_sectors(cfg)
+    blocks, n = osec.build_blocks(left, right, cfg.site_kind, cfg.N, cfg.twoS)
+    tab = (omodel.heisenberg_table() if cfg.site_kind == synth.SPIN_HALF
+           else omodel.qc_skeleton_table(cfg.n_left, cfg.n_right))
+
+    def work(ts):
+        k1, k2 = {}, 0
+        for t in ts:
+            E, F = blocks[t.e], blocks[t.f]
+            if t.D is not None:
+                k1[(tab.terms[t.term].D, t.D, t.e)] = 2 * E.rows * E.cols * F.cols
+            if t.A is not None:
+                k2 += 2 * F.rows * E.rows * F.cols
+        return sum(k1.values()) + k2
+
+    if n < 1_000_000:
+        e = oenv.build_env(tab, cfg, left, right)
+        sample_tasks = oheff.build_tasks(tab, left, right, blocks, cfg.twoS)
+        total = work(sample_tasks)
+        flops = total
+        desc = f"full H.psi of {cfg_name} (all tasks) on {W} processes"
+    else:
+        e = oenv.LazySyntheticEnv(tab, cfg, left, right)
+        all_tasks = oheff.build_tasks(tab, left, right, blocks, cfg.twoS)
+        by_f = {}
+        for t in all_tasks:
+            by_f.setdefault(t.f, []).append(t)
+        wf = {f: work(ts) for f, ts in by_f.items()}
+        total = sum(wf.values())
+        rng = np.random.default_rng(20230928)
+        fs = sorted(wf)
+        p = np.array([wf[f] for f in fs], dtype=np.float64)
+        order = rng.choice(len(fs), size=len(fs), replace=False, p=p / p.sum())
+        keep, acc = [], 0
+        target = max(frac * total, min_flops)
+        for i in order:
+            if acc >= target:
+                break
+            keep.append(fs[i])
+            acc += wf[fs[i]]
+        sample_tasks = [t for f in keep for t in by_f[f]]
+        flops = acc
+        desc = (f"{len(keep)} of {len(blocks)} output blocks of {cfg_name} drawn with probability proportional "
+                f"to their flops ({100 * flops / total:.1f} % of the H.psi flops, every task into them), "
+                f"on {W} processes; rate extrapolated to the whole H.psi")
+
+    def cost(t):
+        E, F = blocks[t.e], blocks[t.f]
+        return 2 * (F.rows * E.rows * E.cols + F.rows * E.cols * F.cols)
+
+    load = [0] * W
+    parts = [[] for _ in range(W)]
+    for i in sorted(range(len(sample_tasks)), key=lambda i: (-cost(sample_tasks[i]), i)):
+        r = min(range(W), key=lambda k: (load[k], k))
+        load[r] += cost(sample_tasks[i])
+        parts[r].append(sample_tasks[i])
+    psi = synth.gaussian_psi(n, synth.psi_seed(cfg))
+    path = tempfile.mktemp(prefix="oracle_sample_", suffix=".pkl")
+    with open(path, "wb") as f:
+        pickle.dump({"table": tab, "env": e, "blocks": blocks, "n": n, "psi": psi, "parts": parts}, f)
+    return path, flops, total, desc
+
+
+def oracle_cpu_baseline(cfg_name: str, repeats: int, workers: int = 0, warmup: int = 0):
     """Times the FP64 oracle (as it stands) on the host cores: `workers`
     processes (default: one per core), one BLAS thread each, `warmup`
-    untimed repeats first.  Small configs
-    on one worker: the full H.psi.  Otherwise a bounded, deterministic sample
-    of whole output blocks (every task into them) shared among the workers,
-    which start their timed repeats together.  Returns (TFLOP/s, cores,
-    sample description, seconds per repeat): the flops of the sample over the
-    slowest worker's time, median over the repeats.  Flops follow the
-    library's definition (K1 counted once per distinct (right block, input
-    block))."""
+    untimed repeats first, then `repeats` timed ones started together.  The
+    work is the full H.psi of a small config, else a flop-weighted sample of
+    output blocks (`_oracle_sample`).  Returns (TFLOP/s, cores, sample
+    description, seconds per repeat): the sample's flops over the slowest
+    worker's time, median over the repeats.  Flops follow the library's
+    definition (K1 counted once per distinct (right block, input block))."""
     W = workers or (os.cpu_count() or 1)
+    path, flops, total, desc = _oracle_sample(cfg_name, W)
     envv = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = _ORACLE_WORKER.replace("sys.path.insert(0, ROOT)", f"sys.path.insert(0, {ROOT!r})")
-    procs = [subprocess.Popen([sys.executable, "-c", code, str(w), str(W), cfg_name, str(repeats), str(flop_budget),
-                               str(warmup)],
+    procs = [subprocess.Popen([sys.executable, "-c", code, str(w), str(W), path, str(repeats), str(warmup)],
                               stdin=subprocess.PIPE, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=envv)
              for w in range(W)]
     try:
@@ -204,7 +233,7 @@ def oracle_cpu_baseline(cfg_name: str, repeats: int, flop_budget: float = 3e10, 
             p.stdin.flush()
         outs = []
         for p in procs:
-            out, err = p.communicate(timeout=600)
+            out, err = p.communicate(timeout=900)
             if p.returncode != 0:
                 raise RuntimeError(err[-2000:])
             outs.append(json.loads(out.strip().splitlines()[-1]))
@@ -212,10 +241,13 @@ def oracle_cpu_baseline(cfg_name: str, repeats: int, flop_budget: float = 3e10, 
         for p in procs:
             if p.poll() is None:
                 p.kill()
-    flops = sum(d["flops"] for d in outs)
+        try:
+            os.unlink(path)
+        except OSError:
+            pass
     per_rep = [max(d["times"][r] for d in outs) for r in range(repeats)]
     t = statistics.median(per_rep)
-    return flops / t / 1e12, W, f"{outs[0]['sample']}, median of {repeats}", t
+    return flops / t / 1e12, W, f"{desc}, median of {repeats}", t
 
 
 def run_reference(args):
@@ -285,17 +317,24 @@ def main():
     info = env.info
     flops = info["flops_su2"]
 
-    rel_err_fp64 = None
-    if prec != P.SU2_FP64:
-        ref = torch.empty_like(psi)
-        P.apply_heff(ctx, env, psi, ref, P.SU2_FP64)
+    def status_ok(where):
+        """The device status word after a section: a bounded device wait that
+        gave up makes the bench fail instead of reporting a faster, aborted run."""
+        st = ctx.status()
+        if st:
+            raise RuntimeError(f"device status {st} after {where}: a bounded device wait gave up")
+
+    # the split result before any timing; the last timed step must reproduce
+    # it bit for bit (the path is deterministic: no atomics in the sums)
+    first = None
+    if split:
         P.apply_heff(ctx, env, psi, out, prec)
         torch.cuda.synchronize()
-        rel_err_fp64 = float(torch.linalg.norm(out - ref) / torch.linalg.norm(ref))
-
+        first = out.clone()
     for _ in range(args.warmup):
         P.apply_heff(ctx, env, psi, out, prec)
     torch.cuda.synchronize()
+    status_ok("warm-up")
     env.profile(True)
     env.profile_reset()
     clocks = ClockSampler(local)
@@ -316,6 +355,10 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
+    status_ok("the timed steps")
+    repeat_identical = bool(torch.equal(out, first)) if first is not None else None
+    if first is not None and not repeat_identical:
+        raise RuntimeError("the last timed H.psi differs from the first one")
     step_ms = [a.elapsed_time(b) for a, b in evs]
     tot_ms = sum(step_ms)
     prof = env.profile_read()
@@ -327,20 +370,22 @@ def main():
     value = world * args.steps * flops / (tot_ms / 1e3) / 1e12
 
     # end to end through the C-ABI with host buffers (copies inside the call)
+    e2e_steps = max(1, min(args.steps, 5))
     hin = torch.from_numpy(synth.gaussian_psi(n, synth.psi_seed(cfg))).pin_memory()
     hout = torch.empty(n, dtype=torch.float64).pin_memory()
     P.apply_heff_host(ctx, env, hin.numpy(), hout.numpy(), prec)
     e2e_t = []
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         t1 = time.perf_counter()
         P.apply_heff_host(ctx, env, hin.numpy(), hout.numpy(), prec)
         e2e_t.append(time.perf_counter() - t1)
+    status_ok("the end-to-end steps")
     e2e_tot = sum(e2e_t)
     if world > 1:
         t = torch.tensor([e2e_tot], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_tot = float(t.item())
-    e2e_value = world * args.steps * flops / e2e_tot / 1e12
+    e2e_value = world * e2e_steps * flops / e2e_tot / 1e12
 
     # one Davidson iteration (H.psi + FP64 Gram-Schmidt, Rayleigh-Ritz, residual,
     # correction), eager and as a CUDA-graph replay; host-timed (each step
@@ -349,13 +394,53 @@ def main():
     for graph in (False, True):
         d = P.Davidson(ctx, env, psi, tol=1e-14, max_sub=24, keep=2, max_iter=1000, prec=prec, use_graph=graph)
         d.step()
-        d.step()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        for _ in range(3):
+        for _ in range(2):
             d.step()
-        dav_ms["iter_ms_graph" if graph else "iter_ms_eager"] = (time.perf_counter() - t1) / 3 * 1e3
+        dav_ms["iter_ms_graph" if graph else "iter_ms_eager"] = (time.perf_counter() - t1) / 2 * 1e3
         d.close()
+    status_ok("the Davidson steps")
+
+    # the native-FP64 path on the same workload: a term shard (the operator
+    # terms dealt to shards in longest-processing-time order of their flops),
+    # timed with CUDA events; its rate is the shard's flops over its time.
+    # On the same shard, the split H.psi against the FP64 one.
+    fp64 = None
+    rel_err_fp64 = None
+    if split and rank == 0:
+        n_sh = max(1, int(round(flops / 4e12)))
+        if n_sh > 1:
+            _, senv = workload.build(ctx, cfg, prepare_split=True, n_slices=info["split_slices"], shard=(0, n_sh))
+        else:
+            senv = env
+        sfl = senv.info["flops_su2"]
+        y64 = torch.empty_like(psi)
+        ysp = torch.empty_like(psi)
+        P.apply_heff(ctx, senv, psi, y64, P.SU2_FP64)
+        P.apply_heff(ctx, senv, psi, ysp, P.SU2_SPLIT_BF16)
+        torch.cuda.synchronize()
+        rel_err_fp64 = float(torch.linalg.norm(ysp - y64) / torch.linalg.norm(y64))
+        fms = []
+        for _ in range(2):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            P.apply_heff(ctx, senv, psi, y64, P.SU2_FP64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            fms.append(a.elapsed_time(b))
+        status_ok("the FP64-path steps")
+        fv = sfl / (statistics.median(fms) / 1e3) / 1e12
+        fp64 = {"value": fv, "unit": "TFLOP/s", "ms_per_step_sample": statistics.median(fms),
+                "sample": (f"term shard 0 of {n_sh} ({100 * sfl / flops:.1f} % of the H.psi flops), "
+                           "median of 2 timed H.psi after one untimed" if n_sh > 1 else
+                           "the whole H.psi, median of 2 timed after one untimed"),
+                "split_over_fp64": value / world / fv,
+                "frac_of_nominal_fp64": fv / FP64_PEAK_TFLOPS}
+        if senv is not env:
+            senv.close()
 
     # roofline of the dominant kernel
     launch_count = prof.pop("kernel_launches")[0]
@@ -387,6 +472,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == P.SU2_FP64 else "bf16",
             "data": "synthetic",
             "config": {"workload": cfg.name, "L": cfg.L, "N": cfg.N, "twoS": cfg.twoS, "D": cfg.D,
+                       "operators": "synthetic-entry environments (ab initio normal/complementary term "
+                                    "structure, counter-generated entries)" if cfg.site_kind else
+                                    "Heisenberg, renormalised from a seeded MPS",
                        "prec": "fp64" if prec == P.SU2_FP64 else
                        "bf16 slices on tcgen05, fp32 accumulate (exact per 192-K chunk), float-float/fp64 recombine",
                        "psi_len": n, "terms": info["n_terms"], "tasks": info["n_tasks"],
@@ -397,7 +485,10 @@ def main():
             "value_u1_equiv": value * info["r_d"],
             "flops_su2_per_step": flops,
             "rel_err_vs_fp64": rel_err_fp64,
-            "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+            "repeat_bit_identical": repeat_identical,
+            "fp64_path": fp64,
+            "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+                    "steps": e2e_steps},
             "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                          "frac": achieved / peak if peak else None,
                          "traffic": (k2_traffic(cfg.name, info["split_slices"], info["split_stage_k"])
@@ -409,6 +500,7 @@ def main():
             "clocks": clk,
             "cpu_baseline": cpu,
             "build_s": build_s,
+            "hbm_gb_in_use": round((torch.cuda.mem_get_info(dev)[1] - torch.cuda.mem_get_info(dev)[0]) / 1e9, 1),
         }
         print(json.dumps(line))
     if world > 1:

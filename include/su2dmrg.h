@@ -112,6 +112,15 @@ typedef struct {
                               paper's own distribution is by GPU task
                               queues (Sec. III); this is a data-parallel
                               split of Eq. 2's sum over i.                 */
+  int32_t spin_limit;      /* polls of each work-loop mbarrier wait in the
+                              split GEMM before the CTA gives up, sets the
+                              device status to SU2_ETIMEOUT and returns
+                              (0: 2^26, seconds of waiting).  A CTA that
+                              gives up still waits the full 2^26 polls for
+                              its own bulk copies and MMAs before it frees
+                              TMEM and exits.  Small values are for testing
+                              the timeout path; the H.psi result of a call
+                              that timed out is undefined.                 */
 } su2_env_opts;
 
 typedef struct {
@@ -127,6 +136,8 @@ typedef struct {
   double split_err_est;    /* autotune: relative difference of the chosen
                               S to S = 6 on the test vector (-1: not
                               measured)                                    */
+  int64_t t_chunk_bytes;   /* FP64 bytes of the intermediate T of the
+                              largest term chunk (native-FP64 path)        */
 } su2_env_info;
 
 typedef struct {
@@ -152,6 +163,14 @@ const char* su2_last_error(su2_ctx* ctx);
  * bounded device-side wait gave up (SU2_ETIMEOUT).  The call itself
  * returns SU2_ECUDA if the stream reports an error. */
 int su2_ctx_status(su2_ctx* ctx, int32_t* device_status);
+/* Host watchdog: polls the context stream (cudaStreamQuery) until its work
+ * is done or `timeout_s` seconds have passed (timeout_s < 0: no limit).
+ * SU2_ETIMEOUT if the stream is still busy at the limit (the work keeps
+ * running; the call may be repeated), SU2_ECUDA if the stream reports an
+ * error, otherwise the device status word is read and cleared as in
+ * su2_ctx_status and a non-zero word returns SU2_ETIMEOUT.  The paper has no
+ * counterpart; failure detection of the library. */
+int su2_ctx_wait(su2_ctx* ctx, double timeout_s);
 
 /* Sector-table of psi (Sec. II.A, Eq. 3): all blocks (a, s1, s2, b, jL1,
  * j2R) with N_a + n1 + n2 + N_b = N_target and the couplings a x s1 -> jL1,
@@ -185,10 +204,14 @@ int su2_env_operator_block(const su2_env* env, int32_t side, int32_t op, int32_t
 int su2_env_destroy(su2_env* env);
 
 /* F = H_eff psi (Eq. 2 over the sector-task-table).  psi_in, psi_out:
- * device pointers, 8-byte aligned, psi_len doubles, not overlapping. */
+ * device pointers, 8-byte aligned, psi_len doubles, not overlapping.  The
+ * call does not synchronise: a bounded device wait that gives up during it
+ * is reported by the next su2_ctx_status / su2_ctx_wait (or by a
+ * synchronising call), and F is then undefined. */
 int su2_apply_heff(su2_ctx* ctx, const su2_env* env, const double* psi_in_dev,
                    double* psi_out_dev, int32_t prec);
-/* Same with host buffers: copies psi in, runs, copies F out, synchronises. */
+/* Same with host buffers: copies psi in, runs, copies F out, synchronises;
+ * SU2_ETIMEOUT if a bounded device-side wait gave up during the call. */
 int su2_apply_heff_host(su2_ctx* ctx, const su2_env* env, const double* psi_in_host,
                         double* psi_out_host, int32_t prec);
 /* H.psi for callers that cannot allocate device memory while they run (a
@@ -204,7 +227,13 @@ int su2_apply_heff_host(su2_ctx* ctx, const su2_env* env, const double* psi_in_h
  * rejected with SU2_EINVAL (build it with t_budget_bytes <= 64 MiB).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, once per device); make that first call before any
- * stream capture.  All calls share the one array: calls that overlap on the
+ * stream capture.  The cached address belongs to the device's primary
+ * context: do not use this entry point on a device after cudaDeviceReset in
+ * the same process.  The array is resident on a GPU once the library's device module
+ * is loaded there; under CUDA's lazy module loading that load (and the
+ * driver's 64 MiB allocation for it) may happen inside the first call on a
+ * device, so a caller that must not allocate at all makes one call at
+ * start-up.  All calls share the one array: calls that overlap on the
  * GPU (other streams, other threads) race on it; calls ordered on one stream
  * are safe.  The array keeps the last call's contents; nothing in it has to
  * start at zero (every element of T that is read is written first). */
@@ -221,7 +250,11 @@ int su2_diag_heff(su2_ctx* ctx, const su2_env* env, double* diag_dev);
 int su2_davidson_create(su2_ctx* ctx, const su2_env* env, const double* psi0_dev,
                         const su2_dav_opts* opts, su2_dav** out);
 int su2_davidson_step(su2_ctx* ctx, su2_dav* dav, double* theta, double* resnorm);
-/* Runs steps until ||r|| <= tol or max_iter; SU2_ENOTCONV if not reached. */
+/* su2_davidson_step synchronises on every iteration and returns
+ * SU2_ETIMEOUT (clearing the device status word) if a bounded device-side
+ * wait of that iteration gave up; theta and the residual are then not
+ * updated.  Runs steps until ||r|| <= tol or max_iter; SU2_ENOTCONV if not
+ * reached. */
 int su2_davidson_solve(su2_ctx* ctx, su2_dav* dav, double* theta, double* resnorm,
                        int32_t* iterations);
 int su2_energy(const su2_dav* dav, double* E);

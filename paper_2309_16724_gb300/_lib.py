@@ -20,7 +20,7 @@ SU2_SITE_SPIN_HALF, SU2_SITE_ORBITAL = 0, 1
 SU2_MODEL_HEISENBERG, SU2_MODEL_QC_SKELETON, SU2_MODEL_CASIMIR_S2, SU2_MODEL_CASIMIR_N = range(4)
 
 SYMBOLS = [
-    "su2_ctx_create", "su2_ctx_destroy", "su2_last_error", "su2_ctx_status", "su2_build_sectors", "su2_sectors_query",
+    "su2_ctx_create", "su2_ctx_destroy", "su2_last_error", "su2_ctx_status", "su2_ctx_wait", "su2_build_sectors", "su2_sectors_query",
     "su2_sectors_destroy", "su2_build_environment", "su2_env_query", "su2_env_tasks", "su2_env_operator_block", "su2_env_destroy",
     "su2_apply_heff", "su2_apply_heff_host", "su2_apply_heff_static_scratch", "su2_diag_heff", "su2_davidson_create", "su2_davidson_step",
     "su2_davidson_solve", "su2_energy", "su2_davidson_vector", "su2_davidson_destroy",
@@ -51,7 +51,7 @@ class Hamiltonian(C.Structure):
 class EnvOpts(C.Structure):
     _fields_ = [("t_budget_bytes", C.c_int64), ("n_slices", C.c_int32), ("prepare_split", C.c_int32),
                 ("autotune", C.c_int32), ("split_tol", C.c_double), ("shard_rank", C.c_int32),
-                ("shard_count", C.c_int32)]
+                ("shard_count", C.c_int32), ("spin_limit", C.c_int32)]
 
 
 class EnvInfo(C.Structure):
@@ -59,7 +59,7 @@ class EnvInfo(C.Structure):
                 ("n_tasks", C.c_int64), ("n_k1", C.c_int64), ("n_chunks", C.c_int64),
                 ("flops_su2", C.c_double), ("flops_u1_equiv", C.c_double), ("r_d", C.c_double),
                 ("env_bytes", C.c_double), ("split_slices", C.c_int32), ("split_stage_k", C.c_int32),
-                ("split_err_est", C.c_double)]
+                ("split_err_est", C.c_double), ("t_chunk_bytes", C.c_int64)]
 
 
 class DavOpts(C.Structure):
@@ -82,6 +82,7 @@ def lib():
         L.su2_last_error.argtypes = [vp]
         L.su2_last_error.restype = C.c_char_p
         L.su2_ctx_status.argtypes = [vp, C.POINTER(C.c_int32)]
+        L.su2_ctx_wait.argtypes = [vp, C.c_double]
         L.su2_build_sectors.argtypes = [vp, C.POINTER(Sector), C.c_int32, C.POINTER(Sector), C.c_int32,
                                         C.c_int32, C.c_int32, C.c_int32, C.POINTER(vp)]
         L.su2_sectors_query.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32),
@@ -135,6 +136,43 @@ def _ptr(x):
     raise TypeError(type(x))
 
 
+def _vec(ctx, x, n, where):
+    """Address of a length-n FP64 vector after checking it: a torch tensor or
+    numpy array must be float64, contiguous, hold at least n elements and
+    live on the context's GPU (where="device") or in host memory
+    (where="host"); anything else raises Su2Error(SU2_EINVAL) before the
+    library is called.  A plain int is passed through as a raw address (the
+    caller vouches for it)."""
+    if isinstance(x, int):
+        return x
+    def bad(msg):
+        return Su2Error(SU2_EINVAL, f"{msg} (a {where} vector of {n} float64 is expected)")
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        if str(x.dtype) != "torch.float64":
+            raise bad(f"dtype {x.dtype}")
+        if not x.is_contiguous():
+            raise bad("tensor not contiguous")
+        if x.numel() < n:
+            raise bad(f"tensor has {x.numel()} elements")
+        if where == "device":
+            if not x.is_cuda or x.device.index != ctx.device:
+                raise bad(f"tensor on {x.device}, the context is on cuda:{ctx.device}")
+        elif x.is_cuda:
+            raise bad("tensor on a GPU")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if where != "host":
+            raise bad("numpy array given for device memory")
+        if x.dtype != np.float64:
+            raise bad(f"dtype {x.dtype}")
+        if not x.flags.c_contiguous:
+            raise bad("array not contiguous")
+        if x.size < n:
+            raise bad(f"array has {x.size} elements")
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
 class Context:
     def __init__(self, device: int = 0, stream=None):
         h = C.c_void_p()
@@ -156,6 +194,14 @@ class Context:
         v = C.c_int32()
         self.check(lib().su2_ctx_status(self.h, C.byref(v)))
         return v.value
+
+    def wait(self, timeout_s=-1.0):
+        """su2_ctx_wait: host watchdog on the context stream; returns the
+        status code (SU2_OK, SU2_ETIMEOUT) instead of raising for a timeout."""
+        rc = lib().su2_ctx_wait(self.h, float(timeout_s))
+        if rc not in (SU2_OK, SU2_ETIMEOUT):
+            self.check(rc)
+        return rc
 
     def close(self):
         if self.h:
@@ -224,13 +270,13 @@ class Environment:
 
     def __init__(self, ctx: Context, sectors: Sectors, model, left_chain, right_chain, n_left=0, n_right=0,
                  J=1.0, seed=0, t_budget_bytes=0, n_slices=0, prepare_split=False, autotune=False,
-                 split_tol=0.0, shard=(0, 0)):
+                 split_tol=0.0, shard=(0, 0), spin_limit=0):
         self.ctx = ctx
         H = Hamiltonian(model, n_left, n_right, J, seed)
         lc, keep1 = _chain(left_chain)
         rc_, keep2 = _chain(right_chain)
         opts = EnvOpts(t_budget_bytes, n_slices, 1 if prepare_split else 0, 1 if autotune else 0, split_tol,
-                       shard[0], shard[1])
+                       shard[0], shard[1], spin_limit)
         h = C.c_void_p()
         ctx.check(lib().su2_build_environment(ctx.h, C.byref(H), C.byref(lc), C.byref(rc_), sectors.h,
                                               C.byref(opts), C.byref(h)))
@@ -281,21 +327,27 @@ class Environment:
 
 
 def apply_heff(ctx: Context, env: Environment, psi_in, psi_out, prec=SU2_FP64):
-    ctx.check(lib().su2_apply_heff(ctx.h, env.h, _ptr(psi_in), _ptr(psi_out), prec))
+    n = env.psi_len
+    ctx.check(lib().su2_apply_heff(ctx.h, env.h, _vec(ctx, psi_in, n, "device"), _vec(ctx, psi_out, n, "device"),
+                                   prec))
 
 
-def apply_heff_host(ctx: Context, env: Environment, psi_in: np.ndarray, psi_out: np.ndarray, prec=SU2_FP64):
-    ctx.check(lib().su2_apply_heff_host(ctx.h, env.h, _ptr(psi_in), _ptr(psi_out), prec))
+def apply_heff_host(ctx: Context, env: Environment, psi_in, psi_out, prec=SU2_FP64):
+    n = env.psi_len
+    ctx.check(lib().su2_apply_heff_host(ctx.h, env.h, _vec(ctx, psi_in, n, "host"), _vec(ctx, psi_out, n, "host"),
+                                        prec))
 
 
 def apply_heff_static_scratch(ctx: Context, env: Environment, psi_in, psi_out):
     """su2_apply_heff_static_scratch: FP64 H.psi that allocates nothing
     (its intermediate lives in a fixed 64 MiB device array)."""
-    ctx.check(lib().su2_apply_heff_static_scratch(ctx.h, env.h, _ptr(psi_in), _ptr(psi_out)))
+    n = env.psi_len
+    ctx.check(lib().su2_apply_heff_static_scratch(ctx.h, env.h, _vec(ctx, psi_in, n, "device"),
+                                                  _vec(ctx, psi_out, n, "device")))
 
 
 def diag_heff(ctx: Context, env: Environment, diag_out):
-    ctx.check(lib().su2_diag_heff(ctx.h, env.h, _ptr(diag_out)))
+    ctx.check(lib().su2_diag_heff(ctx.h, env.h, _vec(ctx, diag_out, env.psi_len, "device")))
 
 
 class Davidson:
@@ -306,8 +358,10 @@ class Davidson:
         self.ctx = ctx
         h = C.c_void_p()
         o = DavOpts(tol, max_sub, keep, max_iter, prec, 1 if use_graph else 0)
-        ctx.check(lib().su2_davidson_create(ctx.h, env.h, _ptr(psi0), C.byref(o), C.byref(h)))
+        ctx.check(lib().su2_davidson_create(ctx.h, env.h, _vec(ctx, psi0, env.psi_len, "device"), C.byref(o),
+                                            C.byref(h)))
         self.h = h
+        self.n = env.psi_len
 
     def step(self):
         th, r = C.c_double(), C.c_double()
@@ -327,7 +381,7 @@ class Davidson:
         return e.value
 
     def vector(self, out):
-        self.ctx.check(lib().su2_davidson_vector(self.ctx.h, self.h, _ptr(out)))
+        self.ctx.check(lib().su2_davidson_vector(self.ctx.h, self.h, _vec(self.ctx, out, self.n, "device")))
 
     def close(self):
         if self.h:

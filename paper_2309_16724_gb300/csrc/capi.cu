@@ -7,6 +7,8 @@
 #include <map>
 #include <new>
 #include <string>
+#include <thread>
+#include <chrono>
 #include <unordered_map>
 
 #include "su2_device.h"
@@ -84,6 +86,18 @@ int set_device(su2_ctx* ctx) {
   return SU2_OK;
 }
 
+// Reads and clears the device status word; call after the context stream has
+// been synchronised.  A non-zero word (a bounded device wait gave up) turns
+// into SU2_ETIMEOUT, so a call that synchronises never reports success for a
+// result computed by a kernel that aborted.
+int device_status_rc(su2_ctx* ctx) {
+  int v = 0;
+  CUDA_TRY(ctx, cudaMemcpy(&v, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v == 0) return SU2_OK;
+  CUDA_TRY(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+  return fail(ctx, SU2_ETIMEOUT, "a bounded device-side wait gave up (device status " + std::to_string(v) + ")");
+}
+
 }  // namespace
 
 extern "C" {
@@ -126,6 +140,23 @@ int su2_ctx_destroy(su2_ctx* ctx) {
 }
 
 const char* su2_last_error(su2_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int su2_ctx_wait(su2_ctx* ctx, double timeout_s) {
+  if (!ctx) return SU2_EINVAL;
+  int rc = set_device(ctx);
+  if (rc) return rc;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery(ctx->stream);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return fail(ctx, SU2_ECUDA, std::string("cudaStreamQuery: ") + cudaGetErrorString(e));
+    const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (timeout_s >= 0.0 && dt > timeout_s)
+      return fail(ctx, SU2_ETIMEOUT, "host watchdog: the context stream is still busy after the time limit");
+    std::this_thread::sleep_for(std::chrono::microseconds(dt < 1e-3 ? 10 : 200));
+  }
+  return device_status_rc(ctx);
+}
 
 int su2_ctx_status(su2_ctx* ctx, int32_t* device_status) {
   if (!ctx || !device_status) return fail(ctx, SU2_EINVAL, "null argument");
@@ -304,6 +335,7 @@ static int build_plan(su2_env* env, const su2_sectors* S, int64_t budget) {
   }
   if (int64_t(env->k2t.size()) >= (int64_t(1) << 31)) return fail(env->ctx, SU2_EINVAL, "task table too large");
   env->t_elems = max_t;
+  env->info.t_chunk_bytes = max_t * int64_t(sizeof(double));
   env->info.flops_su2 = flops;
   env->info.n_k1 = nk1;
   env->info.n_chunks = int64_t(env->chunks.size());
@@ -412,6 +444,7 @@ int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond
   env->lsec = S->left;
   env->rsec = S->right;
   env->split_budget = (opts && opts->t_budget_bytes > 0) ? opts->t_budget_bytes : 0;
+  env->spin_limit = (opts && opts->spin_limit > 0) ? opts->spin_limit : 0;
   try {
     env->table = make_table(*H, S->site_kind);
     const bool host_values = ctx->device < 0;
@@ -573,7 +606,7 @@ int su2_apply_heff_host(su2_ctx* ctx, const su2_env* env_c, const double* in_h, 
   if (rc) return rc;
   CUDA_TRY(ctx, cudaMemcpyAsync(out_h, env->d_out_scratch, bytes, cudaMemcpyDeviceToHost, ctx->stream));
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  return SU2_OK;
+  return device_status_rc(ctx);
 }
 
 int su2_profile_enable(su2_env* env, int32_t on) {
@@ -814,6 +847,8 @@ int su2_davidson_step(su2_ctx* ctx, su2_dav* d, double* theta, double* resnorm) 
     }
     rc = dav_graph_step(ctx, d);
     if (rc) return rc;
+    rc = device_status_rc(ctx);
+    if (rc) return rc;
     d->iters += 1;
     d->theta = d->host[0];
     d->res = std::sqrt(std::max(0.0, d->host[1]));
@@ -842,6 +877,8 @@ int su2_davidson_step(su2_ctx* ctx, su2_dav* d, double* theta, double* resnorm) 
   CUDA_TRY(ctx, cudaMemcpyAsync(d->host, d->w, sizeof(double), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(ctx, cudaMemcpyAsync(d->host + 1, d->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  rc = device_status_rc(ctx);
+  if (rc) return rc;
   d->iters += 1;
   d->theta = d->host[0];
   d->res = std::sqrt(std::max(0.0, d->host[1]));

@@ -146,6 +146,7 @@ struct SplitState {
   std::vector<int64_t> scoff;
   int64_t n_scale = 0;
   int n_sms = 148;
+  int spin = int(sp::kSpinLimit);  // polls of each work-loop mbarrier wait of the split GEMM
 };
 
 // ------------------------------------------------------------------ device helpers
@@ -622,7 +623,7 @@ int exp_host(double x) {
 
 // the stripe GEMM instantiated for each mode and slice count
 using GemmFn = void (*)(const sp::Job*, int, const sp::Item*, const unsigned char*, const unsigned char*, const int*,
-                        const int*, int, float*, float*, double*, int*, int*, sp::TaskScale, int);
+                        const int*, int, float*, float*, double*, int*, int*, sp::TaskScale, int, int);
 GemmFn gemm_fn(int mode, int S) {
   static const GemmFn t[2][sp::kMaxS - 1] = {
       {sp::split_gemm_kernel<sp::MODE_T, 2>, sp::split_gemm_kernel<sp::MODE_T, 3>, sp::split_gemm_kernel<sp::MODE_T, 4>,
@@ -643,7 +644,7 @@ void launch_gemm(int mode, cudaStream_t s, SplitState* st, const Job* jobs, int 
   const int grid = std::min(njobs, st->n_sms);
   cudaMemsetAsync(st->d_counter, 0, sizeof(int), s);
   gemm_fn(mode, st->S)<<<grid, sp::kThreads, smem, s>>>(jobs, njobs, items, A, B, rexp, cexp, 2 * sp::kLead, Th, Tl, F,
-                                                        st->d_status, st->d_counter, ts, st->sk);
+                                                        st->d_status, st->d_counter, ts, st->sk, st->spin);
 }
 
 }  // namespace
@@ -672,6 +673,7 @@ int split_prepare(su2_env* env, int S, std::string& err) {
     return SU2_ECUDA;
   }
   st->d_status = env->ctx->d_status;
+  if (env->spin_limit > 0) st->spin = env->spin_limit;
   if (int rc0 = dalloc(&st->d_counter, 1, err)) return rc0;
   const auto& B = env->blocks;
   const auto& ls = env->lsec;

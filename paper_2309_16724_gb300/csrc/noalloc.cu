@@ -16,13 +16,22 @@
 
 namespace {
 
-// Scratch for T of one term chunk: 64 MiB, held by every GPU that loads the
-// library until the process exits.
+// Scratch for T of one term chunk: 64 MiB.  It is part of this library's
+// device module, so a GPU holds it from the moment the module is loaded on it
+// until the process exits (or the context is reset).  With CUDA's lazy module
+// loading the load, and so the 64 MiB allocation by the driver, can happen at
+// the first use on a device, i.e. inside the first call of the entry point on
+// that device: a caller that must not allocate at all during its run makes
+// one call at start-up.
 constexpr size_t kScratchDoubles = size_t(8) << 20;
 static __device__ __align__(256) double g_t_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// per device: the array's device address, looked up once.  cudaDeviceReset
+// destroys the context it belongs to; after a reset of a device the cached
+// address is stale, so the library must not be used on a device after
+// cudaDeviceReset in the same process.
 double* g_scratch_ptr[kMaxDevices] = {};
 
 }  // namespace

@@ -42,7 +42,9 @@
 // arrive on barriers with one lane each.
 // Every mbarrier wait is bounded; on timeout the CTA records a status,
 // stops issuing, waits (bounded) for its own copies and MMAs, frees TMEM and
-// returns.
+// returns.  The waits of the work loops poll at most `spin` times (a launch
+// argument, normally kSpinLimit); the final waits for the CTA's own copies
+// and MMAs always use kSpinLimit.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -154,9 +156,11 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait; false on timeout or when another role aborted
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  for (long it = 0; it < kSpinLimit; ++it) {
+// bounded wait of the work loops (at most `limit` polls, a launch argument:
+// kSpinLimit unless the caller shortened it); false on timeout or when
+// another role aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int limit) {
+  for (int it = 0; it < limit; ++it) {
     if (mbar_try(bar, parity)) return true;
     if ((it & 255) == 255 && *abort_flag) return false;
   }
@@ -166,8 +170,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 // bounded wait by every lane of a warp, then a warp vote: the warp leaves
 // converged (the .sync.aligned TMEM loads that follow need that) and agrees
 // on the outcome (polling by lane 0 alone measured slower)
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  const bool got = mbar_wait(bar, parity, abort_flag);
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int limit) {
+  const bool got = mbar_wait(bar, parity, abort_flag, limit);
   return __all_sync(0xffffffffu, got);
 }
 
@@ -321,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                       const unsigned char* __restrict__ Aslab, const unsigned char* __restrict__ Bslab,
                       const int* __restrict__ rexp, const int* __restrict__ cexp, int shift,
                       float* __restrict__ Th, float* __restrict__ Tl, double* __restrict__ F, int* __restrict__ status,
-                      int* __restrict__ job_counter, TaskScale ts, int sk) {
+                      int* __restrict__ job_counter, TaskScale ts, int sk, int spin) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int stage_bytes = stage_bytes_of(S, sk);
@@ -372,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int k = 0; ok; ++k) {
         const int slot = k % kRing;
-        if (!mbar_wait(smem_u32(&jq_empty[slot]), ((k / kRing) & 1) ^ 1, &abort_flag)) {
+        if (!mbar_wait(smem_u32(&jq_empty[slot]), ((k / kRing) & 1) ^ 1, &abort_flag, spin)) {
           ok = false;
           break;
         }
@@ -396,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const Item item = items[it];
           const int nstage = (item.nst + sk - 1) / sk;
           for (int ks = 0; ks < nstage; ++ks) {
-            if (!mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1, &abort_flag)) {
+            if (!mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1, &abort_flag, spin)) {
               ok = false;
               break;
             }
@@ -433,7 +437,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // end marker for the MMA issuer: a stage without data
       if (ok) {
-        if (mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1, &abort_flag)) {
+        if (mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1, &abort_flag, spin)) {
           stage_meta[st] = kMetaEnd;
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[st])) : "memory");
           ++nissued;
@@ -474,7 +478,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       const uint32_t sbase = smem_u32(smem);
       for (;;) {
-        if (!warp_wait(smem_u32(&full_bar[st]), ph, &abort_flag)) {
+        if (!warp_wait(smem_u32(&full_bar[st]), ph, &abort_flag, spin)) {
           ok = false;
           break;
         }
@@ -483,7 +487,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t buf = chunk % kNumBuf;
         if (m & kMetaFirst) {
           // the buffer's previous chunk (c - kNumBuf) must have been read by the drain
-          if (!warp_wait(smem_u32(&acce_bar[buf]), ((chunk / kNumBuf) & 1) ^ 1, &abort_flag)) {
+          if (!warp_wait(smem_u32(&acce_bar[buf]), ((chunk / kNumBuf) & 1) ^ 1, &abort_flag, spin)) {
             ok = false;
             break;
           }
@@ -530,7 +534,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int k = 0; ok; ++k) {
       const int slot = k % kRing;
-      if (!warp_wait(smem_u32(&jq_full[slot]), (k / kRing) & 1, &abort_flag)) {
+      if (!warp_wait(smem_u32(&jq_full[slot]), (k / kRing) & 1, &abort_flag, spin)) {
         ok = false;
         break;
       }
@@ -584,7 +588,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int nch = (item.nst + kChunkSteps - 1) / kChunkSteps;
         for (int ch = 0; ch < nch; ++ch) {
           const uint32_t buf = chunk % kNumBuf;
-          if (!warp_wait(smem_u32(&accf_bar[buf]), (chunk / kNumBuf) & 1, &abort_flag)) {
+          if (!warp_wait(smem_u32(&accf_bar[buf]), (chunk / kNumBuf) & 1, &abort_flag, spin)) {
             ok = false;
             break;
           }

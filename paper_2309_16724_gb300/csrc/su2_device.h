@@ -128,6 +128,7 @@ struct su2_env {
   std::vector<su2::Block> blocks;   // psi blocks
   std::vector<su2::Sector> lsec, rsec;
   int64_t split_budget = 0;
+  int spin_limit = 0;  // polls of each work-loop wait of the split GEMM (0: the kernel's default)
   // FP64 plan
   std::vector<su2::Chunk> chunks;
   std::vector<su2::K1Job> k1;
