@@ -362,6 +362,7 @@ class Davidson:
                                             C.byref(h)))
         self.h = h
         self.n = env.psi_len
+        self.env = env  # the solver reads the environment: keep it alive as long as the solver
 
     def step(self):
         th, r = C.c_double(), C.c_double()

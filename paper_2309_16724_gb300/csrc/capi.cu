@@ -83,6 +83,9 @@ int upload(su2_ctx* ctx, T** d, const std::vector<T>& h) {
 int set_device(su2_ctx* ctx) {
   if (ctx->device < 0) return fail(ctx, SU2_EINVAL, "host-only context cannot run device work");
   CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  // an error latched in this thread by code outside the library (it is
+  // reported to whoever made that call) must not fail the launch checks below
+  (void)cudaGetLastError();
   return SU2_OK;
 }
 
@@ -363,8 +366,8 @@ static int build_plan(su2_env* env, const su2_sectors* S, int64_t budget) {
 }
 
 static void env_free_device(su2_env* e) {
-  if (!e->ctx || e->ctx->device < 0) return;
-  cudaSetDevice(e->ctx->device);
+  if (e->device < 0) return;
+  cudaSetDevice(e->device);
   split_free(e);
   cudaFree(e->dL);
   cudaFree(e->dR);
@@ -439,6 +442,7 @@ int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond
   su2_env* env = new (std::nothrow) su2_env();
   if (!env) return fail(ctx, SU2_ENOMEM, "host allocation");
   env->ctx = ctx;
+  env->device = ctx->device;
   env->psi_len = S->psi_len;
   env->blocks = S->blocks;
   env->lsec = S->left;
@@ -554,7 +558,7 @@ int su2_env_operator_block(const su2_env* env, int32_t side, int32_t op, int32_t
     return SU2_OK;
   }
   const double* dsrc = (side == 0 ? env->dL : env->dR) + so.blocks[b].off;
-  if (cudaSetDevice(env->ctx->device) != cudaSuccess ||
+  if (cudaSetDevice(env->device) != cudaSuccess ||
       cudaMemcpy(out, dsrc, sizeof(double) * size_t(rows) * cols, cudaMemcpyDeviceToHost) != cudaSuccess)
     return SU2_ECUDA;
   return SU2_OK;
@@ -648,6 +652,7 @@ int su2_diag_heff(su2_ctx* ctx, const su2_env* env, double* diag_dev) {
 // ------------------------------------------------------------------ Davidson
 struct su2_dav {
   su2_ctx* ctx = nullptr;
+  int device = -1;  // kept so that destroying the solver never reads its context
   const su2_env* env = nullptr;
   su2_dav_opts o{};
   int64_t n = 0;
@@ -671,7 +676,7 @@ struct su2_dav {
 };
 
 static void dav_free(su2_dav* d) {
-  if (d->ctx && d->ctx->device >= 0) cudaSetDevice(d->ctx->device);
+  if (d->device >= 0) cudaSetDevice(d->device);
   if (d->gexec) cudaGraphExecDestroy(d->gexec);
   if (d->graph) cudaGraphDestroy(d->graph);
   if (d->gstream) cudaStreamDestroy(d->gstream);
@@ -697,6 +702,7 @@ int su2_davidson_create(su2_ctx* ctx, const su2_env* env, const double* psi0, co
   su2_dav* d = new (std::nothrow) su2_dav();
   if (!d) return fail(ctx, SU2_ENOMEM, "host allocation");
   d->ctx = ctx;
+  d->device = ctx->device;
   d->env = env;
   d->o.tol = 1e-8;
   d->o.max_sub = 24;

@@ -662,7 +662,7 @@ int split_prepare(su2_env* env, int S, std::string& err) {
   env->split = st;
   st->S = S;
   cudaDeviceProp prop;
-  cudaGetDeviceProperties(&prop, env->ctx->device);
+  cudaGetDeviceProperties(&prop, env->device);
   st->n_sms = prop.multiProcessorCount;
   const int smem = sp::kSmemMax;
   if (cudaFuncSetAttribute((const void*)gemm_fn(sp::MODE_T, S), cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=

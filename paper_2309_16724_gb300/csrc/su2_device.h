@@ -120,6 +120,9 @@ struct su2_sectors {
 
 struct su2_env {
   su2_ctx* ctx = nullptr;
+  int device = -1;  // the context's device, kept here so that destroying the
+                    // environment never reads its context (which the caller
+                    // may already have destroyed)
   su2::OpTable table;
   su2::SideOps L, R;
   std::vector<su2::Task> tasks;
