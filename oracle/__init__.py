@@ -22,6 +22,11 @@ Each function cites the passage of arXiv:2309.16724 it follows:
 * ``expand``   independent definitions used as pins: Clebsch-Gordan
                expansion to the m-resolved (U(1)) basis, explicit full-space
                projection P^T H P for small spin chains.
+* ``abinitio`` the ab initio Hamiltonian (Eq. 1) from integrals: spin-adapted
+               normal/complementary block operators renormalised from a
+               seeded MPS (Sec. II.A, II.C) and the operator-table at the
+               two-site bond.
+* ``fci``      full configuration interaction of small ab initio problems.
 * ``davidson`` Davidson eigensolver (the diagonalisation of Sec. II).
 * ``ed``       exact diagonalisation of small Heisenberg chains.
 

@@ -8,10 +8,12 @@ coupling order of the W9j^(l), W9j^(r), W9j^(h) factors, Sec. II.C).  Each
 block is a dense d_a x d_b column-major FP64 matrix; blocks are stored one
 after another in the canonical order of the nested loops below.
 
-Parity: the block list is bit-exact against the library (``tests``), and
-pinned by the dimension count sum_blocks d_a d_b (2S+1) = dimension of the
-m-resolved two-site space with M = S summed over allowed S (checked in
-``tests/test_oracle_expand.py`` through the explicit expansion).
+Parity: the block list is bit-exact against the library
+(``tests/test_lib_host.py``) and pinned in ``tests/test_oracle_abinitio.py``:
+sum_blocks d_a d_b equals an independent count of the spin-S multiplets of
+(S_a x s1 x s2 x S_b) by characters (states with M = S minus M = S + 1) on
+truncated bonds, and the Weyl-Paldus number of spin-S multiplets of N
+electrons in L orbitals when the bonds keep every multiplet.
 """
 from __future__ import annotations
 

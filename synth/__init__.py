@@ -174,3 +174,36 @@ def gaussian_psi(n: int, seed: int) -> np.ndarray:
 
 def psi_seed(cfg: Config) -> int:
     return cfg.seed + 100
+
+
+N_CHOLESKY = 32
+
+
+def integrals(L: int, seed: int):
+    """Seeded synthetic ab initio integrals (h, (ij|kl)) of L orbitals.
+
+    Draws, in this order, from ``numpy.random.default_rng(seed)``: g (L x L
+    standard normal, row-major), u (L values uniform in [-2, 0)), then for
+    r = 0..31 the upper triangle i <= j of z^r (standard normal, row-major).
+    h_ij = (g_ij + g_ji)/2 * exp(-|i-j|/4) off the diagonal, h_ii = u_i;
+    B^r_ij = B^r_ji = 0.1 z^r_ij exp(-|i-j|/4) (standard deviation 0.1 times
+    the decay); (ij|kl) = sum_r B^r_ij B^r_kl (chemists' notation: 8-fold
+    symmetric and positive semidefinite as an (ij) x (kl) matrix).  No core
+    energy.  Returns (h, eri) with eri[i, j, k, l] = (ij|kl).
+    """
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((L, L))
+    u = rng.uniform(-2.0, 0.0, L)
+    iu = np.triu_indices(L)
+    z = [rng.standard_normal(len(iu[0])) for _ in range(N_CHOLESKY)]
+    i, j = np.indices((L, L))
+    decay = np.exp(-np.abs(i - j) / 4.0)
+    h = 0.5 * (g + g.T) * decay
+    h[np.diag_indices(L)] = u
+    B = np.zeros((N_CHOLESKY, L, L))
+    for r in range(N_CHOLESKY):
+        B[r][iu] = z[r]
+        B[r] = np.triu(B[r]) + np.triu(B[r], 1).T
+        B[r] *= 0.1 * decay
+    eri = np.einsum("rij,rkl->ijkl", B, B)
+    return h, eri
