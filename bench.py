@@ -406,11 +406,15 @@ def main():
     # terms dealt to shards in longest-processing-time order of their flops),
     # timed with CUDA events; its rate is the shard's flops over its time.
     # On the same shard, the split H.psi against the FP64 one.
+    # roofline inputs of the main environment before it may be released
+    launch_count = prof.pop("kernel_launches")[0]
     fp64 = None
     rel_err_fp64 = None
     if split and rank == 0:
         n_sh = max(1, int(round(flops / 4e12)))
         if n_sh > 1:
+            env.close()   # the shard's environment needs the memory (all timed sections are done)
+            torch.cuda.synchronize()
             _, senv = workload.build(ctx, cfg, prepare_split=True, n_slices=info["split_slices"], shard=(0, n_sh))
         else:
             senv = env
@@ -443,7 +447,6 @@ def main():
             senv.close()
 
     # roofline of the dominant kernel
-    launch_count = prof.pop("kernel_launches")[0]
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     name, (launches, ms, fl) = dom
     pk, src = peaks()

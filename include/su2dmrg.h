@@ -56,7 +56,15 @@ enum su2_model {
   SU2_MODEL_QC_SKELETON = 1,  /* ab initio normal/complementary term
                                  structure, seeded synthetic entries         */
   SU2_MODEL_CASIMIR_S2 = 2,   /* total spin squared (S(S+1) psi)            */
-  SU2_MODEL_CASIMIR_N = 3     /* total particle number (N psi)              */
+  SU2_MODEL_CASIMIR_N = 3,    /* total particle number (N psi)              */
+  SU2_MODEL_AB_INITIO = 4     /* H = sum h_ij E_ij + 1/2 sum (ij|kl)(E_ij E_kl
+                                 - delta_jk E_il) of Eq. 1 from the caller's
+                                 integrals: spin-adapted normal (left block)
+                                 and complementary (right block) operators of
+                                 Sec. II.A, renormalised orbital by orbital
+                                 from a seeded SU(2) MPS (Sec. II.C) on the
+                                 context's GPU (Sec. IV.D), or on the host
+                                 for a host-only context                     */
 };
 
 /* One bond sector: particle number, twice the spin, kept multiplets. */
@@ -86,6 +94,14 @@ typedef struct {
   double J;           /* Heisenberg coupling                 */
   uint64_t seed;      /* seed of the counter-based generator (SplitMix64)
                          for synthetic entries and MPS tensors */
+  const double* h;    /* SU2_MODEL_AB_INITIO: host array of the one-electron
+                         integrals h_ij, L x L row-major, L = n_left + 2 +
+                         n_right orbitals in chain order (left block, the
+                         two sites, right block); read during the call   */
+  const double* eri;  /* SU2_MODEL_AB_INITIO: host array of the two-electron
+                         integrals (ij|kl) (chemists' notation) at
+                         ((i L + j) L + k) L + l; read during the call.
+                         Other models: both NULL                          */
 } su2_hamiltonian;
 
 typedef struct {
@@ -138,6 +154,9 @@ typedef struct {
                               measured)                                    */
   int64_t t_chunk_bytes;   /* FP64 bytes of the intermediate T of the
                               largest term chunk (native-FP64 path)        */
+  double renorm_flops;     /* SU2_MODEL_AB_INITIO: flops of the products
+                              of the renormalisation that built the block
+                              operators (0 for the other models)           */
 } su2_env_info;
 
 typedef struct {
@@ -187,7 +206,11 @@ int su2_sectors_destroy(su2_sectors* s);
  * (Eq. 3) and sector-value table (Sec. II.C), built once per site.  The
  * chains give the bond sectors grown from the vacuum to the two-site
  * window (their last bonds must equal the sectors' left/right lists).  With
- * a device context the tables and operators are uploaded. */
+ * a device context the tables and operators are uploaded; the ab initio
+ * model renormalises its block operators on the device (its products run
+ * through the grouped FP64 kernels; intermediate arenas are allocated and
+ * freed during the call).  SU2_EINVAL for a missing integral array or
+ * chains whose lengths differ from n_left + 1 / n_right + 1. */
 int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H,
                           const su2_bond_chain* left_chain, const su2_bond_chain* right_chain,
                           const su2_sectors* sectors, const su2_env_opts* opts, su2_env** out);
@@ -196,6 +219,11 @@ int su2_env_query(const su2_env* env, su2_env_info* info);
  * b_out, b_in, flags) with a_* = -1 for an identity left operator, b_* = -1
  * for an identity right operator, and v per task; arrays of n_tasks rows. */
 int su2_env_tasks(const su2_env* env, int32_t* rows8, double* v, int64_t n_tasks);
+/* Copies the operator-table (Eq. 2): per row i the left operator id of
+ * A_i, the right operator id of D_i (op 0 of a side is its identity),
+ * the coupling rank k (twos) and alpha_i; any output pointer may be NULL.
+ * Arrays of n_terms entries; SU2_EINVAL if n_terms differs. */
+int su2_env_terms(const su2_env* env, int32_t* a_op, int32_t* d_op, int32_t* k, double* alpha, int64_t n_terms);
 /* Copies block (out sector qo, in sector qi) of block operator `op` of
  * side 0 (left, A_i) or 1 (right, D_i) into out (rows x cols, column-major).
  * SU2_EINVAL if the operator has no such block or the shape differs. */

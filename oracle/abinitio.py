@@ -661,6 +661,11 @@ def build_problem(cfg, h=None, eri=None):
 
     IL = op_id("L", "I", None)
     IR = op_id("R", "I", None)
+    # the block Hamiltonians first (left / right operator 1)
+    if ((), ()) in Lb.C:
+        op_id("L", ("C", (), ()), Lb.C[((), ())])
+    if ((), ()) in Rb.C:
+        op_id("R", ("C", (), ()), Rb.C[((), ())])
 
     def site_pairs(Bops, Cops):
         """Coupled site operators (labels, SiteOp) of the parts on sites p and q."""

@@ -17,11 +17,12 @@ LIB_PATH = os.path.join(HERE, "libsu2dmrg.so")
 SU2_OK, SU2_EINVAL, SU2_ENOMEM, SU2_ECUDA, SU2_ETIMEOUT, SU2_ENOTCONV = range(6)
 SU2_FP64, SU2_SPLIT_BF16 = 0, 1
 SU2_SITE_SPIN_HALF, SU2_SITE_ORBITAL = 0, 1
-SU2_MODEL_HEISENBERG, SU2_MODEL_QC_SKELETON, SU2_MODEL_CASIMIR_S2, SU2_MODEL_CASIMIR_N = range(4)
+(SU2_MODEL_HEISENBERG, SU2_MODEL_QC_SKELETON, SU2_MODEL_CASIMIR_S2, SU2_MODEL_CASIMIR_N,
+ SU2_MODEL_AB_INITIO) = range(5)
 
 SYMBOLS = [
     "su2_ctx_create", "su2_ctx_destroy", "su2_last_error", "su2_ctx_status", "su2_ctx_wait", "su2_build_sectors", "su2_sectors_query",
-    "su2_sectors_destroy", "su2_build_environment", "su2_env_query", "su2_env_tasks", "su2_env_operator_block", "su2_env_destroy",
+    "su2_sectors_destroy", "su2_build_environment", "su2_env_query", "su2_env_tasks", "su2_env_terms", "su2_env_operator_block", "su2_env_destroy",
     "su2_apply_heff", "su2_apply_heff_host", "su2_apply_heff_static_scratch", "su2_diag_heff", "su2_davidson_create", "su2_davidson_step",
     "su2_davidson_solve", "su2_energy", "su2_davidson_vector", "su2_davidson_destroy",
     "su2_profile_enable", "su2_profile_reset", "su2_profile_read",
@@ -45,7 +46,7 @@ class BondChain(C.Structure):
 
 class Hamiltonian(C.Structure):
     _fields_ = [("model", C.c_int32), ("n_left", C.c_int32), ("n_right", C.c_int32),
-                ("J", C.c_double), ("seed", C.c_uint64)]
+                ("J", C.c_double), ("seed", C.c_uint64), ("h", C.c_void_p), ("eri", C.c_void_p)]
 
 
 class EnvOpts(C.Structure):
@@ -59,7 +60,7 @@ class EnvInfo(C.Structure):
                 ("n_tasks", C.c_int64), ("n_k1", C.c_int64), ("n_chunks", C.c_int64),
                 ("flops_su2", C.c_double), ("flops_u1_equiv", C.c_double), ("r_d", C.c_double),
                 ("env_bytes", C.c_double), ("split_slices", C.c_int32), ("split_stage_k", C.c_int32),
-                ("split_err_est", C.c_double), ("t_chunk_bytes", C.c_int64)]
+                ("split_err_est", C.c_double), ("t_chunk_bytes", C.c_int64), ("renorm_flops", C.c_double)]
 
 
 class DavOpts(C.Structure):
@@ -92,6 +93,7 @@ def lib():
                                             C.POINTER(BondChain), vp, C.POINTER(EnvOpts), C.POINTER(vp)]
         L.su2_env_query.argtypes = [vp, C.POINTER(EnvInfo)]
         L.su2_env_tasks.argtypes = [vp, vp, vp, C.c_int64]
+        L.su2_env_terms.argtypes = [vp, vp, vp, vp, vp, C.c_int64]
         L.su2_env_operator_block.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp,
                                              C.c_int32, C.c_int32]
         L.su2_env_destroy.argtypes = [vp]
@@ -270,9 +272,18 @@ class Environment:
 
     def __init__(self, ctx: Context, sectors: Sectors, model, left_chain, right_chain, n_left=0, n_right=0,
                  J=1.0, seed=0, t_budget_bytes=0, n_slices=0, prepare_split=False, autotune=False,
-                 split_tol=0.0, shard=(0, 0), spin_limit=0):
+                 split_tol=0.0, shard=(0, 0), spin_limit=0, h=None, eri=None):
         self.ctx = ctx
-        H = Hamiltonian(model, n_left, n_right, J, seed)
+        if model == SU2_MODEL_AB_INITIO:
+            L = n_left + 2 + n_right
+            if h is None or eri is None:
+                raise Su2Error(SU2_EINVAL, "the ab initio model needs the integrals h and eri")
+            h = np.ascontiguousarray(h, dtype=np.float64)
+            eri = np.ascontiguousarray(eri, dtype=np.float64)
+            if h.shape != (L, L) or eri.shape != (L, L, L, L):
+                raise Su2Error(SU2_EINVAL, f"integrals must be ({L}, {L}) and ({L},)*4 arrays")
+        H = Hamiltonian(model, n_left, n_right, J, seed, None if h is None else h.ctypes.data,
+                        None if eri is None else eri.ctypes.data)
         lc, keep1 = _chain(left_chain)
         rc_, keep2 = _chain(right_chain)
         opts = EnvOpts(t_budget_bytes, n_slices, 1 if prepare_split else 0, 1 if autotune else 0, split_tol,
@@ -292,6 +303,16 @@ class Environment:
         v = np.zeros(n, dtype=np.float64)
         self.ctx.check(lib().su2_env_tasks(self.h, rows.ctypes.data, v.ctypes.data, n))
         return rows, v
+
+    def terms(self):
+        """(left op id, right op id, k, alpha) per operator-table row."""
+        n = self.info["n_terms"]
+        a = np.zeros(n, dtype=np.int32)
+        d = np.zeros(n, dtype=np.int32)
+        k = np.zeros(n, dtype=np.int32)
+        al = np.zeros(n, dtype=np.float64)
+        self.ctx.check(lib().su2_env_terms(self.h, a.ctypes.data, d.ctypes.data, k.ctypes.data, al.ctypes.data, n))
+        return a, d, k, al
 
     def operator_block(self, side, op, qo, qi, rows, cols):
         out = np.zeros((cols, rows), dtype=np.float64)

@@ -414,8 +414,9 @@ int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond
                           const su2_sectors* S, const su2_env_opts* opts, su2_env** out) {
   if (!ctx || !H || !lc || !rc || !S || !out) return fail(ctx, SU2_EINVAL, "null argument");
   *out = nullptr;
-  if (H->model < 0 || H->model > 3) return fail(ctx, SU2_EINVAL, "unknown model");
-  if ((H->model == SU2_MODEL_HEISENBERG) != (S->site_kind == SU2_SITE_SPIN_HALF) && H->model <= 1)
+  if (H->model < 0 || H->model > 4) return fail(ctx, SU2_EINVAL, "unknown model");
+  if (((H->model == SU2_MODEL_HEISENBERG) != (S->site_kind == SU2_SITE_SPIN_HALF) && H->model <= 1) ||
+      (H->model == SU2_MODEL_AB_INITIO && S->site_kind != SU2_SITE_ORBITAL))
     return fail(ctx, SU2_EINVAL, "model and site kind disagree");
   if (H->model == SU2_MODEL_QC_SKELETON && (H->n_left < 1 || H->n_right < 1))
     return fail(ctx, SU2_EINVAL, "n_left and n_right must be >= 1");
@@ -450,10 +451,18 @@ int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond
   env->split_budget = (opts && opts->t_budget_bytes > 0) ? opts->t_budget_bytes : 0;
   env->spin_limit = (opts && opts->spin_limit > 0) ? opts->spin_limit : 0;
   try {
-    env->table = make_table(*H, S->site_kind);
-    const bool host_values = ctx->device < 0;
-    std::string err = build_side_ops(env->table, true, lch, *H, env->L, host_values);
-    if (err.empty()) err = build_side_ops(env->table, false, rch, *H, env->R, host_values);
+    std::string err;
+    if (H->model == SU2_MODEL_AB_INITIO) {
+      if (ctx->device >= 0 && cudaSetDevice(ctx->device) != cudaSuccess) err = "cudaSetDevice failed";
+      if (err.empty())
+        err = build_abinitio(*H, lch, rch, ctx->device, ctx->stream, env->split_budget, env->table, env->L, env->R,
+                             &env->info.renorm_flops);
+    } else {
+      env->table = make_table(*H, S->site_kind);
+      const bool host_values = ctx->device < 0;
+      err = build_side_ops(env->table, true, lch, *H, env->L, host_values);
+      if (err.empty()) err = build_side_ops(env->table, false, rch, *H, env->R, host_values);
+    }
     if (err.empty()) err = build_tasks(env->table, S->left, S->right, S->blocks, S->twoS, env->L, env->R, env->tasks);
     if (err.empty() && opts && opts->shard_count > 1) {
       if (opts->shard_rank < 0 || opts->shard_rank >= opts->shard_count) err = "shard_rank outside [0, shard_count)";
@@ -495,7 +504,10 @@ int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond
     for (int side = 0; side < 2 && !rc; ++side) {
       SideOps& so = side == 0 ? env->L : env->R;
       double** dst = side == 0 ? &env->dL : &env->dR;
-      if (so.host_values) {
+      if (so.dev_ready) {  // filled on the device by the builder
+        *dst = so.dev_ready;
+        so.dev_ready = nullptr;
+      } else if (so.host_values) {
         rc = upload(ctx, dst, so.arena);
       } else {
         rc = dev_alloc(ctx, dst, size_t(std::max<int64_t>(so.arena_size, 2)));
@@ -543,6 +555,18 @@ int su2_env_tasks(const su2_env* env, int32_t* rows8, double* v, int64_t n_tasks
       r[7] = (t.ablk < 0 ? 1 : 0) | (t.dblk < 0 ? 2 : 0);
     }
     if (v) v[i] = t.v;
+  }
+  return SU2_OK;
+}
+
+int su2_env_terms(const su2_env* env, int32_t* a_op, int32_t* d_op, int32_t* k, double* alpha, int64_t n_terms) {
+  if (!env || n_terms != int64_t(env->table.terms.size())) return SU2_EINVAL;
+  for (int64_t i = 0; i < n_terms; ++i) {
+    const Term& t = env->table.terms[size_t(i)];
+    if (a_op) a_op[i] = t.A;
+    if (d_op) d_op[i] = t.D;
+    if (k) k[i] = t.k;
+    if (alpha) alpha[i] = t.alpha;
   }
   return SU2_OK;
 }

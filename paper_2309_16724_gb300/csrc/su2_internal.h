@@ -25,7 +25,7 @@ struct SiteOp {
   double red[3][3] = {{0}};               // reduced matrix [out][in], CG form of Wigner-Eckart
 };
 
-enum OpKind { OP_IDENTITY = 0, OP_HAM, OP_RANDOM, OP_ADJOINT, OP_MPS_RENORM, OP_SPINTOT, OP_NUMTOT };
+enum OpKind { OP_IDENTITY = 0, OP_HAM, OP_RANDOM, OP_ADJOINT, OP_MPS_RENORM, OP_SPINTOT, OP_NUMTOT, OP_VALUES };
 
 struct BlockOp {
   std::string name;
@@ -51,6 +51,8 @@ void site_states(int site_kind, std::vector<int>& N, std::vector<int>& twoS);
 SiteOp site_op(int site_kind, const char* name);
 SiteOp site_adjoint(const SiteOp& op, int site_kind);
 OpTable make_table(const su2_hamiltonian& H, int site_kind);
+// Q factor (positive diagonal of R) of a rows x cols column-major matrix
+void orthonormalize(std::vector<double>& G, int rows, int cols);
 
 // ---------------------------------------------------------------- operators
 struct OpBlock { int op, qo, qi, rows, cols; int64_t off; };
@@ -69,6 +71,7 @@ struct SideOps {
   int64_t arena_size = 0;     // doubles
   bool host_values = true;
   std::vector<GenBlock> gen;  // device-generated blocks (device mode)
+  double* dev_ready = nullptr;  // device arena already filled by the builder (device mode; the environment takes it)
   std::unordered_map<uint64_t, int> index;  // key(op, qo, qi) -> block
   static uint64_t key(int op, int qo, int qi) {
     return (uint64_t(uint32_t(op)) << 32) | (uint64_t(uint32_t(qo)) << 16) | uint64_t(uint32_t(qi));
@@ -93,6 +96,13 @@ std::string build_side_ops(const OpTable& t, bool left_side, const std::vector<s
 std::string build_tasks(const OpTable& t, const std::vector<Sector>& left, const std::vector<Sector>& right,
                         const std::vector<Block>& blocks, int twoS, const SideOps& L, const SideOps& R,
                         std::vector<Task>& tasks);
+
+// ab initio environment (Eq. 1 from integrals): operator-table and block
+// operators of both sides, renormalised on the context's device (device >= 0)
+// or on the host
+std::string build_abinitio(const su2_hamiltonian& H, const std::vector<std::vector<Sector>>& lchain,
+                           const std::vector<std::vector<Sector>>& rchain, int device, void* stream,
+                           int64_t t_budget_bytes, OpTable& table, SideOps& L, SideOps& R, double* renorm_flops);
 
 // counter-based generator (SplitMix64, Steele/Lea/Flood 2014)
 uint64_t splitmix(uint64_t x);

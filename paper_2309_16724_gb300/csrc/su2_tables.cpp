@@ -295,6 +295,8 @@ std::vector<std::pair<int, int>> allowed(const BlockOp& op, const std::vector<Se
   return r;
 }
 
+}  // namespace
+
 // Q factor (positive diagonal of R) of a rows x cols column-major matrix by
 // classical Gram-Schmidt applied twice.
 void orthonormalize(std::vector<double>& G, int rows, int cols) {
@@ -319,6 +321,8 @@ void orthonormalize(std::vector<double>& G, int rows, int cols) {
     for (int r = 0; r < rows; ++r) gc[r] /= nrm;
   }
 }
+
+namespace {
 
 struct Mat {
   int r = 0, c = 0;
