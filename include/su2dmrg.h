@@ -290,6 +290,18 @@ int su2_energy(const su2_dav* dav, double* E);
 int su2_davidson_vector(su2_ctx* ctx, su2_dav* dav, double* x_dev);
 int su2_davidson_destroy(su2_dav* dav);
 
+/* Group order of the paper's hash-based semi-dynamic scheduling (Sec.
+ * III.D, Fig. 2) for a multi-GPU run: worker `id` of `step` workers picks, at
+ * its i-th pick, group (id + step * i + cycle) mod group_count, where
+ * cycle = floor(i / cycle_len) and cycle_len = group_count / gcd(group_count,
+ * step) is the length of the cyclic subset reached by steps of `step`; the
+ * shift by `cycle` makes every group reachable, so group_count consecutive
+ * picks visit every group once, and workers start on disjoint groups.
+ * Workers claim the tasks of the group they picked from a shared counter (the
+ * paper's Contract Book) and move on when it is exhausted.  Host-only
+ * arithmetic; SU2_EINVAL unless 0 <= id < step, group_count >= 1, i >= 0. */
+int su2_hash_group(int32_t id, int32_t step, int64_t group_count, int64_t i, int64_t* group);
+
 /* Per-kernel timing of su2_apply_heff (off by default): with profiling on,
  * every kernel launch of the hot path is bracketed by CUDA events on the
  * context stream.  su2_profile_read synchronises on the recorded events and

@@ -25,7 +25,7 @@ SYMBOLS = [
     "su2_sectors_destroy", "su2_build_environment", "su2_env_query", "su2_env_tasks", "su2_env_terms", "su2_env_operator_block", "su2_env_destroy",
     "su2_apply_heff", "su2_apply_heff_host", "su2_apply_heff_static_scratch", "su2_diag_heff", "su2_davidson_create", "su2_davidson_step",
     "su2_davidson_solve", "su2_energy", "su2_davidson_vector", "su2_davidson_destroy",
-    "su2_profile_enable", "su2_profile_reset", "su2_profile_read",
+    "su2_profile_enable", "su2_profile_reset", "su2_profile_read", "su2_hash_group",
 ]
 
 
@@ -112,6 +112,7 @@ def lib():
         L.su2_profile_reset.argtypes = [vp]
         L.su2_profile_read.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                        C.POINTER(C.c_double), C.POINTER(C.c_char_p)]
+        L.su2_hash_group.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.POINTER(C.c_int64)]
         for name in SYMBOLS:
             if name != "su2_last_error":
                 getattr(L, name).restype = C.c_int
@@ -415,6 +416,16 @@ class Davidson:
             self.close()
         except Exception:
             pass
+
+
+def hash_group(worker, workers, group_count, i):
+    """su2_hash_group: the group worker `worker` of `workers` picks at its
+    i-th pick (Fig. 2 order)."""
+    g = C.c_int64()
+    rc = lib().su2_hash_group(worker, workers, group_count, i, C.byref(g))
+    if rc:
+        raise Su2Error(rc, "su2_hash_group: invalid arguments")
+    return g.value
 
 
 # same names as the C-ABI entry points

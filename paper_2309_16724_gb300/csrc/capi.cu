@@ -637,6 +637,22 @@ int su2_apply_heff_host(su2_ctx* ctx, const su2_env* env_c, const double* in_h, 
   return device_status_rc(ctx);
 }
 
+int su2_hash_group(int32_t id, int32_t step, int64_t group_count, int64_t i, int64_t* group) {
+  if (!group || step < 1 || id < 0 || id >= step || group_count < 1 || i < 0) return SU2_EINVAL;
+  int64_t a = group_count, b = step;
+  while (b) {
+    const int64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  const int64_t cycle_len = group_count / a;
+  const int64_t cycle = i / cycle_len;
+  // (id + step i + cycle) mod group_count without overflow for large i
+  const int64_t si = int64_t((__int128)step * i % group_count);
+  *group = ((int64_t(id) % group_count) + si + cycle % group_count) % group_count;
+  return SU2_OK;
+}
+
 int su2_profile_enable(su2_env* env, int32_t on) {
   if (!env) return SU2_EINVAL;
   env->prof.drain();
