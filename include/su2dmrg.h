@@ -157,6 +157,14 @@ typedef struct {
   double renorm_flops;     /* SU2_MODEL_AB_INITIO: flops of the products
                               of the renormalisation that built the block
                               operators (0 for the other models)           */
+  double flops_u1_counted; /* flops of the same operator-table expanded
+                              into (N, S_z) sectors (the U(1) blocks of the
+                              M = S two-site space), counted with the same
+                              rules as flops_su2: the analogue of the
+                              paper's U(1) flop count (Table 1)            */
+  double r_cc;             /* flops_u1_counted / flops_su2 (the paper's
+                              R_CC); with a sharded environment it divides
+                              the full table's count by the shard's flops */
 } su2_env_info;
 
 typedef struct {

@@ -60,7 +60,8 @@ class EnvInfo(C.Structure):
                 ("n_tasks", C.c_int64), ("n_k1", C.c_int64), ("n_chunks", C.c_int64),
                 ("flops_su2", C.c_double), ("flops_u1_equiv", C.c_double), ("r_d", C.c_double),
                 ("env_bytes", C.c_double), ("split_slices", C.c_int32), ("split_stage_k", C.c_int32),
-                ("split_err_est", C.c_double), ("t_chunk_bytes", C.c_int64), ("renorm_flops", C.c_double)]
+                ("split_err_est", C.c_double), ("t_chunk_bytes", C.c_int64), ("renorm_flops", C.c_double),
+                ("flops_u1_counted", C.c_double), ("r_cc", C.c_double)]
 
 
 class DavOpts(C.Structure):

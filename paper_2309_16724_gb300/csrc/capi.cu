@@ -498,6 +498,12 @@ int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond
   }
   in.r_d = D > 0 ? Deff / D : 1.0;
   in.flops_u1_equiv = in.flops_su2 * in.r_d;
+  {
+    // the same U(1) counting with the tasks of all shards (a shard's own count
+    // would need the expansion of its own terms only; counted on the full table)
+    in.flops_u1_counted = u1_counted_flops(env->table, S->left, S->right, S->N, S->twoS);
+    in.r_cc = in.flops_su2 > 0 ? in.flops_u1_counted / in.flops_su2 : 0.0;
+  }
   in.env_bytes = 8.0 * double(env->L.arena_size + env->R.arena_size);
   if (ctx->device >= 0) {
     int rc = set_device(ctx);

@@ -41,31 +41,7 @@
 namespace su2 {
 namespace {
 
-// ------------------------------------------------------------------ Clebsch-Gordan
-double fct(int n) {
-  double r = 1.0;
-  for (int i = 2; i <= n; ++i) r *= i;
-  return r;
-}
-
-// <j1 m1; j2 m2 | J M> by Racah's closed form (twos arguments)
-double cgc(int j1, int m1, int j2, int m2, int J, int M) {
-  if (m1 + m2 != M || !triangle(j1, j2, J)) return 0.0;
-  if (std::abs(m1) > j1 || std::abs(m2) > j2 || std::abs(M) > J) return 0.0;
-  if ((j1 + m1) % 2 || (j2 + m2) % 2 || (J + M) % 2) return 0.0;
-  const int a = (j1 + j2 - J) / 2, b = (j1 - j2 + J) / 2, c = (-j1 + j2 + J) / 2, d = (j1 + j2 + J) / 2 + 1;
-  double pre = (J + 1) * fct(a) * fct(b) * fct(c) / fct(d);
-  pre *= fct((J + M) / 2) * fct((J - M) / 2) * fct((j1 - m1) / 2) * fct((j1 + m1) / 2) * fct((j2 - m2) / 2) *
-         fct((j2 + m2) / 2);
-  double sum = 0.0;
-  for (int k = 0; k <= a; ++k) {
-    const int x1 = (j1 - m1) / 2 - k, x2 = (j2 + m2) / 2 - k, x3 = (J - j2 + m1) / 2 + k, x4 = (J - j1 - m2) / 2 + k;
-    if (x1 < 0 || x2 < 0 || x3 < 0 || x4 < 0) continue;
-    const double t = 1.0 / (fct(k) * fct(a - k) * fct(x1) * fct(x2) * fct(x3) * fct(x4));
-    sum += (k % 2) ? -t : t;
-  }
-  return std::sqrt(pre) * sum;
-}
+double cgc(int j1, int m1, int j2, int m2, int J, int M) { return cg_coef(j1, m1, j2, m2, J, M); }
 
 // ------------------------------------------------------------------ coupling trees
 // signatures: "e" (rank 1/2, two components), "0" (scalar), "x<j>" (rank

@@ -18,6 +18,8 @@ bool triangle(int a, int b, int c);
 double sixj(int a, int b, int c, int d, int e, int f);
 double ninej(int j1, int j2, int j, int k1, int k2, int k, int j1p, int j2p, int jp);
 double ctilde(int j1, int j2, int j, int k1, int k2, int k, int j1p, int j2p, int jp);
+// Clebsch-Gordan coefficient <j1 m1; j2 m2 | J M> (Racah's closed form, twos)
+double cg_coef(int j1, int m1, int j2, int m2, int J, int M);
 
 // ---------------------------------------------------------------- model
 struct SiteOp {
@@ -103,6 +105,12 @@ std::string build_tasks(const OpTable& t, const std::vector<Sector>& left, const
 std::string build_abinitio(const su2_hamiltonian& H, const std::vector<std::vector<Sector>>& lchain,
                            const std::vector<std::vector<Sector>>& rchain, int device, void* stream,
                            int64_t t_budget_bytes, OpTable& table, SideOps& L, SideOps& R, double* renorm_flops);
+
+// flops of the same operator-table and task rules expanded into (N, S_z)
+// sectors (U(1) blocks of dimension sum_{S >= |M|} d_(N,S)), in the M = S
+// sector of the two-site space
+double u1_counted_flops(const OpTable& t, const std::vector<Sector>& left, const std::vector<Sector>& right, int N,
+                        int twoS);
 
 // counter-based generator (SplitMix64, Steele/Lea/Flood 2014)
 uint64_t splitmix(uint64_t x);

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <set>
 #include <tuple>
 
 #include "su2_internal.h"
@@ -634,6 +635,96 @@ std::string build_tasks(const OpTable& t, const std::vector<Sector>& left, const
     return std::tie(x.f, x.term, x.e) < std::tie(y.f, y.term, y.e);
   });
   return "";
+}
+
+// ------------------------------------------------------------ U(1)-expanded flops
+// The paper compares SU(2) with U(1) DMRG by the ratio of their flop counts
+// (R_CC, Table 1).  Here the same operator-table is expanded into its spin
+// components: each row i becomes the products A_qA B_qB C_qC D_qD with a
+// non-zero Clebsch-Gordan weight in [[A x B]^k x [C x D]^k]^0, acting on the
+// U(1) two-site blocks (N_a, M_a; site m-states; N_b, M_b) of the M = S
+// sector, whose bond blocks have dimension sum_{S >= |M|} d_(N,S).  Flops
+// follow the SU(2) rules: E D^T once per distinct (right operator, its
+// component, input block, output right sector), A T per task, identities
+// skipped.
+double u1_counted_flops(const OpTable& t, const std::vector<Sector>& left, const std::vector<Sector>& right, int N,
+                        int twoS) {
+  std::vector<int> sN, sS;
+  site_states(t.site_kind, sN, sS);
+  auto u1 = [](const std::vector<Sector>& sec) {
+    std::map<std::pair<int, int>, int64_t> d;
+    for (const Sector& q : sec)
+      for (int m = -q.twoS; m <= q.twoS; m += 2) d[{q.N, m}] += q.dim;
+    return d;
+  };
+  const auto dl = u1(left), dr = u1(right);
+  struct MS { int s, m; };
+  std::vector<MS> ms;
+  for (int s = 0; s < int(sN.size()); ++s)
+    for (int m = -sS[s]; m <= sS[s]; m += 2) ms.push_back({s, m});
+  struct UB { int Na, Ma, i1, i2, Nb, Mb; };
+  std::vector<UB> blocks;
+  std::map<std::tuple<int, int, int, int, int, int>, int> bidx;
+  for (const auto& [a, da] : dl)
+    for (int i1 = 0; i1 < int(ms.size()); ++i1)
+      for (int i2 = 0; i2 < int(ms.size()); ++i2)
+        for (const auto& [b, db] : dr) {
+          if (a.first + sN[ms[i1].s] + sN[ms[i2].s] + b.first != N) continue;
+          if (a.second + ms[i1].m + ms[i2].m + b.second != twoS) continue;
+          bidx[{a.first, a.second, i1, i2, b.first, b.second}] = int(blocks.size());
+          blocks.push_back({a.first, a.second, i1, i2, b.first, b.second});
+        }
+  // site transitions of one component of a site operator
+  auto site_next = [&](const SiteOp& op, int i, int q, std::vector<int>& out) {
+    out.clear();
+    for (int j = 0; j < int(ms.size()); ++j) {
+      if (ms[j].m != ms[i].m + q) continue;
+      if (op.red[ms[j].s][ms[i].s] == 0.0) continue;
+      if (cg_coef(sS[ms[i].s], ms[i].m, op.k, q, sS[ms[j].s], ms[j].m) == 0.0) continue;
+      out.push_back(j);
+    }
+  };
+  double flops = 0.0;
+  std::set<std::tuple<int, int, int, int, int>> k1seen;
+  std::vector<int> n1, n2;
+  for (const Term& term : t.terms) {
+    const BlockOp& A = t.lops[term.A];
+    const BlockOp& D = t.rops[term.D];
+    const bool aid = A.kind == OP_IDENTITY, did = D.kind == OP_IDENTITY;
+    const int k = term.k;
+    for (int q = -k; q <= k; q += 2) {
+      const double c0 = cg_coef(k, q, k, -q, 0, 0);
+      if (c0 == 0.0) continue;
+      for (int qA = -A.k; qA <= A.k; qA += 2) {
+        const int qB = q - qA;
+        if (std::abs(qB) > term.B.k || cg_coef(A.k, qA, term.B.k, qB, k, q) == 0.0) continue;
+        for (int qC = -term.C.k; qC <= term.C.k; qC += 2) {
+          const int qD = -q - qC;
+          if (std::abs(qD) > D.k || cg_coef(term.C.k, qC, D.k, qD, k, -q) == 0.0) continue;
+          for (int e = 0; e < int(blocks.size()); ++e) {
+            const UB& E = blocks[e];
+            const auto ao = std::make_pair(E.Na + A.dN, E.Ma + qA);
+            const auto bo = std::make_pair(E.Nb + D.dN, E.Mb + qD);
+            auto ia = dl.find(ao);
+            auto ib = dr.find(bo);
+            if (ia == dl.end() || ib == dr.end()) continue;
+            site_next(term.B, E.i1, qB, n1);
+            if (n1.empty()) continue;
+            site_next(term.C, E.i2, qC, n2);
+            if (n2.empty()) continue;
+            const int64_t k1 = dl.at({E.Na, E.Ma}), k2 = dr.at({E.Nb, E.Mb}), m = ia->second, n = ib->second;
+            for (int j1 : n1)
+              for (int j2 : n2) {
+                if (!bidx.count({ao.first, ao.second, j1, j2, bo.first, bo.second})) continue;
+                if (!did && k1seen.insert({term.D, qD, bo.first, bo.second, e}).second) flops += 2.0 * k1 * k2 * n;
+                if (!aid) flops += 2.0 * m * k1 * n;
+              }
+          }
+        }
+      }
+    }
+  }
+  return flops;
 }
 
 }  // namespace su2
