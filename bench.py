@@ -44,7 +44,7 @@ def k2_traffic(workload, slices, stage_k):
     root = os.path.dirname(os.path.abspath(__file__))
     src = os.path.join(root, "paper_2309_16724_gb300", "csrc")
     try:
-        txt = open(os.path.join(root, "profiles", "split_gemm_traffic_qc32.md")).read()
+        txt = open(os.path.join(root, "profiles", "split_gemm_dram_qc48.md")).read()
         h = hashlib.sha256()
         for f in ("split_gemm.cuh", "heff_split.cu"):
             h.update(open(os.path.join(src, f), "rb").read())

@@ -326,10 +326,11 @@ class _Grow:
     """One renormalisation step: coupled products of a site operator and an
     operator of the previous block, projected on the new bond's MPS basis."""
 
-    def __init__(self, cfg, step, prev, cur, left):
+    def __init__(self, A, prev, cur, left):
+        """A: MPS tensor {new sector: (stacked rows [(q_prev, site, row0, d)],
+        Q with orthonormal columns)} from bond `prev` to bond `cur`."""
         self.left = left
-        side = envmod.SIDE_MPS_L if left else envmod.SIDE_MPS_R
-        self.A = envmod.mps_tensor(cfg.seed, side, step, prev, cur, synth.SPATIAL_ORBITAL)
+        self.A = A
         self.prev, self.cur = prev, cur
         self.sites = synth.site_states(synth.SPATIAL_ORBITAL)
 
@@ -380,35 +381,49 @@ class RightBlock:
     """Operators of a right block (orbitals first .. L-1), grown from the
     vacuum one orbital at a time (site added on the left of the block)."""
 
-    def __init__(self, strings, cfg, n_sites):
+    def __init__(self, strings, L):
         self.S = strings
-        self.cfg = cfg
-        L = cfg.L
-        chain = synth.bond_sector_chain(cfg, n_sites)
-        self.sectors = chain[0]
+        self.L = L
+        self.sectors = [(0, 0, 1)]
         self.orbs = []
         self.N1, self.C = {}, {}
         self._direct_cache = {}
+
+    @classmethod
+    def seeded(cls, strings, cfg, n_sites):
+        """The block of the last n_sites orbitals of cfg from its seeded MPS."""
+        b = cls(strings, cfg.L)
+        chain = synth.bond_sector_chain(cfg, n_sites)
         for step in range(1, n_sites + 1):
-            s = L - step
-            g = _Grow(cfg, step, chain[step - 1], chain[step], left=False)
-            outside = _elementary(range(s))
-            N1, C = {}, {}
-            I_site = site_op((), ())
-            for (o, d) in _elementary([s]):
-                N1[(o, d)] = g.build(1, 1 if d == CREATE else -1, 1, [(1.0, site_op((d,), ()), None, 1)])
-            for x, X in self.N1.items():
-                N1[x] = g.build(1, X.dN, 1, [(1.0, I_site, X, 1)])
-            for (O, lam) in _outside_keys(outside, 2):
-                kO = lab_rank(len(O), lam)
-                dN, par = _ops_meta(O)
-                contribs = self._recursion(O, lam, s)
-                if contribs:
-                    C[(O, lam)] = g.build(kO, -dN, par, contribs)
-            self.N1, self.C = N1, C
-            self.orbs = [s] + self.orbs
-            self.sectors = chain[step]
-            self._direct_cache = {}
+            A = envmod.mps_tensor(cfg.seed, envmod.SIDE_MPS_R, step, chain[step - 1], chain[step],
+                                  synth.SPATIAL_ORBITAL)
+            b = b.grown(chain[step], A)
+        return b
+
+    def grown(self, cur, A):
+        """A new block: this one with orbital s = first - 1 added on its left,
+        projected on the bond `cur` by the MPS tensor A (rows stacked
+        (block sector, site state), see ``env.mps_tensor``)."""
+        s = (self.orbs[0] if self.orbs else self.L) - 1
+        g = _Grow(A, self.sectors, cur, left=False)
+        outside = _elementary(range(s))
+        N1, C = {}, {}
+        I_site = site_op((), ())
+        for (o, d) in _elementary([s]):
+            N1[(o, d)] = g.build(1, 1 if d == CREATE else -1, 1, [(1.0, site_op((d,), ()), None, 1)])
+        for x, X in self.N1.items():
+            N1[x] = g.build(1, X.dN, 1, [(1.0, I_site, X, 1)])
+        for (O, lam) in _outside_keys(outside, 2):
+            kO = lab_rank(len(O), lam)
+            dN, par = _ops_meta(O)
+            contribs = self._recursion(O, lam, s)
+            if contribs:
+                C[(O, lam)] = g.build(kO, -dN, par, contribs)
+        b = RightBlock(self.S, self.L)
+        b.N1, b.C = N1, C
+        b.orbs = [s] + self.orbs
+        b.sectors = list(cur)
+        return b
 
     def get(self, O, lam):
         """C(O, lam) of the current block (None when it vanishes)."""
@@ -483,55 +498,69 @@ class LeftBlock:
     operators with one and two elementary factors, complementary operators
     with |O| <= 1 outside factors (H and the three-index operators)."""
 
-    def __init__(self, strings, cfg, n_sites):
+    def __init__(self, strings, L):
         self.S = strings
-        self.cfg = cfg
-        L = cfg.L
-        chain = synth.bond_sector_chain(cfg, n_sites)
-        self.sectors = chain[0]
+        self.L = L
+        self.sectors = [(0, 0, 1)]
         self.orbs = []
         self.N1, self.N2, self.C = {}, {}, {}
         self._direct_cache = {}
-        I_site = site_op((), ())
+
+    @classmethod
+    def seeded(cls, strings, cfg, n_sites):
+        """The block of the first n_sites orbitals of cfg from its seeded MPS."""
+        b = cls(strings, cfg.L)
+        chain = synth.bond_sector_chain(cfg, n_sites)
         for step in range(1, n_sites + 1):
-            s = step - 1
-            g = _Grow(cfg, step, chain[step - 1], chain[step], left=True)
-            outside = _elementary(range(s + 1, L))
-            N1, N2, C = {}, {}, {}
-            for x, X in self.N1.items():
-                N1[x] = g.build(1, X.dN, 1, [(1.0, I_site, X, 1)])
-            for (o, d) in _elementary([s]):
-                N1[(o, d)] = g.build(1, 1 if d == CREATE else -1, 1, [(1.0, site_op((d,), ()), None, 1)])
-            for (pair, lab), X in self.N2.items():
-                N2[(pair, lab)] = g.build(X.k, X.dN, 0, [(1.0, I_site, X, X.k)])
-            for x, X in self.N1.items():
-                for y in _elementary([s]):
-                    for lab in labelings(2):
-                        K = lab[0]
-                        dN, _ = _ops_meta((x, y))
-                        N2[((x, y), lab)] = g.build(K, dN, 0, [(1.0, site_op((y[1],), ()), X, K)])
-            sel = _elementary([s])
-            for a in range(2):
-                for b in range(a, 2):
-                    pair = (sel[a], sel[b])
-                    for lab in labelings(2):
-                        if not valid_labels(pair, lab):
-                            continue
-                        Y = site_op((pair[0][1], pair[1][1]), lab)
-                        if Y is None:
-                            continue
-                        dN, _ = _ops_meta(pair)
-                        N2[(pair, lab)] = g.build(lab[0], dN, 0, [(1.0, Y, None, lab[0])])
-            for (O, lam) in _outside_keys(outside, 1):
-                kO = lab_rank(len(O), lam)
-                dN, par = _ops_meta(O)
-                contribs = self._recursion(O, lam, s)
-                if contribs:
-                    C[(O, lam)] = g.build(kO, -dN, par, contribs)
-            self.N1, self.N2, self.C = N1, N2, C
-            self.orbs = self.orbs + [s]
-            self.sectors = chain[step]
-            self._direct_cache = {}
+            A = envmod.mps_tensor(cfg.seed, envmod.SIDE_MPS_L, step, chain[step - 1], chain[step],
+                                  synth.SPATIAL_ORBITAL)
+            b = b.grown(chain[step], A)
+        return b
+
+    def grown(self, cur, A):
+        """A new block: this one with orbital s = last + 1 added on its right,
+        projected on the bond `cur` by the MPS tensor A."""
+        s = len(self.orbs)
+        L = self.L
+        I_site = site_op((), ())
+        g = _Grow(A, self.sectors, cur, left=True)
+        outside = _elementary(range(s + 1, L))
+        N1, N2, C = {}, {}, {}
+        for x, X in self.N1.items():
+            N1[x] = g.build(1, X.dN, 1, [(1.0, I_site, X, 1)])
+        for (o, d) in _elementary([s]):
+            N1[(o, d)] = g.build(1, 1 if d == CREATE else -1, 1, [(1.0, site_op((d,), ()), None, 1)])
+        for (pair, lab), X in self.N2.items():
+            N2[(pair, lab)] = g.build(X.k, X.dN, 0, [(1.0, I_site, X, X.k)])
+        for x, X in self.N1.items():
+            for y in _elementary([s]):
+                for lab in labelings(2):
+                    K = lab[0]
+                    dN, _ = _ops_meta((x, y))
+                    N2[((x, y), lab)] = g.build(K, dN, 0, [(1.0, site_op((y[1],), ()), X, K)])
+        sel = _elementary([s])
+        for a in range(2):
+            for b_ in range(a, 2):
+                pair = (sel[a], sel[b_])
+                for lab in labelings(2):
+                    if not valid_labels(pair, lab):
+                        continue
+                    Y = site_op((pair[0][1], pair[1][1]), lab)
+                    if Y is None:
+                        continue
+                    dN, _ = _ops_meta(pair)
+                    N2[(pair, lab)] = g.build(lab[0], dN, 0, [(1.0, Y, None, lab[0])])
+        for (O, lam) in _outside_keys(outside, 1):
+            kO = lab_rank(len(O), lam)
+            dN, par = _ops_meta(O)
+            contribs = self._recursion(O, lam, s)
+            if contribs:
+                C[(O, lam)] = g.build(kO, -dN, par, contribs)
+        b = LeftBlock(self.S, self.L)
+        b.N1, b.N2, b.C = N1, N2, C
+        b.orbs = self.orbs + [s]
+        b.sectors = list(cur)
+        return b
 
     def get(self, O, lam):
         if len(O) <= 1 and self.orbs:
@@ -626,16 +655,24 @@ def _split4(S, nL, p, q):
 
 
 def build_problem(cfg, h=None, eri=None):
-    """(OperatorTable, env) of the ab initio Hamiltonian of cfg at its middle
-    bond (left block cfg.n_left orbitals, sites p = n_left and q = n_left + 1,
-    right block the rest).  Integrals default to ``synth.integrals``."""
+    """(OperatorTable, env, left sectors, right sectors) of the ab initio
+    Hamiltonian of cfg at its middle bond (left block cfg.n_left orbitals,
+    sites p = n_left and q = n_left + 1, right block the rest), blocks from
+    the seeded MPS.  Integrals default to ``synth.integrals``."""
     if h is None:
         h, eri = synth.integrals(cfg.L, cfg.seed)
     strings = hamiltonian_strings(h, eri)
-    nL, nR = cfg.n_left, cfg.n_right
+    Lb = LeftBlock.seeded(strings, cfg, cfg.n_left)
+    Rb = RightBlock.seeded(strings, cfg, cfg.n_right)
+    return problem_from_blocks(strings, Lb, Rb)
+
+
+def problem_from_blocks(strings, Lb, Rb):
+    """(OperatorTable, env, left sectors, right sectors) at the two-site bond
+    between a left block (orbitals 0 .. nL-1) and a right block (orbitals
+    nL+2 .. L-1); sites p = nL, q = nL + 1."""
+    nL = len(Lb.orbs)
     p, q = nL, nL + 1
-    Lb = LeftBlock(strings, cfg, nL)
-    Rb = RightBlock(strings, cfg, nR)
     lsec, rsec = Lb.sectors, Rb.sectors
     table = model.OperatorTable(synth.SPATIAL_ORBITAL)
     env = {}
@@ -741,7 +778,7 @@ def build_problem(cfg, h=None, eri=None):
     # family (i): left complementary x sites x right normal
     left_keys = []
     sites_ops = _elementary([p, q])
-    right_el = _elementary(list(range(q + 1, cfg.L)))
+    right_el = _elementary(list(range(q + 1, Lb.L)))
     for o in sites_ops + right_el:
         left_keys.append(((o,), ()))
     outside_L = sites_ops + right_el

@@ -1,0 +1,155 @@
+"""Two-site sweep of SU(2) spin-adapted DMRG (Sec. II) on the ab initio
+Hamiltonian: at every bond the lowest eigenpair of H_eff (Davidson), the
+singular value decomposition of the reduced two-site wavefunction per bond
+sector, truncation to D multiplets, and the block grown by one orbital with
+the kept singular vectors (renormalisation, Sec. II.C).
+
+Oracle module (test infrastructure only).  Plain Python/NumPy, FP64.
+
+Readings (the paper gives no sweep algorithm):
+* Total spin S = 0: every two-site block has j_L1 = j_2R = j, so the
+  reduced wavefunction of the bond sector (N_L1, j) is one matrix with rows
+  (left sector a, site s1) and columns (site s2, right sector b), stacked as
+  in ``env.mps_tensor`` (previous sector outer, site state inner).
+* Truncation keeps the D largest sigma^2 (one per multiplet) over all
+  sectors; ties go to the lower (N, 2S) sector, then the lower index.
+* Moving right, the left block grows with U (the left singular vectors);
+  moving left, the right block grows with V.  Each Davidson starts from a
+  seeded Gaussian vector (no wavefunction prediction: slower, equally exact).
+* Sweep order: bonds i = 0 .. L-2 (window sites i, i+1) left to right, then
+  L-2 .. 0; the initial right blocks come from the seeded MPS of the bond
+  recipe.
+
+Parity: pinned by full CI (with bonds that keep every multiplet every step's
+energy is the ground-state energy) and by the variational bound with
+truncated bonds.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import synth
+from . import abinitio, davidson, heff, sectors
+from . import env as envmod
+from .su2 import triangle
+
+
+def _stacks(prev, sites, Nq, Sq):
+    """Stacked rows (prev sector, site state) of a new sector, in the order of
+    ``env.mps_tensor``: [(qp, s, r0, d)] and the total."""
+    rows, r0 = [], 0
+    for qp, (Np, Sp, dp) in enumerate(prev):
+        for s, (ns, ts) in enumerate(sites):
+            if Np + ns == Nq and triangle(Sp, ts, Sq):
+                rows.append((qp, s, r0, dp))
+                r0 += dp
+    return rows, r0
+
+
+def _bond_matrices(psi, blocks, left, right, site_kind, N):
+    """{(N_L1, j): (left stacks, right stacks, matrix)} of an S = 0 two-site
+    wavefunction across the bond between the two sites."""
+    sites = synth.site_states(site_kind)
+    bidx = sectors.block_index(blocks)
+    keys = sorted({(left[B.a][0] + sites[B.s1][0], B.jL1) for B in blocks})
+    out = {}
+    for (Nq, j) in keys:
+        lrows, nr = _stacks(left, sites, Nq, j)
+        rrows, nc = _stacks(right, sites, N - Nq, j)
+        M = np.zeros((nr, nc))
+        for (a, s1, r0, da) in lrows:
+            for (b, s2, c0, db) in rrows:
+                i = bidx.get((a, s1, s2, b, j, j))
+                if i is not None:
+                    M[r0:r0 + da, c0:c0 + db] = sectors.block_view(psi, blocks[i])
+        out[(Nq, j)] = (lrows, rrows, M)
+    return out
+
+
+def _truncate(svals, D):
+    """Indices kept per sector: the D largest sigma^2, ties to the lower
+    (N, 2S) sector and then the lower index."""
+    cand = []
+    for key, s in svals.items():
+        for i, x in enumerate(s):
+            cand.append((-x * x, key, i))
+    cand.sort()
+    keep = {}
+    for (_, key, i) in cand[:D]:
+        keep.setdefault(key, []).append(i)
+    return keep
+
+
+def isometry(psi, blocks, left, right, site_kind, N, D, side):
+    """New bond sectors and MPS tensor of the grown block (side 'L': the left
+    block grows by site 1 with U; 'R': the right block grows by site 2 with
+    V), and the discarded weight."""
+    mats = _bond_matrices(psi, blocks, left, right, site_kind, N)
+    svd, svals = {}, {}
+    for key, (lrows, rrows, M) in mats.items():
+        U, s, Vt = np.linalg.svd(M, full_matrices=False)
+        svd[key] = (U, Vt.T)
+        svals[key] = s
+    keep = _truncate(svals, D)
+    total = sum(float(np.sum(s * s)) for s in svals.values())
+    kept = sum(float(np.sum(svals[k][idx] ** 2)) for k, idx in keep.items())
+    new = []
+    for (Nq, j), idx in keep.items():
+        Nb = Nq if side == "L" else N - Nq
+        new.append((Nb, j, len(idx), (Nq, j), idx))
+    new.sort()
+    sec = [(Nb, j, d) for (Nb, j, d, _, _) in new]
+    A = {}
+    for qo, (Nb, j, d, key, idx) in enumerate(new):
+        lrows, rrows, _ = mats[key]
+        U, V = svd[key]
+        if side == "L":
+            A[qo] = (lrows, U[:, sorted(idx)])
+        else:
+            A[qo] = (rrows, V[:, sorted(idx)])
+    return sec, A, total - kept
+
+
+def _solve(strings, Lb, Rb, N, seed, tol):
+    table, env, ls, rs = abinitio.problem_from_blocks(strings, Lb, Rb)
+    blocks, n = sectors.build_blocks(ls, rs, synth.SPATIAL_ORBITAL, N, 0)
+    tasks = heff.build_tasks(table, ls, rs, blocks, 0)
+    apply = lambda v: heff.apply_heff(table, env, tasks, blocks, n, v)
+    diag = heff.diag_heff(table, env, tasks, blocks, n)
+    theta, x, res, it = davidson.davidson(apply, diag, synth.gaussian_psi(n, seed), tol=tol)
+    return theta, x, blocks, ls, rs
+
+
+def sweep(cfg, D, n_half, tol=1e-9, h=None, eri=None):
+    """Energies of every two-site step of n_half half-sweeps (S = 0), with the
+    initial right blocks from cfg's seeded MPS; returns (energies, discarded
+    weights)."""
+    assert cfg.twoS == 0 and cfg.site_kind == synth.SPATIAL_ORBITAL
+    if h is None:
+        h, eri = synth.integrals(cfg.L, cfg.seed)
+    strings = abinitio.hamiltonian_strings(h, eri)
+    L, N = cfg.L, cfg.N
+    chain = synth.bond_sector_chain(cfg, L - 2)
+    R = [abinitio.RightBlock(strings, L)]
+    for k in range(1, L - 1):
+        A = envmod.mps_tensor(cfg.seed, envmod.SIDE_MPS_R, k, chain[k - 1], chain[k], synth.SPATIAL_ORBITAL)
+        R.append(R[-1].grown(chain[k], A))
+    Lbs = [abinitio.LeftBlock(strings, L)] + [None] * (L - 2)
+    energies, discarded = [], []
+    step = 0
+    for half in range(n_half):
+        order = range(0, L - 1) if half % 2 == 0 else range(L - 2, -1, -1)
+        for i in order:
+            Lb, Rb = Lbs[i], R[L - 2 - i]
+            theta, x, blocks, ls, rs = _solve(strings, Lb, Rb, N, cfg.seed + 1000 + step, tol)
+            step += 1
+            energies.append(theta)
+            if half % 2 == 0 and i < L - 2:
+                sec, A, w = isometry(x, blocks, ls, rs, synth.SPATIAL_ORBITAL, N, D, "L")
+                Lbs[i + 1] = Lb.grown(sec, A)
+                discarded.append(w)
+            elif half % 2 == 1 and i > 0:
+                sec, A, w = isometry(x, blocks, ls, rs, synth.SPATIAL_ORBITAL, N, D, "R")
+                R[L - 1 - i] = Rb.grown(sec, A)
+                discarded.append(w)
+    return np.array(energies), np.array(discarded)
