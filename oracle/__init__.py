@@ -27,6 +27,9 @@ Each function cites the passage of arXiv:2309.16724 it follows:
                seeded MPS (Sec. II.A, II.C) and the operator-table at the
                two-site bond.
 * ``fci``      full configuration interaction of small ab initio problems.
+* ``sweep``    the two-site sweep (Sec. II): Davidson at every bond, SVD of
+               the reduced wavefunction per bond sector, truncation to D
+               multiplets, block growth with the kept singular vectors.
 * ``davidson`` Davidson eigensolver (the diagonalisation of Sec. II).
 * ``ed``       exact diagonalisation of small Heisenberg chains.
 
