@@ -298,6 +298,35 @@ int su2_energy(const su2_dav* dav, double* E);
 int su2_davidson_vector(su2_ctx* ctx, su2_dav* dav, double* x_dev);
 int su2_davidson_destroy(su2_dav* dav);
 
+/* Two-site sweep of the ab initio model (Sec. II; total spin 0): at every
+ * window (sites i, i+1) the environment is assembled from blocks kept on the
+ * device, the lowest eigenpair of H_eff found by Davidson (split or FP64
+ * H.psi), the reduced two-site wavefunction decomposed per bond sector by a
+ * singular value decomposition (on the host), the D largest singular values
+ * kept (ties to the lower (N, 2S) sector, then the lower index), and the
+ * block on the side the sweep moves to grown by one orbital with the kept
+ * singular vectors (renormalisation on the device, Sec. IV.D).  The sweep
+ * starts at window 0 moving right with the right blocks of a seeded MPS
+ * (right_chain: the bonds of 0 .. L-2 orbitals, L = n_left + 2 + n_right)
+ * and turns at the ends; every window's Davidson starts from a seeded vector
+ * (no wavefunction prediction).  Device contexts only. */
+typedef struct su2_sweep su2_sweep;
+typedef struct {
+  int32_t D;             /* multiplets kept per bond                        */
+  int32_t prec;          /* su2_prec of the Davidson H.psi                  */
+  double tol;            /* Davidson residual 2-norm (0: 1e-8)              */
+  int32_t max_iter;      /* Davidson iterations per window (0: 400)         */
+  int32_t n_slices;      /* BF16 slices of the split path (0: 5)            */
+  uint64_t guess_seed;   /* seed of the Davidson start vectors              */
+} su2_sweep_opts;
+int su2_sweep_create(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond_chain* right_chain, int32_t N,
+                     const su2_sweep_opts* opts, su2_sweep** out);
+/* Runs n_steps windows; energies[k] is the Davidson energy of the k-th
+ * window run, discarded[k] the weight (sum of sigma^2) dropped by its
+ * truncation (0 at a turn); either may be NULL. */
+int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies, double* discarded);
+int su2_sweep_destroy(su2_sweep* sw);
+
 /* Group order of the paper's hash-based semi-dynamic scheduling (Sec.
  * III.D, Fig. 2) for a multi-GPU run: worker `id` of `step` workers picks, at
  * its i-th pick, group (id + step * i + cycle) mod group_count, where

@@ -26,6 +26,7 @@ SYMBOLS = [
     "su2_apply_heff", "su2_apply_heff_host", "su2_apply_heff_static_scratch", "su2_diag_heff", "su2_davidson_create", "su2_davidson_step",
     "su2_davidson_solve", "su2_energy", "su2_davidson_vector", "su2_davidson_destroy",
     "su2_profile_enable", "su2_profile_reset", "su2_profile_read", "su2_hash_group",
+    "su2_sweep_create", "su2_sweep_run", "su2_sweep_destroy",
 ]
 
 
@@ -62,6 +63,11 @@ class EnvInfo(C.Structure):
                 ("env_bytes", C.c_double), ("split_slices", C.c_int32), ("split_stage_k", C.c_int32),
                 ("split_err_est", C.c_double), ("t_chunk_bytes", C.c_int64), ("renorm_flops", C.c_double),
                 ("flops_u1_counted", C.c_double), ("r_cc", C.c_double)]
+
+
+class SweepOpts(C.Structure):
+    _fields_ = [("D", C.c_int32), ("prec", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
+                ("n_slices", C.c_int32), ("guess_seed", C.c_uint64)]
 
 
 class DavOpts(C.Structure):
@@ -114,6 +120,10 @@ def lib():
         L.su2_profile_read.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                        C.POINTER(C.c_double), C.POINTER(C.c_char_p)]
         L.su2_hash_group.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.POINTER(C.c_int64)]
+        L.su2_sweep_create.argtypes = [vp, C.POINTER(Hamiltonian), C.POINTER(BondChain), C.c_int32,
+                                       C.POINTER(SweepOpts), C.POINTER(vp)]
+        L.su2_sweep_run.argtypes = [vp, vp, C.c_int32, vp, vp]
+        L.su2_sweep_destroy.argtypes = [vp]
         for name in SYMBOLS:
             if name != "su2_last_error":
                 getattr(L, name).restype = C.c_int
@@ -410,6 +420,47 @@ class Davidson:
     def close(self):
         if self.h:
             lib().su2_davidson_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Sweep:
+    """su2_sweep_create / su2_sweep_run: the two-site sweep of the ab initio
+    model (S = 0) on the GPU, starting at window 0 moving right with the right
+    blocks of the seeded MPS of `right_chain` (bonds of 0 .. L-2 orbitals)."""
+
+    def __init__(self, ctx: Context, h, eri, right_chain, N, D, prec=SU2_SPLIT_BF16, tol=1e-8, max_iter=400,
+                 n_slices=5, seed=0, guess_seed=1):
+        self.ctx = ctx
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        eri = np.ascontiguousarray(eri, dtype=np.float64)
+        L = h.shape[0]
+        if eri.shape != (L, L, L, L) or len(right_chain) != L - 1:
+            raise Su2Error(SU2_EINVAL, "integrals or chain of the wrong size")
+        self._keep = (h, eri)
+        H = Hamiltonian(SU2_MODEL_AB_INITIO, 0, L - 2, 1.0, seed, h.ctypes.data, eri.ctypes.data)
+        rc_, keep = _chain(right_chain)
+        o = SweepOpts(D, prec, tol, max_iter, n_slices, guess_seed)
+        hd = C.c_void_p()
+        ctx.check(lib().su2_sweep_create(ctx.h, C.byref(H), C.byref(rc_), N, C.byref(o), C.byref(hd)))
+        self.h = hd
+        self.L = L
+
+    def run(self, n_steps):
+        """(energies, discarded weights) of the next n_steps windows."""
+        e = np.zeros(n_steps)
+        w = np.zeros(n_steps)
+        self.ctx.check(lib().su2_sweep_run(self.ctx.h, self.h, n_steps, e.ctypes.data, w.ctypes.data))
+        return e, w
+
+    def close(self):
+        if self.h:
+            lib().su2_sweep_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -410,6 +410,80 @@ void shard_terms(std::vector<Task>& tasks, const std::vector<Block>& blocks, int
   tasks.swap(kept);
 }
 
+}  // extern "C"
+
+// Execution plan, environment info, device uploads and the split-precision
+// arenas of an environment whose table, operators and tasks are set; on
+// failure the environment is deleted.
+static int finish_env(su2_ctx* ctx, su2_env* env, const su2_sectors* S, const su2_env_opts* opts) {
+  int64_t budget = (opts && opts->t_budget_bytes > 0) ? opts->t_budget_bytes : (int64_t(2) << 30);
+  int rc2 = build_plan(env, S, budget);
+  if (rc2) {
+    delete env;
+    return rc2;
+  }
+  // info
+  su2_env_info& in = env->info;
+  in.psi_len = S->psi_len;
+  in.n_blocks = int64_t(S->blocks.size());
+  in.n_terms = int64_t(env->table.terms.size());
+  in.n_tasks = int64_t(env->tasks.size());
+  double D = 0, Deff = 0;
+  for (const Sector& s : S->left) {
+    D += s.dim;
+    Deff += double(s.dim) * (s.twoS + 1);
+  }
+  in.r_d = D > 0 ? Deff / D : 1.0;
+  in.flops_u1_equiv = in.flops_su2 * in.r_d;
+  {
+    // the same U(1) counting with the tasks of all shards (a shard's own count
+    // would need the expansion of its own terms only; counted on the full table)
+    in.flops_u1_counted = u1_counted_flops(env->table, S->left, S->right, S->N, S->twoS);
+    in.r_cc = in.flops_su2 > 0 ? in.flops_u1_counted / in.flops_su2 : 0.0;
+  }
+  in.env_bytes = 8.0 * double(env->L.arena_size + env->R.arena_size);
+  if (ctx->device >= 0) {
+    int rc = set_device(ctx);
+    for (int side = 0; side < 2 && !rc; ++side) {
+      SideOps& so = side == 0 ? env->L : env->R;
+      double** dst = side == 0 ? &env->dL : &env->dR;
+      if (so.dev_ready) {  // filled on the device by the builder
+        *dst = so.dev_ready;
+        so.dev_ready = nullptr;
+      } else if (so.host_values) {
+        rc = upload(ctx, dst, so.arena);
+      } else {
+        rc = dev_alloc(ctx, dst, size_t(std::max<int64_t>(so.arena_size, 2)));
+        if (!rc) {
+          const int ce = generate_side(so, *dst, ctx->stream);
+          if (ce) rc = fail(ctx, SU2_ECUDA, std::string("operator generation: ") + cudaGetErrorString(cudaError_t(ce)));
+        }
+      }
+    }
+    if (!rc) rc = dev_alloc(ctx, &env->dT, size_t(std::max<int64_t>(env->t_elems, 2)));
+    if (!rc) rc = upload(ctx, &env->dk1, env->k1);
+    if (!rc) rc = upload(ctx, &env->dk2, env->k2);
+    if (!rc) rc = upload(ctx, &env->dk2t, env->k2t);
+    if (!rc) rc = upload(ctx, &env->ddj, env->dj);
+    if (!rc) rc = upload(ctx, &env->ddt, env->dt);
+    if (!rc && opts && (opts->prepare_split || opts->autotune)) {
+      std::string err;
+      if (opts->autotune) rc = split_autotune(env, opts->split_tol > 0 ? opts->split_tol : 3e-11, err);
+      else rc = split_prepare(env, opts->n_slices > 0 ? opts->n_slices : 5, err);
+      if (rc) fail(ctx, rc, err);
+    }
+    if (rc) {
+      env_free_device(env);
+      delete env;
+      return rc;
+    }
+  }
+  return SU2_OK;
+}
+
+
+extern "C" {
+
 int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond_chain* lc, const su2_bond_chain* rc,
                           const su2_sectors* S, const su2_env_opts* opts, su2_env** out) {
   if (!ctx || !H || !lc || !rc || !S || !out) return fail(ctx, SU2_EINVAL, "null argument");
@@ -479,67 +553,9 @@ int su2_build_environment(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond
     delete env;
     return fail(ctx, SU2_EINVAL, ex.what());
   }
-  int64_t budget = (opts && opts->t_budget_bytes > 0) ? opts->t_budget_bytes : (int64_t(2) << 30);
-  int rc2 = build_plan(env, S, budget);
-  if (rc2) {
-    delete env;
-    return rc2;
-  }
-  // info
-  su2_env_info& in = env->info;
-  in.psi_len = S->psi_len;
-  in.n_blocks = int64_t(S->blocks.size());
-  in.n_terms = int64_t(env->table.terms.size());
-  in.n_tasks = int64_t(env->tasks.size());
-  double D = 0, Deff = 0;
-  for (const Sector& s : S->left) {
-    D += s.dim;
-    Deff += double(s.dim) * (s.twoS + 1);
-  }
-  in.r_d = D > 0 ? Deff / D : 1.0;
-  in.flops_u1_equiv = in.flops_su2 * in.r_d;
   {
-    // the same U(1) counting with the tasks of all shards (a shard's own count
-    // would need the expansion of its own terms only; counted on the full table)
-    in.flops_u1_counted = u1_counted_flops(env->table, S->left, S->right, S->N, S->twoS);
-    in.r_cc = in.flops_su2 > 0 ? in.flops_u1_counted / in.flops_su2 : 0.0;
-  }
-  in.env_bytes = 8.0 * double(env->L.arena_size + env->R.arena_size);
-  if (ctx->device >= 0) {
-    int rc = set_device(ctx);
-    for (int side = 0; side < 2 && !rc; ++side) {
-      SideOps& so = side == 0 ? env->L : env->R;
-      double** dst = side == 0 ? &env->dL : &env->dR;
-      if (so.dev_ready) {  // filled on the device by the builder
-        *dst = so.dev_ready;
-        so.dev_ready = nullptr;
-      } else if (so.host_values) {
-        rc = upload(ctx, dst, so.arena);
-      } else {
-        rc = dev_alloc(ctx, dst, size_t(std::max<int64_t>(so.arena_size, 2)));
-        if (!rc) {
-          const int ce = generate_side(so, *dst, ctx->stream);
-          if (ce) rc = fail(ctx, SU2_ECUDA, std::string("operator generation: ") + cudaGetErrorString(cudaError_t(ce)));
-        }
-      }
-    }
-    if (!rc) rc = dev_alloc(ctx, &env->dT, size_t(std::max<int64_t>(env->t_elems, 2)));
-    if (!rc) rc = upload(ctx, &env->dk1, env->k1);
-    if (!rc) rc = upload(ctx, &env->dk2, env->k2);
-    if (!rc) rc = upload(ctx, &env->dk2t, env->k2t);
-    if (!rc) rc = upload(ctx, &env->ddj, env->dj);
-    if (!rc) rc = upload(ctx, &env->ddt, env->dt);
-    if (!rc && opts && (opts->prepare_split || opts->autotune)) {
-      std::string err;
-      if (opts->autotune) rc = split_autotune(env, opts->split_tol > 0 ? opts->split_tol : 3e-11, err);
-      else rc = split_prepare(env, opts->n_slices > 0 ? opts->n_slices : 5, err);
-      if (rc) fail(ctx, rc, err);
-    }
-    if (rc) {
-      env_free_device(env);
-      delete env;
-      return rc;
-    }
+    const int rcf = finish_env(ctx, env, S, opts);
+    if (rcf) return rcf;
   }
   *out = env;
   return SU2_OK;
@@ -1030,6 +1046,160 @@ int su2_davidson_destroy(su2_dav* d) {
   if (!d) return SU2_EINVAL;
   dav_free(d);
   delete d;
+  return SU2_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ two-site sweep
+struct su2_sweep {
+  su2_ctx* ctx = nullptr;
+  int device = -1;
+  su2::SweepBlocks* w = nullptr;
+  int L = 0, N = 0;
+  su2_sweep_opts o{};
+  int pos = 0, dir = 1;  // next window and direction
+  int64_t steps = 0;
+};
+
+extern "C" {
+
+int su2_sweep_create(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond_chain* right_chain, int32_t N,
+                     const su2_sweep_opts* opts, su2_sweep** out) {
+  if (!ctx || !H || !right_chain || !opts || !out) return fail(ctx, SU2_EINVAL, "null argument");
+  *out = nullptr;
+  if (ctx->device < 0) return fail(ctx, SU2_EINVAL, "the sweep needs a device context");
+  if (H->model != SU2_MODEL_AB_INITIO || !H->h || !H->eri) return fail(ctx, SU2_EINVAL, "the sweep needs the ab initio model");
+  if (opts->D < 1 || N < 0) return fail(ctx, SU2_EINVAL, "D must be >= 1");
+  if (opts->prec != SU2_FP64 && opts->prec != SU2_SPLIT_BF16) return fail(ctx, SU2_EINVAL, "unknown precision");
+  std::vector<std::vector<Sector>> rch;
+  if (right_chain->n_bonds < 1 || !right_chain->bond_offset || !right_chain->sectors)
+    return fail(ctx, SU2_EINVAL, "bad bond chain");
+  for (int k = 0; k < right_chain->n_bonds; ++k) {
+    std::vector<Sector> v;
+    for (int i = right_chain->bond_offset[k]; i < right_chain->bond_offset[k + 1]; ++i)
+      v.push_back(Sector{right_chain->sectors[i].N, right_chain->sectors[i].twoS, right_chain->sectors[i].dim});
+    rch.push_back(v);
+  }
+  int rc = set_device(ctx);
+  if (rc) return rc;
+  su2_sweep* sw = new (std::nothrow) su2_sweep();
+  if (!sw) return fail(ctx, SU2_ENOMEM, "host allocation");
+  sw->ctx = ctx;
+  sw->device = ctx->device;
+  sw->L = H->n_left + 2 + H->n_right;
+  sw->N = N;
+  sw->o = *opts;
+  if (sw->o.tol <= 0) sw->o.tol = 1e-8;
+  if (sw->o.max_iter <= 0) sw->o.max_iter = 400;
+  if (sw->o.n_slices <= 0) sw->o.n_slices = 5;
+  std::string err;
+  sw->w = sweep_init(*H, rch, ctx->device, ctx->stream, 0, err);
+  if (!sw->w) {
+    delete sw;
+    return fail(ctx, SU2_EINVAL, err);
+  }
+  *out = sw;
+  return SU2_OK;
+}
+
+int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies, double* discarded) {
+  if (!ctx || !sw || sw->ctx != ctx || n_steps < 0) return fail(ctx, SU2_EINVAL, "null argument");
+  int rc = set_device(ctx);
+  if (rc) return rc;
+  const int L = sw->L;
+  for (int k = 0; k < n_steps; ++k) {
+    const int i = sw->pos;
+    su2_sectors S;
+    S.site_kind = SU2_SITE_ORBITAL;
+    S.N = sw->N;
+    S.twoS = 0;
+    su2_env* env = new (std::nothrow) su2_env();
+    if (!env) return fail(ctx, SU2_ENOMEM, "host allocation");
+    env->ctx = ctx;
+    env->device = ctx->device;
+    std::string err = sweep_env(sw->w, i, env->table, env->L, env->R, S.left, S.right);
+    if (err.empty()) build_blocks(S.left, S.right, SU2_SITE_ORBITAL, sw->N, 0, S.blocks, S.psi_len);
+    if (err.empty() && S.psi_len == 0) err = "no two-site state with the target particle number";
+    if (err.empty()) {
+      env->psi_len = S.psi_len;
+      env->blocks = S.blocks;
+      env->lsec = S.left;
+      env->rsec = S.right;
+      err = build_tasks(env->table, S.left, S.right, S.blocks, 0, env->L, env->R, env->tasks);
+    }
+    if (!err.empty()) {
+      cudaFree(env->L.dev_ready);
+      cudaFree(env->R.dev_ready);
+      delete env;
+      return fail(ctx, SU2_EINVAL, err);
+    }
+    su2_env_opts eo{};
+    eo.prepare_split = sw->o.prec == SU2_SPLIT_BF16;
+    eo.n_slices = sw->o.n_slices;
+    rc = finish_env(ctx, env, &S, &eo);
+    if (rc) return rc;
+    // Davidson from a seeded start vector
+    const int64_t n = S.psi_len;
+    std::vector<double> h(static_cast<size_t>(n));
+    const uint64_t key = block_key(sw->o.guess_seed, 9, uint64_t(sw->steps), 0, 0);
+    for (int64_t x = 0; x < n; ++x) h[size_t(x)] = uniform_elem(key, uint64_t(x));
+    double* d0 = nullptr;
+    double* dx = nullptr;
+    rc = dev_alloc(ctx, &d0, size_t(n));
+    if (!rc) rc = dev_alloc(ctx, &dx, size_t(n));
+    if (!rc && cudaMemcpy(d0, h.data(), size_t(n) * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = fail(ctx, SU2_ECUDA, "upload");
+    su2_dav* dav = nullptr;
+    double theta = 0.0, res = 0.0;
+    int32_t its = 0;
+    if (!rc) {
+      su2_dav_opts dop{sw->o.tol, 24, 2, sw->o.max_iter, sw->o.prec, 0};
+      rc = su2_davidson_create(ctx, env, d0, &dop, &dav);
+    }
+    if (!rc) {
+      rc = su2_davidson_solve(ctx, dav, &theta, &res, &its);
+      if (rc == SU2_ENOTCONV) rc = SU2_OK;  // the energy of the last iterate is reported
+    }
+    if (!rc) rc = su2_davidson_vector(ctx, dav, dx);
+    if (!rc && cudaMemcpy(h.data(), dx, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = fail(ctx, SU2_ECUDA, "download");
+    if (dav) su2_davidson_destroy(dav);
+    cudaFree(d0);
+    cudaFree(dx);
+    env_free_device(env);
+    delete env;
+    if (rc) return rc;
+    if (energies) energies[k] = theta;
+    // truncate and grow the block on the side the sweep moves to
+    double w = 0.0;
+    const bool grow = sw->dir > 0 ? i < L - 2 : i > 0;
+    if (grow) {
+      std::vector<Sector> cur;
+      std::vector<std::vector<double>> Q;
+      err = sweep_split(S.blocks, h.data(), S.left, S.right, sw->N, sw->o.D, sw->dir > 0, cur, Q, &w);
+      if (err.empty()) err = sweep_grow(sw->w, i, sw->dir > 0, cur, Q);
+      if (!err.empty()) return fail(ctx, SU2_EINVAL, err);
+    }
+    if (discarded) discarded[k] = w;
+    sw->steps += 1;
+    // next window: turn at the ends
+    if (sw->dir > 0) {
+      if (i == L - 2) sw->dir = -1;
+      else sw->pos = i + 1;
+    } else {
+      if (i == 0) sw->dir = 1;
+      else sw->pos = i - 1;
+    }
+  }
+  return SU2_OK;
+}
+
+int su2_sweep_destroy(su2_sweep* sw) {
+  if (!sw) return SU2_EINVAL;
+  if (sw->device >= 0) cudaSetDevice(sw->device);
+  sweep_free(sw->w);
+  delete sw;
   return SU2_OK;
 }
 

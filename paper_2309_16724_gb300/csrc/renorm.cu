@@ -71,6 +71,17 @@ class DeviceBackend : public RenormBackend {
   }
 
   std::string run(const RStep& st) override {
+    double* out = nullptr;
+    std::string err = run_keep(st, cur_, &out);
+    if (!err.empty()) return err;
+    cudaFree(cur_);
+    cur_ = out;
+    size_ = st.dst_size;
+    return "";
+  }
+
+  std::string run_keep(const RStep& st, const double* old, double** out) override {
+    *out = nullptr;
     std::string err;
     double *src = nullptr, *dst = nullptr, *q = nullptr, *T = nullptr;
     RIdent* did = nullptr;
@@ -87,7 +98,7 @@ class DeviceBackend : public RenormBackend {
     (void)cudaGetLastError();
     const int64_t srcn = std::max<int64_t>(st.src_size, 1), dstn = std::max<int64_t>(st.dst_size, 1);
     if (ck(cudaMalloc(&src, size_t(srcn) * sizeof(double)), "source arena") && st.old_size > 0)
-      ck(cudaMemcpyAsync(src, cur_, size_t(st.old_size) * sizeof(double), cudaMemcpyDeviceToDevice, s_), "copy");
+      ck(cudaMemcpyAsync(src, old, size_t(st.old_size) * sizeof(double), cudaMemcpyDeviceToDevice, s_), "copy");
     if (err.empty() && st.src_size > st.old_size)
       ck(cudaMemsetAsync(src + st.old_size, 0, size_t(st.src_size - st.old_size) * sizeof(double), s_), "memset");
     if (err.empty() && !st.idents.empty() && ck(upload(&did, st.idents), "identities"))
@@ -96,11 +107,6 @@ class DeviceBackend : public RenormBackend {
     if (err.empty() && !tp.empty() && ck(upload(&dtp, tp), "temps") && ck(upload(&dtt, st.temp_terms), "temp terms"))
       group_kernel<<<unsigned(tp.size()), 256, 0, s_>>>(dtp, dtt, src, src);
     if (err.empty()) ck(cudaStreamSynchronize(s_), "temporaries");
-    if (err.empty()) {
-      cudaFree(cur_);
-      cur_ = nullptr;
-      size_ = 0;
-    }
     if (err.empty()) ck(upload(&q, st.q), "Q arena");
     if (err.empty() && ck(cudaMalloc(&dst, size_t(dstn) * sizeof(double)), "destination arena"))
       ck(cudaMemsetAsync(dst, 0, size_t(dstn) * sizeof(double), s_), "memset");
@@ -195,8 +201,7 @@ class DeviceBackend : public RenormBackend {
       cudaFree(dst);
       return err;
     }
-    cur_ = dst;
-    size_ = st.dst_size;
+    *out = dst;
     return "";
   }
 

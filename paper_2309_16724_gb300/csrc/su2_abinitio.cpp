@@ -35,6 +35,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "su2_internal.h"
 #include "su2_renorm.h"
 
@@ -404,18 +406,23 @@ class Builder {
   // the operators of one block after its last step; `left` selects the side
   struct Side {
     Layout lay;
-    std::unique_ptr<RenormBackend> be;
+    std::unique_ptr<RenormBackend> own;
+    RenormBackend* be = nullptr;
     std::vector<int> orbs;
+    const double* arena = nullptr;  // keep mode: the block's device arena (not consumed)
+    int64_t arena_size = 0;
   };
 
   std::string grow(bool left, const std::vector<std::vector<Sector>>& chain, Side& out) {
-    out.be.reset(device_ >= 0 ? make_device_backend(device_, stream_, budget_) : make_host_backend());
+    out.own.reset(device_ >= 0 ? make_device_backend(device_, stream_, budget_) : make_host_backend());
+    out.be = out.own.get();
     Layout old;
     old.sec = chain[0];
     std::vector<int> orbs;
     for (size_t step = 1; step < chain.size(); ++step) {
       const int s = left ? int(step) - 1 : L_ - int(step);
-      std::string err = step_block(left, int(step), s, chain[step - 1], chain[step], orbs, old, *out.be);
+      std::string err =
+          step_block(left, int(step), s, chain[step - 1], chain[step], nullptr, orbs, old, *out.be, nullptr, 0, nullptr);
       if (!err.empty()) return err;
       if (left) orbs.push_back(s);
       else orbs.insert(orbs.begin(), s);
@@ -425,15 +432,19 @@ class Builder {
     return "";
   }
 
-  std::string assemble(const std::vector<std::vector<Sector>>& lchain, const std::vector<std::vector<Sector>>& rchain,
-                       OpTable& table, SideOps& Lops, SideOps& Rops, double* flops);
+  std::string assemble(OpTable& table, SideOps& Lops, SideOps& Rops, double* flops);
 
- private:
   // ---------------------------------------------------------------- one step
+  // Grows a block by orbital s: the new bond `cur` and the MPS tensor Qin
+  // (per new sector, its stacked rows x dim, column-major), or the seeded
+  // tensor of `step` when Qin is null.  Keep mode (keep_out non-null): the
+  // old arena keep_old of keep_size doubles is read and kept, the new arena
+  // returned; otherwise the backend's current arena is replaced.
   std::string step_block(bool left, int step, int s, const std::vector<Sector>& prev, const std::vector<Sector>& cur,
-                         const std::vector<int>& orbs, Layout& old, RenormBackend& be) {
+                         const std::vector<std::vector<double>>* Qin, const std::vector<int>& orbs, Layout& old,
+                         RenormBackend& be, const double* keep_old, int64_t keep_size, double** keep_out) {
     RStep st;
-    st.old_size = be.size();
+    st.old_size = keep_out ? keep_size : be.size();
     old_ = &old;
     orbs_ = &orbs;
     left_ = left;
@@ -466,10 +477,15 @@ class Builder {
       const int d = cur[qo].dim;
       if (r0 < d) return "bond dimension exceeds the states available from the previous bond";
       std::vector<double> G(size_t(r0) * d);
-      const uint64_t key = block_key(H_.seed, side, uint64_t(step), uint64_t(qo), 0);
-      for (int c = 0; c < d; ++c)
-        for (int r = 0; r < r0; ++r) G[size_t(r) + size_t(c) * r0] = uniform_elem(key, uint64_t(r) + uint64_t(c) * r0);
-      orthonormalize(G, r0, d);
+      if (Qin) {
+        if ((*Qin)[size_t(qo)].size() != G.size()) return "MPS tensor does not match the stacked rows of its sector";
+        G = (*Qin)[size_t(qo)];
+      } else {
+        const uint64_t key = block_key(H_.seed, side, uint64_t(step), uint64_t(qo), 0);
+        for (int c = 0; c < d; ++c)
+          for (int r = 0; r < r0; ++r) G[size_t(r) + size_t(c) * r0] = uniform_elem(key, uint64_t(r) + uint64_t(c) * r0);
+        orthonormalize(G, r0, d);
+      }
       qoff[qo] = int64_t(st.q.size());
       // Q^T (d x r0), column-major
       st.q.resize(st.q.size() + size_t(r0) * d);
@@ -612,11 +628,13 @@ class Builder {
         }
       }
     }
-    std::string err = be.run(st);
+    std::string err = keep_out ? be.run_keep(st, keep_old, keep_out) : be.run(st);
     if (!err.empty()) return err;
     old = nl;
     return "";
   }
+
+ private:
 
   Src ident(double c) {
     Src x;
@@ -770,7 +788,7 @@ class Builder {
     return cs;
   }
 
-  const su2_hamiltonian& H_;
+  su2_hamiltonian H_;
   int L_;
   Strings strings_;
   Trees tr_;
@@ -861,15 +879,13 @@ void init_final(Final& f, const std::vector<Sector>& sec, int64_t old_size) {
   f.ids["I"] = 0;
 }
 
-std::string Builder::assemble(const std::vector<std::vector<Sector>>& lchain,
-                              const std::vector<std::vector<Sector>>& rchain, OpTable& table, SideOps& Lops,
-                              SideOps& Rops, double* flops) {
-  const int nL = H_.n_left, p = nL, q = nL + 1;
+std::string Builder::assemble(OpTable& table, SideOps& Lops, SideOps& Rops, double* flops) {
+  const int nL = int(lside.orbs.size()), p = nL, q = nL + 1;
   const Layout& LL = lside.lay;
   const Layout& RL = rside.lay;
   Final fl, fr;
-  init_final(fl, lchain.back(), lside.be->size());
-  init_final(fr, rchain.back(), rside.be->size());
+  init_final(fl, LL.sec, lside.arena ? lside.arena_size : lside.be->size());
+  init_final(fr, RL.sec, rside.arena ? rside.arena_size : rside.be->size());
   // the block Hamiltonians first (left / right operator 1)
   auto must = [](int i) {
     if (i < 0) throw std::runtime_error("missing block operator");
@@ -1143,13 +1159,14 @@ std::string Builder::assemble(const std::vector<std::vector<Sector>>& lchain,
     Final& f = side == 0 ? fl : fr;
     Side& sd = side == 0 ? lside : rside;
     RStep st;
-    st.old_size = sd.be->size();
+    st.old_size = sd.arena ? sd.arena_size : sd.be->size();
     st.src_size = f.src_size;
     st.idents = f.idents;
     st.dst_size = f.lay.size;
     st.copies = f.groups;
     st.copy_terms = f.terms;
-    std::string err = sd.be->run(st);
+    double* kept = nullptr;
+    std::string err = sd.arena ? sd.be->run_keep(st, sd.arena, &kept) : sd.be->run(st);
     if (!err.empty()) return err;
     SideOps& so = side == 0 ? Lops : Rops;
     so = SideOps();
@@ -1164,7 +1181,7 @@ std::string Builder::assemble(const std::vector<std::vector<Sector>>& lchain,
     so.arena_size = f.lay.size;
     if (device_ >= 0) {
       so.host_values = false;
-      so.dev_ready = sd.be->take_device();
+      so.dev_ready = sd.arena ? kept : sd.be->take_device();
     } else {
       so.host_values = true;
       so.arena = sd.be->take_host();
@@ -1189,13 +1206,308 @@ std::string build_abinitio(const su2_hamiltonian& H, const std::vector<std::vect
     Builder b(H, device, stream, t_budget_bytes);
     std::string err = b.grow(true, lchain, b.lside);
     if (err.empty()) err = b.grow(false, rchain, b.rside);
-    if (err.empty()) err = b.assemble(lchain, rchain, table, L, R, renorm_flops);
+    if (err.empty()) err = b.assemble(table, L, R, renorm_flops);
     return err;
   } catch (const std::bad_alloc&) {
     return "host allocation failed";
   } catch (const std::exception& ex) {
     return ex.what();
   }
+}
+
+// ------------------------------------------------------------------ two-site sweep
+// Blocks of every length kept on the device during a sweep: left block i
+// holds orbitals 0 .. i-1, right block k the last k orbitals.
+struct SweepBlocks {
+  struct Rec {
+    Layout lay;
+    std::vector<int> orbs;
+    double* arena = nullptr;
+    int64_t size = 0;
+  };
+  std::unique_ptr<Builder> b;
+  std::unique_ptr<RenormBackend> be;
+  std::vector<Rec> Lb, Rb;
+  int L = 0, device = 0;
+  ~SweepBlocks() {
+    if (device >= 0) cudaSetDevice(device);
+    for (auto& r : Lb) cudaFree(r.arena);
+    for (auto& r : Rb) cudaFree(r.arena);
+  }
+};
+
+namespace {
+
+// left singular vectors and values of M (r x c, column-major), descending,
+// by one-sided Jacobi rotations (Hestenes) on the narrower side
+void svd_left(int r, int c, const std::vector<double>& M, std::vector<double>& U, std::vector<double>& sv) {
+  const bool tr = c > r;               // rotate the columns of M^T: then U is the accumulated rotation
+  const int rows = tr ? c : r, cols = tr ? r : c;
+  std::vector<double> B(size_t(rows) * cols), V;
+  for (int j = 0; j < cols; ++j)
+    for (int i = 0; i < rows; ++i) B[size_t(i) + size_t(j) * rows] = tr ? M[size_t(j) + size_t(i) * r] : M[size_t(i) + size_t(j) * r];
+  if (tr) {
+    V.assign(size_t(cols) * cols, 0.0);
+    for (int i = 0; i < cols; ++i) V[size_t(i) * (cols + 1)] = 1.0;
+  }
+  for (int sweep = 0; sweep < 80; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < cols; ++p)
+      for (int q = p + 1; q < cols; ++q) {
+        double a = 0, b = 0, g = 0;
+        const double* bp = &B[size_t(p) * rows];
+        const double* bq = &B[size_t(q) * rows];
+        for (int i = 0; i < rows; ++i) {
+          a += bp[i] * bp[i];
+          b += bq[i] * bq[i];
+          g += bp[i] * bq[i];
+        }
+        if (g == 0.0 || std::abs(g) <= 1e-15 * std::sqrt(a * b)) continue;
+        off = std::max(off, std::abs(g) / std::sqrt(a * b));
+        const double zeta = (b - a) / (2.0 * g);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::abs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = cs * t;
+        double* xp = &B[size_t(p) * rows];
+        double* xq = &B[size_t(q) * rows];
+        for (int i = 0; i < rows; ++i) {
+          const double u = xp[i], w = xq[i];
+          xp[i] = cs * u - sn * w;
+          xq[i] = sn * u + cs * w;
+        }
+        if (tr) {
+          double* vp = &V[size_t(p) * cols];
+          double* vq = &V[size_t(q) * cols];
+          for (int i = 0; i < cols; ++i) {
+            const double u = vp[i], w = vq[i];
+            vp[i] = cs * u - sn * w;
+            vq[i] = sn * u + cs * w;
+          }
+        }
+      }
+    if (off < 1e-15) break;
+  }
+  std::vector<double> nrm(static_cast<size_t>(cols));
+  for (int j = 0; j < cols; ++j) {
+    double x = 0;
+    for (int i = 0; i < rows; ++i) x += B[size_t(i) + size_t(j) * rows] * B[size_t(i) + size_t(j) * rows];
+    nrm[size_t(j)] = std::sqrt(x);
+  }
+  std::vector<int> ord(static_cast<size_t>(cols));
+  for (int j = 0; j < cols; ++j) ord[size_t(j)] = j;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return nrm[size_t(a)] > nrm[size_t(b)]; });
+  const int k = std::min(r, c);
+  U.assign(size_t(r) * k, 0.0);
+  sv.assign(size_t(k), 0.0);
+  for (int x = 0; x < k; ++x) {
+    const int j = ord[size_t(x)];
+    sv[size_t(x)] = nrm[size_t(j)];
+    for (int i = 0; i < r; ++i)
+      U[size_t(i) + size_t(x) * r] = tr ? V[size_t(i) + size_t(j) * cols]
+                                        : (nrm[size_t(j)] > 0 ? B[size_t(i) + size_t(j) * rows] / nrm[size_t(j)] : 0.0);
+  }
+}
+
+}  // namespace
+
+SweepBlocks* sweep_init(const su2_hamiltonian& H, const std::vector<std::vector<Sector>>& rchain, int device,
+                        void* stream, int64_t budget, std::string& err) {
+  const int L = H.n_left + 2 + H.n_right;
+  if (int(rchain.size()) != L - 1) {
+    err = "the initial right chain must hold the bonds of 0 .. L-2 orbitals";
+    return nullptr;
+  }
+  auto* w = new SweepBlocks();
+  w->L = L;
+  w->device = device;
+  try {
+    w->b.reset(new Builder(H, device, stream, budget));
+    w->be.reset(make_device_backend(device, stream, budget));
+    w->Rb.resize(size_t(L - 1));
+    w->Lb.resize(size_t(L - 1));
+    w->Rb[0].lay.sec = rchain[0];
+    w->Lb[0].lay.sec = std::vector<Sector>{Sector{0, 0, 1}};
+    for (int k = 1; k < L - 1; ++k) {
+      SweepBlocks::Rec& o = w->Rb[size_t(k - 1)];
+      Layout lay = o.lay;
+      double* out = nullptr;
+      err = w->b->step_block(false, k, L - k, rchain[size_t(k - 1)], rchain[size_t(k)], nullptr, o.orbs, lay, *w->be,
+                             o.arena, o.size, &out);
+      if (!err.empty()) break;
+      SweepBlocks::Rec& r = w->Rb[size_t(k)];
+      r.lay = lay;
+      r.orbs = o.orbs;
+      r.orbs.insert(r.orbs.begin(), L - k);
+      r.arena = out;
+      r.size = lay.size;
+    }
+  } catch (const std::exception& ex) {
+    err = ex.what();
+  }
+  if (!err.empty()) {
+    delete w;
+    return nullptr;
+  }
+  return w;
+}
+
+void sweep_free(SweepBlocks* w) { delete w; }
+
+std::string sweep_env(SweepBlocks* w, int i, OpTable& table, SideOps& Lops, SideOps& Rops, std::vector<Sector>& lsec,
+                      std::vector<Sector>& rsec) {
+  if (i < 0 || i > w->L - 2) return "window outside the chain";
+  SweepBlocks::Rec& l = w->Lb[size_t(i)];
+  SweepBlocks::Rec& r = w->Rb[size_t(w->L - 2 - i)];
+  if (l.lay.sec.empty() || r.lay.sec.empty()) return "a block of the window has not been built";
+  Builder& b = *w->b;
+  b.lside.lay = l.lay;
+  b.lside.orbs = l.orbs;
+  b.lside.be = w->be.get();
+  b.lside.arena = l.arena;
+  b.lside.arena_size = l.size;
+  b.rside.lay = r.lay;
+  b.rside.orbs = r.orbs;
+  b.rside.be = w->be.get();
+  b.rside.arena = r.arena;
+  b.rside.arena_size = r.size;
+  try {
+    std::string err = b.assemble(table, Lops, Rops, nullptr);
+    if (!err.empty()) return err;
+  } catch (const std::exception& ex) {
+    return ex.what();
+  }
+  lsec = l.lay.sec;
+  rsec = r.lay.sec;
+  return "";
+}
+
+std::string sweep_split(const std::vector<Block>& blocks, const double* psi, const std::vector<Sector>& lsec,
+                        const std::vector<Sector>& rsec, int N, int D, bool left, std::vector<Sector>& new_sec,
+                        std::vector<std::vector<double>>& Q, double* discarded) {
+  std::vector<int> sN, sS;
+  site_states(SU2_SITE_ORBITAL, sN, sS);
+  struct Stk {
+    int q, s, r0, d;
+  };
+  auto stacks = [&](const std::vector<Sector>& sec, int Nq, int j, int& tot) {
+    std::vector<Stk> v;
+    tot = 0;
+    for (int qp = 0; qp < int(sec.size()); ++qp)
+      for (int si = 0; si < 3; ++si)
+        if (sec[qp].N + sN[si] == Nq && triangle(sec[qp].twoS, sS[si], j)) {
+          v.push_back(Stk{qp, si, tot, sec[qp].dim});
+          tot += sec[qp].dim;
+        }
+    return v;
+  };
+  std::map<std::tuple<int, int, int, int>, int> bidx;  // (a, s1, s2, b) -> block (S = 0: jL1 = j2R)
+  std::map<std::pair<int, int>, int> keys;
+  for (int i = 0; i < int(blocks.size()); ++i) {
+    const Block& B = blocks[i];
+    if (B.jL1 != B.j2R) return "the sweep needs a total-spin-0 target";
+    bidx[{B.a, B.s1, B.s2, B.b}] = i;
+    keys[{lsec[B.a].N + sN[B.s1], B.jL1}] = 1;
+  }
+  struct Sec {
+    int Nq, j;
+    std::vector<double> U, sv;
+    int rows;
+  };
+  std::vector<Sec> all;
+  double total = 0.0;
+  for (const auto& kv : keys) {
+    const int Nq = kv.first.first, j = kv.first.second;
+    int nr = 0, nc = 0;
+    const auto ls = stacks(lsec, Nq, j, nr);
+    const auto rs = stacks(rsec, N - Nq, j, nc);
+    std::vector<double> M(size_t(nr) * nc, 0.0);
+    for (const Stk& x : ls)
+      for (const Stk& y : rs) {
+        auto it = bidx.find({x.q, x.s, y.s, y.q});
+        if (it == bidx.end()) continue;
+        const Block& B = blocks[it->second];
+        for (int c = 0; c < B.cols; ++c)
+          for (int r = 0; r < B.rows; ++r)
+            M[size_t(x.r0 + r) + size_t(y.r0 + c) * nr] = psi[B.offset + r + int64_t(c) * B.rows];
+      }
+    Sec sc;
+    sc.Nq = Nq;
+    sc.j = j;
+    if (left) {
+      svd_left(nr, nc, M, sc.U, sc.sv);
+      sc.rows = nr;
+    } else {
+      std::vector<double> Mt(M.size());
+      for (int c = 0; c < nc; ++c)
+        for (int r = 0; r < nr; ++r) Mt[size_t(c) + size_t(r) * nc] = M[size_t(r) + size_t(c) * nr];
+      svd_left(nc, nr, Mt, sc.U, sc.sv);
+      sc.rows = nc;
+    }
+    for (double x : sc.sv) total += x * x;
+    all.push_back(std::move(sc));
+  }
+  // keep the D largest sigma^2; ties to the lower (N, 2S) sector, then the lower index
+  struct Cand {
+    double w;
+    int N, j, sec, idx;
+  };
+  std::vector<Cand> cand;
+  for (int q = 0; q < int(all.size()); ++q) {
+    const int Nb = left ? all[q].Nq : N - all[q].Nq;
+    for (int x = 0; x < int(all[q].sv.size()); ++x) cand.push_back(Cand{all[q].sv[x] * all[q].sv[x], Nb, all[q].j, q, x});
+  }
+  std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
+    if (a.w != b.w) return a.w > b.w;
+    if (a.N != b.N) return a.N < b.N;
+    if (a.j != b.j) return a.j < b.j;
+    return a.idx < b.idx;
+  });
+  std::map<int, int> nkeep;
+  double kept = 0.0;
+  for (int x = 0; x < int(cand.size()) && x < D; ++x) {
+    nkeep[cand[x].sec] += 1;
+    kept += cand[x].w;
+  }
+  std::vector<std::pair<std::pair<int, int>, int>> order;  // ((N, 2S) of the new bond, sector)
+  for (const auto& kv : nkeep) {
+    const Sec& sc = all[size_t(kv.first)];
+    order.push_back({{left ? sc.Nq : N - sc.Nq, sc.j}, kv.first});
+  }
+  std::sort(order.begin(), order.end());
+  new_sec.clear();
+  Q.clear();
+  for (const auto& o : order) {
+    const Sec& sc = all[size_t(o.second)];
+    const int d = nkeep[o.second];  // the d largest of this sector (descending order)
+    new_sec.push_back(Sector{o.first.first, o.first.second, d});
+    Q.emplace_back(sc.U.begin(), sc.U.begin() + size_t(sc.rows) * d);
+  }
+  if (discarded) *discarded = total - kept;
+  return new_sec.empty() ? "the wavefunction is zero" : "";
+}
+
+std::string sweep_grow(SweepBlocks* w, int i, bool left, const std::vector<Sector>& cur,
+                       const std::vector<std::vector<double>>& Q) {
+  const int L = w->L;
+  SweepBlocks::Rec& o = left ? w->Lb[size_t(i)] : w->Rb[size_t(L - 2 - i)];
+  SweepBlocks::Rec& n = left ? w->Lb[size_t(i + 1)] : w->Rb[size_t(L - 1 - i)];
+  const int s = left ? i : i + 1;
+  Layout lay = o.lay;
+  double* out = nullptr;
+  std::string err;
+  try {
+    err = w->b->step_block(left, 0, s, o.lay.sec, cur, &Q, o.orbs, lay, *w->be, o.arena, o.size, &out);
+  } catch (const std::exception& ex) {
+    err = ex.what();
+  }
+  if (!err.empty()) return err;
+  cudaFree(n.arena);
+  n.lay = lay;
+  n.orbs = o.orbs;
+  if (left) n.orbs.push_back(s);
+  else n.orbs.insert(n.orbs.begin(), s);
+  n.arena = out;
+  n.size = lay.size;
+  return "";
 }
 
 }  // namespace su2

@@ -112,6 +112,22 @@ std::string build_abinitio(const su2_hamiltonian& H, const std::vector<std::vect
 double u1_counted_flops(const OpTable& t, const std::vector<Sector>& left, const std::vector<Sector>& right, int N,
                         int twoS);
 
+// two-site sweep of the ab initio model (device contexts): blocks of every
+// length kept on the device; the environment at window i (sites i, i+1);
+// the per-sector SVD of an S = 0 two-site wavefunction with truncation to D
+// multiplets; the block grown by one orbital with the kept singular vectors
+struct SweepBlocks;
+SweepBlocks* sweep_init(const su2_hamiltonian& H, const std::vector<std::vector<Sector>>& rchain, int device,
+                        void* stream, int64_t budget, std::string& err);
+void sweep_free(SweepBlocks* w);
+std::string sweep_env(SweepBlocks* w, int i, OpTable& table, SideOps& L, SideOps& R, std::vector<Sector>& lsec,
+                      std::vector<Sector>& rsec);
+std::string sweep_split(const std::vector<Block>& blocks, const double* psi, const std::vector<Sector>& lsec,
+                        const std::vector<Sector>& rsec, int N, int D, bool left, std::vector<Sector>& new_sec,
+                        std::vector<std::vector<double>>& Q, double* discarded);
+std::string sweep_grow(SweepBlocks* w, int i, bool left, const std::vector<Sector>& cur,
+                       const std::vector<std::vector<double>>& Q);
+
 // counter-based generator (SplitMix64, Steele/Lea/Flood 2014)
 uint64_t splitmix(uint64_t x);
 uint64_t block_key(uint64_t seed, uint64_t side, uint64_t op, uint64_t qo, uint64_t qi);

@@ -54,6 +54,14 @@ class RenormBackend {
   virtual ~RenormBackend() {}
   // executes a step: the destination arena becomes the current arena
   virtual std::string run(const RStep& st) = 0;
+  // executes a step on an explicit old arena (device), which is kept; the
+  // destination arena is returned (the caller owns it; device backend only)
+  virtual std::string run_keep(const RStep& st, const double* old, double** out) {
+    (void)st;
+    (void)old;
+    *out = nullptr;
+    return "renormalisation on an explicit arena needs a device context";
+  }
   virtual int64_t size() const = 0;
   // hands the current arena over (host vector or device pointer)
   virtual std::vector<double> take_host() { return {}; }

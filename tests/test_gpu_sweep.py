@@ -1,0 +1,56 @@
+"""The library's two-site sweep on the GPU (ab initio model, S = 0).
+
+* Bonds that keep every multiplet: every window's energy is the full-CI
+  ground-state energy (native FP64 and split paths).
+* Truncated bonds: the energies of every window equal the oracle's sweep
+  (its own SVD, truncation and renormalisation) on the same seeded MPS.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fci, sweep as osweep
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_16724_gb300 as P
+    torch.cuda.init()
+    return P.Context(0, stream=torch.cuda.current_stream())
+
+
+def lib_sweep(ctx, cfg, D, n_steps, prec):
+    import paper_2309_16724_gb300 as P
+    h, eri = synth.integrals(cfg.L, cfg.seed)
+    chain = synth.bond_sector_chain(cfg, cfg.L - 2)
+    sw = P.Sweep(ctx, h, eri, chain, cfg.N, D, prec=prec, tol=1e-10, seed=cfg.seed)
+    e, w = sw.run(n_steps)
+    sw.close()
+    assert ctx.status() == 0
+    return e, w
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_exact_sweep_equals_full_ci(ctx, prec):
+    cfg = synth.Config("sw6", synth.SPATIAL_ORBITAL, 6, 6, 0, 400, 1002)
+    e, w = lib_sweep(ctx, cfg, 400, 2 * (cfg.L - 1), prec)
+    h, eri = synth.integrals(6, 1002)
+    e0 = fci.spin_levels(h, eri, 6, 0)[0]
+    assert np.abs(e - e0).max() < 1e-9
+    assert np.all(np.abs(w) < 1e-20)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-8)])
+def test_truncated_sweep_matches_oracle(ctx, prec, tol):
+    cfg = synth.Config("sw7", synth.SPATIAL_ORBITAL, 7, 6, 0, 6, 1002)
+    e, w = lib_sweep(ctx, cfg, 6, 2 * (cfg.L - 1), prec)
+    eo, wo = osweep.sweep(cfg, 6, 2, tol=1e-10)
+    assert len(e) == len(eo)
+    assert np.abs(e - eo).max() < tol, (e, eo)
+    wl = w[w > 0]
+    assert np.allclose(np.sort(wl), np.sort(wo[wo > 0]), rtol=1e-6, atol=1e-12)
