@@ -13,6 +13,9 @@ Readings (the paper gives no sweep algorithm):
   in ``env.mps_tensor`` (previous sector outer, site state inner).
 * Truncation keeps the D largest sigma^2 (one per multiplet) over all
   sectors; ties go to the lower (N, 2S) sector, then the lower index.
+  Singular values with sigma^2 <= 1e-24 of the total weight are never kept:
+  their singular vectors are arbitrary (the wavefunction has no weight
+  there), and the bond then holds the Schmidt rank when D exceeds it.
 * Moving right, the left block grows with U (the left singular vectors);
   moving left, the right block grows with V.  Each Davidson starts from a
   seeded Gaussian vector (no wavefunction prediction: slower, equally exact).
@@ -66,13 +69,20 @@ def _bond_matrices(psi, blocks, left, right, site_kind, N):
     return out
 
 
+ZERO_WEIGHT = 1e-24
+
+
 def _truncate(svals, D):
     """Indices kept per sector: the D largest sigma^2, ties to the lower
-    (N, 2S) sector and then the lower index."""
+    (N, 2S) sector and then the lower index; sigma^2 at or below
+    ZERO_WEIGHT times the total weight are never kept (their singular vectors
+    are arbitrary)."""
+    total = sum(float(np.sum(s * s)) for s in svals.values())
     cand = []
     for key, s in svals.items():
         for i, x in enumerate(s):
-            cand.append((-x * x, key, i))
+            if x * x > ZERO_WEIGHT * total:
+                cand.append((-x * x, key, i))
     cand.sort()
     keep = {}
     for (_, key, i) in cand[:D]:

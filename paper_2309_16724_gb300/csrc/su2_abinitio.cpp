@@ -1450,10 +1450,15 @@ std::string sweep_split(const std::vector<Block>& blocks, const double* psi, con
     double w;
     int N, j, sec, idx;
   };
+  // singular values with sigma^2 <= 1e-24 of the total weight are never
+  // kept: their singular vectors are arbitrary
   std::vector<Cand> cand;
   for (int q = 0; q < int(all.size()); ++q) {
     const int Nb = left ? all[q].Nq : N - all[q].Nq;
-    for (int x = 0; x < int(all[q].sv.size()); ++x) cand.push_back(Cand{all[q].sv[x] * all[q].sv[x], Nb, all[q].j, q, x});
+    for (int x = 0; x < int(all[q].sv.size()); ++x) {
+      const double w2 = all[q].sv[x] * all[q].sv[x];
+      if (w2 > 1e-24 * total) cand.push_back(Cand{w2, Nb, all[q].j, q, x});
+    }
   }
   std::stable_sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) {
     if (a.w != b.w) return a.w > b.w;
@@ -1480,6 +1485,7 @@ std::string sweep_split(const std::vector<Block>& blocks, const double* psi, con
     const int d = nkeep[o.second];  // the d largest of this sector (descending order)
     new_sec.push_back(Sector{o.first.first, o.first.second, d});
     Q.emplace_back(sc.U.begin(), sc.U.begin() + size_t(sc.rows) * d);
+    orthonormalize(Q.back(), sc.rows, d);  // removes the rounding of the rotations (the columns are already orthonormal to ~1e-15)
   }
   if (discarded) *discarded = total - kept;
   return new_sec.empty() ? "the wavefunction is zero" : "";
