@@ -89,8 +89,9 @@ typedef struct {
 
 typedef struct {
   int32_t model;      /* su2_model */
-  int32_t n_left;     /* orbitals / sites in the left block  */
-  int32_t n_right;    /* orbitals / sites in the right block */
+  int32_t n_left;     /* orbitals / sites in the left block (>= 1; the ab
+                         initio model also takes an empty block, 0)      */
+  int32_t n_right;    /* orbitals / sites in the right block (likewise)   */
   double J;           /* Heisenberg coupling                 */
   uint64_t seed;      /* seed of the counter-based generator (SplitMix64)
                          for synthetic entries and MPS tensors */

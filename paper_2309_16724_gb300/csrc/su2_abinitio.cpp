@@ -1198,7 +1198,7 @@ std::string build_abinitio(const su2_hamiltonian& H, const std::vector<std::vect
                            const std::vector<std::vector<Sector>>& rchain, int device, void* stream,
                            int64_t t_budget_bytes, OpTable& table, SideOps& L, SideOps& R, double* renorm_flops) {
   if (!H.h || !H.eri) return "the ab initio model needs the integrals h and eri";
-  if (H.n_left < 1 || H.n_right < 1) return "n_left and n_right must be >= 1";
+  if (H.n_left < 0 || H.n_right < 0) return "n_left and n_right must be >= 0";
   if (int(lchain.size()) != H.n_left + 1 || int(rchain.size()) != H.n_right + 1)
     return "the bond chains must have n_left + 1 and n_right + 1 bonds (vacuum first)";
   if (H.n_left + 2 + H.n_right > 1000) return "too many orbitals";
@@ -1399,12 +1399,14 @@ std::string sweep_split(const std::vector<Block>& blocks, const double* psi, con
         }
     return v;
   };
-  std::map<std::tuple<int, int, int, int>, int> bidx;  // (a, s1, s2, b) -> block (S = 0: jL1 = j2R)
+  // (a, s1, s2, b, j) -> block (S = 0: jL1 = j2R = j; one (a, s1) pair may
+  // couple to two values of j)
+  std::map<std::tuple<int, int, int, int, int>, int> bidx;
   std::map<std::pair<int, int>, int> keys;
   for (int i = 0; i < int(blocks.size()); ++i) {
     const Block& B = blocks[i];
     if (B.jL1 != B.j2R) return "the sweep needs a total-spin-0 target";
-    bidx[{B.a, B.s1, B.s2, B.b}] = i;
+    bidx[{B.a, B.s1, B.s2, B.b, B.jL1}] = i;
     keys[{lsec[B.a].N + sN[B.s1], B.jL1}] = 1;
   }
   struct Sec {
@@ -1422,7 +1424,7 @@ std::string sweep_split(const std::vector<Block>& blocks, const double* psi, con
     std::vector<double> M(size_t(nr) * nc, 0.0);
     for (const Stk& x : ls)
       for (const Stk& y : rs) {
-        auto it = bidx.find({x.q, x.s, y.s, y.q});
+        auto it = bidx.find({x.q, x.s, y.s, y.q, j});
         if (it == bidx.end()) continue;
         const Block& B = blocks[it->second];
         for (int c = 0; c < B.cols; ++c)

@@ -110,3 +110,25 @@ def test_ab_initio_argument_errors(hctx):
         P.Environment(hctx, sec, P.SU2_MODEL_AB_INITIO, lch[1:], rch, n_left=cfg.n_left, n_right=cfg.n_right,
                       h=h, eri=eri)
     assert ei.value.code == P._lib.SU2_EINVAL
+
+
+@pytest.mark.parametrize("n_left", [0, 1, 2, 3, 4])
+def test_every_bond_position_equals_full_ci(hctx, n_left):
+    """The window at every position of an L = 6 chain, empty blocks at the
+    ends included: with bonds that keep every multiplet, the lowest
+    eigenvalue of the library's H_eff (built densely from its task table and
+    operator blocks) is the full-CI ground-state energy."""
+    import paper_2309_16724_gb300 as P
+    L, N = 6, 6
+    cfg = synth.Config("ab", synth.SPATIAL_ORBITAL, L, N, 0, 400, 1002)
+    h, eri = synth.integrals(L, 1002)
+    nr = L - 2 - n_left
+    lch, rch = synth.bond_sector_chain(cfg, n_left), synth.bond_sector_chain(cfg, nr)
+    sec = P.Sectors(hctx, lch[-1], rch[-1], cfg.site_kind, N, 0)
+    env = P.Environment(hctx, sec, P.SU2_MODEL_AB_INITIO, lch, rch, n_left=n_left, n_right=nr, seed=1002, h=h, eri=eri)
+    apply = lib_apply(env, sec)
+    n = sec.psi_len
+    H = np.stack([apply(np.eye(n)[i]) for i in range(n)], 1)
+    assert np.abs(H - H.T).max() <= 1e-13
+    assert abs(np.linalg.eigvalsh(H)[0] - fci.spin_levels(h, eri, N, 0)[0]) <= 1e-12
+    env.close()
