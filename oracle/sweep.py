@@ -101,8 +101,8 @@ def isometry(psi, blocks, left, right, site_kind, N, D, side):
         svd[key] = (U, Vt.T)
         svals[key] = s
     keep = _truncate(svals, D)
-    total = sum(float(np.sum(s * s)) for s in svals.values())
-    kept = sum(float(np.sum(svals[k][idx] ** 2)) for k, idx in keep.items())
+    # discarded weight: the sigma^2 not kept, summed directly
+    dropped = sum(float(np.sum(np.delete(s, keep.get(k, [])) ** 2)) for k, s in svals.items())
     new = []
     for (Nq, j), idx in keep.items():
         Nb = Nq if side == "L" else N - Nq
@@ -117,7 +117,7 @@ def isometry(psi, blocks, left, right, site_kind, N, D, side):
             A[qo] = (lrows, U[:, sorted(idx)])
         else:
             A[qo] = (rrows, V[:, sorted(idx)])
-    return sec, A, total - kept
+    return sec, A, dropped
 
 
 def _solve(strings, Lb, Rb, N, seed, tol):

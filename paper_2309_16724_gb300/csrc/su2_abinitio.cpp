@@ -1469,10 +1469,14 @@ std::string sweep_split(const std::vector<Block>& blocks, const double* psi, con
     return a.idx < b.idx;
   });
   std::map<int, int> nkeep;
-  double kept = 0.0;
-  for (int x = 0; x < int(cand.size()) && x < D; ++x) {
-    nkeep[cand[x].sec] += 1;
-    kept += cand[x].w;
+  for (int x = 0; x < int(cand.size()) && x < D; ++x) nkeep[cand[x].sec] += 1;
+  // discarded weight: the sum of the sigma^2 not kept (summed directly, so
+  // that it is 0 when every non-zero singular value is kept)
+  double dropped = 0.0;
+  for (int q = 0; q < int(all.size()); ++q) {
+    const auto it = nkeep.find(q);
+    const int d = it == nkeep.end() ? 0 : it->second;
+    for (int x = d; x < int(all[q].sv.size()); ++x) dropped += all[q].sv[x] * all[q].sv[x];
   }
   std::vector<std::pair<std::pair<int, int>, int>> order;  // ((N, 2S) of the new bond, sector)
   for (const auto& kv : nkeep) {
@@ -1489,7 +1493,7 @@ std::string sweep_split(const std::vector<Block>& blocks, const double* psi, con
     Q.emplace_back(sc.U.begin(), sc.U.begin() + size_t(sc.rows) * d);
     orthonormalize(Q.back(), sc.rows, d);  // removes the rounding of the rotations (the columns are already orthonormal to ~1e-15)
   }
-  if (discarded) *discarded = total - kept;
+  if (discarded) *discarded = dropped;
   return new_sec.empty() ? "the wavefunction is zero" : "";
 }
 
