@@ -138,6 +138,27 @@ typedef struct {
                               TMEM and exits.  Small values are for testing
                               the timeout path; the H.psi result of a call
                               that timed out is undefined.                 */
+  int64_t resident_bytes;  /* out-of-core operators (Sec. III.E-F): 0 keeps
+                              every operator block on the device.  > 0:
+                              about this many bytes of FP64 operator blocks
+                              stay on the device (at least the blocks read
+                              by several term chunks, by the diagonal and
+                              by the small-task class, then the blocks of
+                              the first chunks); the others lie in pinned
+                              host memory, the blocks of each chunk
+                              contiguous, and every H.psi copies them chunk
+                              by chunk into two device slots on an IO
+                              stream of the environment, overlapped with
+                              the compute of other chunks (one
+                              cudaMemcpyAsync per chunk).  The chunk
+                              boundaries then bound both the intermediates
+                              and the operator bytes of a chunk by
+                              t_budget_bytes (0: 4 GiB).  With a host
+                              context only the plan is made (its numbers
+                              in su2_env_info; the host arenas take its
+                              layout).  The static-scratch entry point and
+                              Davidson graph capture reject such an
+                              environment (SU2_EINVAL).                    */
 } su2_env_opts;
 
 typedef struct {
@@ -166,6 +187,11 @@ typedef struct {
   double r_cc;             /* flops_u1_counted / flops_su2 (the paper's
                               R_CC); with a sharded environment it divides
                               the full table's count by the shard's flops */
+  int64_t resident_bytes;  /* FP64 operator bytes on the device            */
+  int64_t streamed_bytes;  /* FP64 operator bytes in pinned host memory,
+                              copied to the device once per H.psi (0: all
+                              resident)                                    */
+  int64_t n_io_chunks;     /* term chunks of the out-of-core plan (0: none) */
 } su2_env_info;
 
 typedef struct {

@@ -53,7 +53,7 @@ class Hamiltonian(C.Structure):
 class EnvOpts(C.Structure):
     _fields_ = [("t_budget_bytes", C.c_int64), ("n_slices", C.c_int32), ("prepare_split", C.c_int32),
                 ("autotune", C.c_int32), ("split_tol", C.c_double), ("shard_rank", C.c_int32),
-                ("shard_count", C.c_int32), ("spin_limit", C.c_int32)]
+                ("shard_count", C.c_int32), ("spin_limit", C.c_int32), ("resident_bytes", C.c_int64)]
 
 
 class EnvInfo(C.Structure):
@@ -62,7 +62,8 @@ class EnvInfo(C.Structure):
                 ("flops_su2", C.c_double), ("flops_u1_equiv", C.c_double), ("r_d", C.c_double),
                 ("env_bytes", C.c_double), ("split_slices", C.c_int32), ("split_stage_k", C.c_int32),
                 ("split_err_est", C.c_double), ("t_chunk_bytes", C.c_int64), ("renorm_flops", C.c_double),
-                ("flops_u1_counted", C.c_double), ("r_cc", C.c_double)]
+                ("flops_u1_counted", C.c_double), ("r_cc", C.c_double), ("resident_bytes", C.c_int64),
+                ("streamed_bytes", C.c_int64), ("n_io_chunks", C.c_int64)]
 
 
 class SweepOpts(C.Structure):
@@ -284,7 +285,7 @@ class Environment:
 
     def __init__(self, ctx: Context, sectors: Sectors, model, left_chain, right_chain, n_left=0, n_right=0,
                  J=1.0, seed=0, t_budget_bytes=0, n_slices=0, prepare_split=False, autotune=False,
-                 split_tol=0.0, shard=(0, 0), spin_limit=0, h=None, eri=None):
+                 split_tol=0.0, shard=(0, 0), spin_limit=0, h=None, eri=None, resident_bytes=0):
         self.ctx = ctx
         if model == SU2_MODEL_AB_INITIO:
             L = n_left + 2 + n_right
@@ -299,7 +300,7 @@ class Environment:
         lc, keep1 = _chain(left_chain)
         rc_, keep2 = _chain(right_chain)
         opts = EnvOpts(t_budget_bytes, n_slices, 1 if prepare_split else 0, 1 if autotune else 0, split_tol,
-                       shard[0], shard[1], spin_limit)
+                       shard[0], shard[1], spin_limit, int(resident_bytes))
         h = C.c_void_p()
         ctx.check(lib().su2_build_environment(ctx.h, C.byref(H), C.byref(lc), C.byref(rc_), sectors.h,
                                               C.byref(opts), C.byref(h)))

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsu2dmrg.so")
 SOURCES = ["su2_coupling.cpp", "su2_tables.cpp", "su2_abinitio.cpp", "capi.cu", "heff_fp64.cu", "heff_split.cu",
-           "davidson.cu", "envgen.cu", "renorm.cu", "noalloc.cu"]
+           "davidson.cu", "envgen.cu", "renorm.cu", "noalloc.cu", "opstream.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -36,6 +36,13 @@ int split_prepare(su2_env* env, int n_slices, std::string& err);
 int split_autotune(su2_env* env, double tol, std::string& err);
 int generate_side(const SideOps& so, double* d_arena, cudaStream_t s);
 int split_apply(su2_env* env, const double* psi, double* F, std::string& err);
+std::string stream_plan(su2_env* env, int64_t budget, int64_t resident_bytes, std::vector<int64_t> old_off[2]);
+std::string stream_populate(su2_env* env, cudaStream_t s, double* dev_old[2], const std::vector<int64_t> old_off[2]);
+void stream_free(OpStream& os);
+void stream_begin(OpStream& os, cudaStream_t s);
+void stream_wait(OpStream& os, int c, cudaStream_t s);
+void stream_release(OpStream& os, int c, cudaStream_t s);
+void stream_end(OpStream& os, cudaStream_t s);
 void split_free(su2_env* env);
 }  // namespace su2
 
@@ -225,9 +232,11 @@ static int build_plan(su2_env* env, const su2_sectors* S, int64_t budget) {
   // uniques of K1 per term (first appearance order)
   std::vector<std::vector<int64_t>> by_term(nterms);
   for (int64_t i = 0; i < int64_t(tasks.size()); ++i) by_term[tasks[i].term].push_back(i);
-  // chunk boundaries over terms
+  // chunk boundaries over terms (out-of-core: the planner's)
   std::vector<int> starts;
-  {
+  if (env->os.on) {
+    starts = env->os.starts;
+  } else {
     std::unordered_map<uint64_t, int64_t> seen;
     int64_t bytes = 0;
     starts.push_back(0);
@@ -273,7 +282,8 @@ static int build_plan(su2_env* env, const su2_sectors* S, int64_t budget) {
         const int k1 = E.rows, k2 = E.cols, n = D.rows;
         for (int tc = 0; tc < (n + kTile - 1) / kTile; ++tc)
           for (int tr = 0; tr < (k1 + kTile - 1) / kTile; ++tr)
-            env->k1.push_back(K1Job{E.offset, D.off, tsz, k1, k2, n, tr, tc, 0});
+            env->k1.push_back(K1Job{E.offset, env->os.on ? env->os.dev_off(D.off, int(c)) : D.off, tsz, k1, k2, n,
+                                    tr, tc, 0});
         flops += 2.0 * k1 * k2 * n;
         ch.k1_flops += 2.0 * k1 * k2 * n;
         ++nk1;
@@ -305,7 +315,7 @@ static int build_plan(su2_env* env, const su2_sectors* S, int64_t budget) {
           k.a_off = -1;
           c2 += 1.0;
         } else {
-          k.a_off = env->L.blocks[t.ablk].off;
+          k.a_off = env->os.on ? env->os.dev_off(env->L.blocks[t.ablk].off, int(c)) : env->L.blocks[t.ablk].off;
           flops += 2.0 * F.rows * E.rows * F.cols;
           ch.k2_flops += 2.0 * F.rows * E.rows * F.cols;
           c2 += E.rows;
@@ -352,10 +362,16 @@ static int build_plan(su2_env* env, const su2_sectors* S, int64_t budget) {
       const Task& t = tasks[i];
       if (t.e != t.f) continue;
       DiagTask d;
-      d.a_off = t.ablk < 0 ? -1 : env->L.blocks[t.ablk].off;
-      d.d_off = t.dblk < 0 ? -1 : env->R.blocks[t.dblk].off;
-      d.lda = blocks[f].rows;
-      d.ldd = blocks[f].cols;
+      if (env->os.on) {  // out-of-core: the kept diagonals, stride 1
+        d.a_off = t.ablk < 0 ? -1 : env->os.dg_off[0][size_t(t.ablk)];
+        d.d_off = t.dblk < 0 ? -1 : env->os.dg_off[1][size_t(t.dblk)];
+        d.lda = d.ldd = 0;
+      } else {
+        d.a_off = t.ablk < 0 ? -1 : env->L.blocks[t.ablk].off;
+        d.d_off = t.dblk < 0 ? -1 : env->R.blocks[t.dblk].off;
+        d.lda = blocks[f].rows;
+        d.ldd = blocks[f].cols;
+      }
       d.v = t.v;
       env->dt.push_back(d);
     }
@@ -369,6 +385,10 @@ static void env_free_device(su2_env* e) {
   if (e->device < 0) return;
   cudaSetDevice(e->device);
   split_free(e);
+  if (e->os.on) {  // dL and dR point into the out-of-core buffer
+    stream_free(e->os);
+    e->dL = e->dR = nullptr;
+  }
   cudaFree(e->dL);
   cudaFree(e->dR);
   cudaFree(e->dT);
@@ -417,6 +437,30 @@ void shard_terms(std::vector<Task>& tasks, const std::vector<Block>& blocks, int
 // failure the environment is deleted.
 static int finish_env(su2_ctx* ctx, su2_env* env, const su2_sectors* S, const su2_env_opts* opts) {
   int64_t budget = (opts && opts->t_budget_bytes > 0) ? opts->t_budget_bytes : (int64_t(2) << 30);
+  std::vector<int64_t> old_off[2];
+  if (opts && opts->resident_bytes > 0) {
+    const int64_t sb = opts->t_budget_bytes > 0 ? opts->t_budget_bytes : (int64_t(4) << 30);
+    std::string err = stream_plan(env, sb, opts->resident_bytes, old_off);
+    if (!err.empty()) {
+      cudaFree(env->L.dev_ready);
+      cudaFree(env->R.dev_ready);
+      delete env;
+      return fail(ctx, SU2_EINVAL, err);
+    }
+    env->split_budget = sb;
+    if (ctx->device < 0) {
+      // host context: the plan only (its numbers in the info); each side's
+      // host arena takes the logical layout
+      for (int sd = 0; sd < 2; ++sd) {
+        SideOps& so = sd == 0 ? env->L : env->R;
+        std::vector<double> a(size_t(std::max<int64_t>(env->os.total, 2)), 0.0);
+        for (size_t b = 0; b < so.blocks.size(); ++b)
+          std::memcpy(&a[size_t(so.blocks[b].off)], &so.arena[size_t(old_off[sd][b])],
+                      sizeof(double) * size_t(so.blocks[b].rows) * so.blocks[b].cols);
+        so.arena.swap(a);
+      }
+    }
+  }
   int rc2 = build_plan(env, S, budget);
   if (rc2) {
     delete env;
@@ -442,9 +486,29 @@ static int finish_env(su2_ctx* ctx, su2_env* env, const su2_sectors* S, const su
     in.r_cc = in.flops_su2 > 0 ? in.flops_u1_counted / in.flops_su2 : 0.0;
   }
   in.env_bytes = 8.0 * double(env->L.arena_size + env->R.arena_size);
+  in.resident_bytes = env->os.on ? 8 * env->os.prefix : int64_t(in.env_bytes);
+  in.streamed_bytes = env->os.on ? 8 * (env->os.total - env->os.prefix) : 0;
+  in.n_io_chunks = env->os.on ? int64_t(env->os.starts.size()) - 1 : 0;
+  if (ctx->device >= 0 && env->os.on) {
+    int rc = set_device(ctx);
+    if (!rc) {
+      double* dev_old[2] = {env->L.dev_ready, env->R.dev_ready};
+      const std::string err = stream_populate(env, ctx->stream, dev_old, old_off);
+      cudaFree(dev_old[0]);
+      cudaFree(dev_old[1]);
+      env->L.dev_ready = env->R.dev_ready = nullptr;
+      env->dL = env->dR = env->os.dbuf;
+      if (!err.empty()) rc = fail(ctx, SU2_ENOMEM, err);
+    }
+    if (rc) {
+      env_free_device(env);
+      delete env;
+      return rc;
+    }
+  }
   if (ctx->device >= 0) {
     int rc = set_device(ctx);
-    for (int side = 0; side < 2 && !rc; ++side) {
+    for (int side = 0; side < 2 && !rc && !env->os.on; ++side) {
       SideOps& so = side == 0 ? env->L : env->R;
       double** dst = side == 0 ? &env->dL : &env->dR;
       if (so.dev_ready) {  // filled on the device by the builder
@@ -603,6 +667,10 @@ int su2_env_operator_block(const su2_env* env, int32_t side, int32_t op, int32_t
     std::memcpy(out, &so.arena[so.blocks[b].off], sizeof(double) * size_t(rows) * cols);
     return SU2_OK;
   }
+  if (env->os.on && so.blocks[b].off >= env->os.prefix) {  // out-of-core: in pinned host memory
+    std::memcpy(out, env->os.host + (so.blocks[b].off - env->os.prefix), sizeof(double) * size_t(rows) * cols);
+    return SU2_OK;
+  }
   const double* dsrc = (side == 0 ? env->dL : env->dR) + so.blocks[b].off;
   if (cudaSetDevice(env->device) != cudaSuccess ||
       cudaMemcpy(out, dsrc, sizeof(double) * size_t(rows) * cols, cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -633,9 +701,14 @@ int su2_apply_heff(su2_ctx* ctx, const su2_env* env_c, const double* psi_in, dou
   }
   if (prec != SU2_FP64) return fail(ctx, SU2_EINVAL, "unknown precision");
   CUDA_TRY(ctx, cudaMemsetAsync(psi_out, 0, size_t(n) * sizeof(double), ctx->stream));
-  for (const Chunk& c : env->chunks)
-    launch_heff_fp64(ctx->stream, env->dL, env->dR, psi_in, psi_out, env->dT, env->dk1, env->dk2, env->dk2t, c, n,
-                     &env->prof);
+  if (env->os.on) stream_begin(env->os, ctx->stream);
+  for (size_t ci = 0; ci < env->chunks.size(); ++ci) {
+    if (env->os.on) stream_wait(env->os, int(ci), ctx->stream);
+    launch_heff_fp64(ctx->stream, env->dL, env->dR, psi_in, psi_out, env->dT, env->dk1, env->dk2, env->dk2t,
+                     env->chunks[ci], n, &env->prof);
+    if (env->os.on) stream_release(env->os, int(ci), ctx->stream);
+  }
+  if (env->os.on) stream_end(env->os, ctx->stream);
   CUDA_TRY(ctx, cudaGetLastError());
   return SU2_OK;
 }
@@ -704,7 +777,9 @@ int su2_diag_heff(su2_ctx* ctx, const su2_env* env, double* diag_dev) {
   if (!ctx || !env || !diag_dev) return fail(ctx, SU2_EINVAL, "null argument");
   int rc = set_device(ctx);
   if (rc) return rc;
-  launch_diag(ctx->stream, env->dL, env->dR, diag_dev, env->ddj, int64_t(env->dj.size()), env->ddt, env->psi_len);
+  const double* Ld = env->os.on ? env->os.ddiag : env->dL;
+  const double* Rd = env->os.on ? env->os.ddiag : env->dR;
+  launch_diag(ctx->stream, Ld, Rd, diag_dev, env->ddj, int64_t(env->dj.size()), env->ddt, env->psi_len);
   CUDA_TRY(ctx, cudaGetLastError());
   return SU2_OK;
 }
@@ -778,6 +853,10 @@ int su2_davidson_create(su2_ctx* ctx, const su2_env* env, const double* psi0, co
     if (opts->max_iter > 0) d->o.max_iter = opts->max_iter;
     d->o.prec = opts->prec;
     d->use_graph = opts->use_graph != 0;
+  }
+  if (d->use_graph && env->os.on) {
+    delete d;
+    return fail(ctx, SU2_EINVAL, "graph capture of an environment with out-of-core operators is not supported");
   }
   if (d->o.max_sub > 32 || d->o.max_sub < 3 || d->o.keep >= d->o.max_sub) {
     delete d;

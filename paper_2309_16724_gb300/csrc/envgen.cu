@@ -21,40 +21,50 @@ __device__ __forceinline__ double duniform(uint64_t key, uint64_t idx) {
   return __dmul_rn(double(x >> 11), 1.0 / 9007199254740992.0) * 2.0 - 1.0;
 }
 
-// one CTA per (block, 64K-element slab)
+// entry (r, c) of a generated block of `kind` (0 random, 1 HAM) with `rows` rows
+__device__ __forceinline__ double gen_value(int kind, uint64_t key, double scale, int rows, int r, int c) {
+  const uint64_t i = uint64_t(r) + uint64_t(c) * uint64_t(rows);
+  if (kind == 0) return __dmul_rn(duniform(key, i), scale);
+  const double x = __dmul_rn(duniform(key, i), scale);
+  const double y = __dmul_rn(duniform(key, uint64_t(c) + uint64_t(r) * uint64_t(rows)), scale);
+  double v = __dmul_rn(0.1, __dadd_rn(x, y));
+  if (r == c) v = __dadd_rn(v, __ddiv_rn(2.0 * r, double(rows)));
+  return v;
+}
+
+// one CTA per (block, 64K-element slab); block g is written at
+// arena[g.off - shift]
 __global__ void gen_kernel(const GenBlock* __restrict__ gb, const int64_t* __restrict__ unit_block,
-                           const int64_t* __restrict__ unit_start, double* __restrict__ arena, int adjoint_pass) {
+                           const int64_t* __restrict__ unit_start, double* __restrict__ arena, int64_t shift) {
   const GenBlock g = gb[unit_block[blockIdx.x]];
-  if ((g.kind == 2) != (adjoint_pass != 0)) return;
   const int64_t n = int64_t(g.rows) * g.cols;
   const int64_t i0 = unit_start[blockIdx.x];
   const int64_t i1 = i0 + 65536 < n ? i0 + 65536 : n;
-  double* m = arena + g.off;
+  double* m = arena + (g.off - shift);
   for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const int r = int(i % g.rows), c = int(i / g.rows);
-    if (g.kind == 0) {
-      m[i] = __dmul_rn(duniform(g.key, uint64_t(i)), g.scale);
-    } else if (g.kind == 1) {
-      const double x = __dmul_rn(duniform(g.key, uint64_t(i)), g.scale);
-      const double y = __dmul_rn(duniform(g.key, uint64_t(c) + uint64_t(r) * g.rows), g.scale);
-      double v = __dmul_rn(0.1, __dadd_rn(x, y));
-      if (r == c) v = __dadd_rn(v, __ddiv_rn(2.0 * r, double(g.rows)));
-      m[i] = v;
-    } else {
-      // adjoint: base block is cols x rows
-      m[i] = __dmul_rn(g.scale, arena[g.base_off + c + int64_t(r) * g.cols]);
-    }
+    if (g.kind == 2)  // adjoint: the base block is cols x rows, entry (c, r)
+      m[i] = __dmul_rn(g.scale, gen_value(g.base_kind, g.key, g.base_scale, g.cols, c, r));
+    else
+      m[i] = gen_value(g.kind, g.key, g.scale, g.rows, r, c);
   }
 }
 
 }  // namespace
 
-// returns a CUDA error code (0 on success)
-int generate_side(const SideOps& so, double* d_arena, cudaStream_t s) {
-  if (so.gen.empty()) return 0;
+// Generates the blocks `which` of `gen` (all of them when which is null) into
+// arena[off - shift]; returns a CUDA error code (0 on success).
+int generate_blocks(const std::vector<GenBlock>& gen, const std::vector<int>* which, double* d_arena, int64_t shift,
+                    cudaStream_t s) {
+  std::vector<GenBlock> sel;
+  if (which) {
+    for (int b : *which) sel.push_back(gen[size_t(b)]);
+  }
+  const std::vector<GenBlock>& g = which ? sel : gen;
+  if (g.empty()) return 0;
   std::vector<int64_t> ub, us;
-  for (size_t b = 0; b < so.gen.size(); ++b) {
-    const int64_t n = int64_t(so.gen[b].rows) * so.gen[b].cols;
+  for (size_t b = 0; b < g.size(); ++b) {
+    const int64_t n = int64_t(g[b].rows) * g[b].cols;
     for (int64_t i = 0; i < n; i += 65536) {
       ub.push_back(int64_t(b));
       us.push_back(i);
@@ -62,15 +72,14 @@ int generate_side(const SideOps& so, double* d_arena, cudaStream_t s) {
   }
   GenBlock* dg = nullptr;
   int64_t *dub = nullptr, *dus = nullptr;
-  cudaError_t e = cudaMalloc(&dg, so.gen.size() * sizeof(GenBlock));
+  cudaError_t e = cudaMalloc(&dg, g.size() * sizeof(GenBlock));
   if (e == cudaSuccess) e = cudaMalloc(&dub, ub.size() * sizeof(int64_t));
   if (e == cudaSuccess) e = cudaMalloc(&dus, us.size() * sizeof(int64_t));
-  if (e == cudaSuccess) e = cudaMemcpy(dg, so.gen.data(), so.gen.size() * sizeof(GenBlock), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dg, g.data(), g.size() * sizeof(GenBlock), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(dub, ub.data(), ub.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(dus, us.data(), us.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !ub.empty()) {
-    gen_kernel<<<unsigned(ub.size()), 256, 0, s>>>(dg, dub, dus, d_arena, 0);
-    gen_kernel<<<unsigned(ub.size()), 256, 0, s>>>(dg, dub, dus, d_arena, 1);
+    gen_kernel<<<unsigned(ub.size()), 256, 0, s>>>(dg, dub, dus, d_arena, shift);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }
@@ -78,6 +87,10 @@ int generate_side(const SideOps& so, double* d_arena, cudaStream_t s) {
   cudaFree(dub);
   cudaFree(dus);
   return int(e);
+}
+
+int generate_side(const SideOps& so, double* d_arena, cudaStream_t s) {
+  return generate_blocks(so.gen, nullptr, d_arena, 0, s);
 }
 
 }  // namespace su2

@@ -43,6 +43,11 @@
 #include "su2_device.h"
 
 namespace su2 {
+void stream_begin(OpStream& os, cudaStream_t s);
+void stream_wait(OpStream& os, int c, cudaStream_t s);
+void stream_release(OpStream& os, int c, cudaStream_t s);
+void stream_end(OpStream& os, cudaStream_t s);
+
 namespace {
 
 using sp::Item;
@@ -83,7 +88,6 @@ struct TPUnit { int32_t task, tr, ks, pad; };
 // (no slabs, no MMA tile padding, no drain chunk).  One warp per segment of
 // up to kSmallSeg tasks of one output block writes a partial block; a second
 // pass adds each block's partials into F in segment order (deterministic).
-constexpr int kSmallDim = 16;
 constexpr int kSmallSeg = 32;
 struct SmallTask {
   int64_t e_off, a_off, d_off;  // psi block, left / right operator block (-1: identity)
@@ -99,6 +103,7 @@ struct SmallSeg { int32_t t0, t1; };  // a segment's tasks (one output block)
 
 struct SChunk {
   int64_t k1_j0, k1_j1, src0, src1, tp0, tp1, tpu0, tpu1, k2_j0, k2_j1;
+  int64_t sau0, sau1, sdu0, sdu1;  // out-of-core: the chunk's slicing units (A side, D side)
   double k1_flops, k2_flops;
 };
 
@@ -147,6 +152,16 @@ struct SplitState {
   int64_t n_scale = 0;
   int n_sms = 148;
   int spin = int(sp::kSpinLimit);  // polls of each work-loop mbarrier wait of the split GEMM
+  // out-of-core operators: the operator slabs of one chunk are cut per H.psi
+  // from the chunk's FP64 blocks (resident or in its device slot) into a
+  // chunk workspace; the identity slabs stay
+  std::vector<SlabDesc> sdesc;   // per-chunk slicing descriptors (A and D sides)
+  std::vector<Unit> sunit;
+  SlabDesc* d_sdesc = nullptr;
+  Unit* d_sunit = nullptr;
+  std::vector<Unit> resunit_a, resunit_d;  // units of the resident blocks (exponents at prepare)
+  Unit *d_resunit_a = nullptr, *d_resunit_d = nullptr;
+  int64_t ident_u0 = 0;          // first unit of the identity descriptors in aunit
 };
 
 // ------------------------------------------------------------------ device helpers
@@ -278,24 +293,75 @@ __global__ void psi_ff_kernel(const double* __restrict__ x, float* __restrict__ 
   }
 }
 
-// column exponents of the float-float sources: one CTA per source; in a
-// column-major block its warps take the columns in turn and their lanes the
-// rows (contiguous), in a row-major one each thread takes a column and walks
-// its rows (the lanes of a warp read neighbouring elements)
+// column exponents of the float-float sources: one CTA per source.  T
+// written by K1 has 16-byte aligned columns (column-major, rows padded to a
+// multiple of 4) or rows (row-major, columns padded), so both read it with
+// 16-byte loads: column-major, each warp takes two columns at a time and its
+// lanes four rows each; row-major, each thread takes four neighbouring
+// columns and walks the rows.  Elements past the valid rows / columns are
+// read (they lie inside the padding) but not used.  psi sources (unpadded)
+// keep a warp per column with one float per lane.
 __global__ void cexp_kernel(const Source* __restrict__ src, const float* __restrict__ Th,
                             const float* __restrict__ Ph, int* __restrict__ cexp) {
   const Source s = src[blockIdx.x];
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
   const float* base = (s.sel ? Ph : Th) + s.off;
   if (s.rowmajor) {
-    for (int c = threadIdx.x; c < s.cols; c += blockDim.x) {
-      float m = 0.f;
-      for (int r = 0; r < s.rows; ++r) m = fmaxf(m, fabsf(base[int64_t(r) * s.ld + c]));
-      cexp[s.cexp_off + c] = exp_of_f(m);
+    for (int c4 = 4 * threadIdx.x; c4 < s.cols; c4 += 4 * blockDim.x) {
+      float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+#pragma unroll 4
+      for (int r = 0; r < s.rows; ++r) {
+        const float4 v = *reinterpret_cast<const float4*>(base + int64_t(r) * s.ld + c4);
+        m0 = fmaxf(m0, fabsf(v.x));
+        m1 = fmaxf(m1, fabsf(v.y));
+        m2 = fmaxf(m2, fabsf(v.z));
+        m3 = fmaxf(m3, fabsf(v.w));
+      }
+      cexp[s.cexp_off + c4] = exp_of_f(m0);
+      if (c4 + 1 < s.cols) cexp[s.cexp_off + c4 + 1] = exp_of_f(m1);
+      if (c4 + 2 < s.cols) cexp[s.cexp_off + c4 + 2] = exp_of_f(m2);
+      if (c4 + 3 < s.cols) cexp[s.cexp_off + c4 + 3] = exp_of_f(m3);
     }
     return;
   }
-  for (int c = threadIdx.x >> 5; c < s.cols; c += nw) {
+  if (s.sel == 0) {
+    for (int c = 2 * warp; c < s.cols; c += 2 * nw) {
+      const bool two = c + 1 < s.cols;
+      const float* h0 = base + int64_t(c) * s.ld;
+      const float* h1 = h0 + s.ld;
+      float m0 = 0.f, m1 = 0.f;
+      for (int r = 4 * lane; r < s.rows; r += 128) {
+        const float4 v0 = *reinterpret_cast<const float4*>(h0 + r);
+        const float4 v1 = two ? *reinterpret_cast<const float4*>(h1 + r) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int left = s.rows - r;  // valid rows from r on (>= 1)
+        m0 = fmaxf(m0, fabsf(v0.x));
+        m1 = fmaxf(m1, fabsf(v1.x));
+        if (left > 1) {
+          m0 = fmaxf(m0, fabsf(v0.y));
+          m1 = fmaxf(m1, fabsf(v1.y));
+        }
+        if (left > 2) {
+          m0 = fmaxf(m0, fabsf(v0.z));
+          m1 = fmaxf(m1, fabsf(v1.z));
+        }
+        if (left > 3) {
+          m0 = fmaxf(m0, fabsf(v0.w));
+          m1 = fmaxf(m1, fabsf(v1.w));
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+      }
+      if (lane == 0) {
+        cexp[s.cexp_off + c] = exp_of_f(m0);
+        if (two) cexp[s.cexp_off + c + 1] = exp_of_f(m1);
+      }
+    }
+    return;
+  }
+  for (int c = warp; c < s.cols; c += nw) {
     const float* h = base + int64_t(c) * s.ld;
     float m = 0.f;
     for (int r = lane; r < s.rows; r += 32) m = fmaxf(m, fabsf(h[r]));
@@ -688,12 +754,14 @@ int split_prepare(su2_env* env, int S, std::string& err) {
     acc += ls[a].dim;
   }
   st->n_rho = acc;
+  const bool ooc = env->os.on;  // out-of-core operators: block slabs live in a per-chunk workspace
   int64_t own = 0, ab = 0;
   for (int bi = 0; bi < nLb; ++bi) {
     const OpBlock& ob = L.blocks[bi];
-    st->adesc.push_back(SlabDesc{ob.off, ab, ob.rows, ob.cols, ob.rows, int32_t(rho_off[ob.qo]), bi, int32_t(own), 0, 0});
+    st->adesc.push_back(SlabDesc{ob.off, ooc ? -1 : ab, ob.rows, ob.cols, ob.rows, int32_t(rho_off[ob.qo]), bi,
+                                 int32_t(own), 0, 0});
     own += ob.rows;
-    ab += slab_bytes(ob.rows, ob.cols, S);
+    if (!ooc) ab += slab_bytes(ob.rows, ob.cols, S);
   }
   for (size_t a = 0; a < ls.size(); ++a) {
     const int d = ls[a].dim;
@@ -704,16 +772,20 @@ int split_prepare(su2_env* env, int S, std::string& err) {
   }
   st->n_aown = own;
   st->a_bytes = ab;
-  for (size_t i = 0; i < st->adesc.size(); ++i) add_units(st->aunit, int(i), st->adesc[i].rows, st->adesc[i].cols);
+  for (size_t i = 0; i < st->adesc.size(); ++i) {
+    if (int(i) == nLb) st->ident_u0 = int64_t(st->aunit.size());
+    add_units(st->aunit, int(i), st->adesc[i].rows, st->adesc[i].cols);
+  }
+  if (nLb == int(st->adesc.size())) st->ident_u0 = int64_t(st->aunit.size());
   // ---------------------------------------------------------- D side
   int64_t zoff = 0, db = 0;
   std::vector<int64_t> zeta_off(R.blocks.size());
   for (size_t bi = 0; bi < R.blocks.size(); ++bi) {
     const OpBlock& ob = R.blocks[bi];
     zeta_off[bi] = zoff;
-    st->ddesc.push_back(SlabDesc{ob.off, db, ob.rows, ob.cols, ob.rows, int32_t(zoff), -1, -1, 0, 0});
+    st->ddesc.push_back(SlabDesc{ob.off, ooc ? -1 : db, ob.rows, ob.cols, ob.rows, int32_t(zoff), -1, -1, 0, 0});
     zoff += ob.rows;
-    db += slab_bytes(ob.rows, ob.cols, S);
+    if (!ooc) db += slab_bytes(ob.rows, ob.cols, S);
   }
   st->n_zeta = zoff;
   st->d_bytes = db;
@@ -780,7 +852,9 @@ int split_prepare(su2_env* env, int S, std::string& err) {
     budget = std::min<int64_t>(int64_t(16) << 30, std::max<int64_t>(int64_t(fr) / 4, int64_t(1) << 30));
   }
   std::vector<int> starts{0};
-  {
+  if (ooc) {
+    starts = env->os.starts;
+  } else {
     int64_t bytes = 0;
     std::unordered_map<uint64_t, char> seen;
     for (int ti = 0; ti < nterms; ++ti) {
@@ -809,11 +883,58 @@ int split_prepare(su2_env* env, int S, std::string& err) {
     }
     starts.push_back(nterms);
   }
-  int64_t max_t = 0, max_tp = 0, max_cexp = 0;
+  int64_t max_t = 0, max_tp = 0, max_cexp = 0, max_as = 0, max_ds = 0;
   const int64_t nt = int64_t(env->tasks.size());
+  if (ooc) {  // units of the resident blocks: their exponents are taken once, at prepare
+    for (size_t i = 0; i < size_t(nLb); ++i)
+      if (L.blocks[i].off < env->os.prefix) add_units(st->resunit_a, int(i), st->adesc[i].rows, st->adesc[i].cols);
+    for (size_t i = st->ident_u0; i < st->aunit.size(); ++i) st->resunit_a.push_back(st->aunit[i]);
+    for (size_t i = 0; i < R.blocks.size(); ++i)
+      if (R.blocks[i].off < env->os.prefix) add_units(st->resunit_d, int(i), st->ddesc[i].rows, st->ddesc[i].cols);
+  }
   for (size_t c = 0; c + 1 < starts.size(); ++c) {
     const int t0 = starts[c], t1 = starts[c + 1];
     SChunk ch{};
+    // out-of-core: the chunk's operator blocks, sliced into the chunk
+    // workspace (A blocks after the identity slabs) from their device place
+    // for this chunk
+    std::unordered_map<int, int64_t> aloc, dloc;
+    if (ooc) {
+      ch.sau0 = ch.sdu0 = 0;
+      std::vector<Unit> ua, ud;
+      int64_t ab_c = ab, db_c = 0;
+      for (int ti = t0; ti < t1; ++ti)
+        for (int64_t i : by_term[ti]) {
+          const Task& t = env->tasks[i];
+          if (t.ablk >= 0 && !aloc.count(t.ablk)) {
+            SlabDesc d = st->adesc[t.ablk];
+            d.src_off = env->os.dev_off(L.blocks[t.ablk].off, int(c));
+            d.slab_off = ab_c;
+            aloc[t.ablk] = ab_c;
+            ab_c += slab_bytes(d.rows, d.cols, S);
+            st->sdesc.push_back(d);
+            add_units(ua, int(st->sdesc.size()) - 1, d.rows, d.cols);
+          }
+          if (t.dblk >= 0 && !dloc.count(t.dblk)) {
+            SlabDesc d = st->ddesc[t.dblk];
+            d.src_off = env->os.dev_off(R.blocks[t.dblk].off, int(c));
+            d.slab_off = db_c;
+            dloc[t.dblk] = db_c;
+            db_c += slab_bytes(d.rows, d.cols, S);
+            st->sdesc.push_back(d);
+            add_units(ud, int(st->sdesc.size()) - 1, d.rows, d.cols);
+          }
+        }
+      ch.sau0 = int64_t(st->sunit.size());
+      st->sunit.insert(st->sunit.end(), ua.begin(), ua.end());
+      ch.sau1 = ch.sdu0 = int64_t(st->sunit.size());
+      st->sunit.insert(st->sunit.end(), ud.begin(), ud.end());
+      ch.sdu1 = int64_t(st->sunit.size());
+      max_as = std::max(max_as, ab_c);
+      max_ds = std::max(max_ds, db_c);
+    }
+    auto aslab = [&](int aid) -> int64_t { return (ooc && aid < nLb) ? aloc.at(aid) : st->adesc[aid].slab_off; };
+    auto dslab = [&](int dblk) -> int64_t { return ooc ? dloc.at(dblk) : st->ddesc[dblk].slab_off; };
     ch.k1_j0 = int64_t(st->k1j.size());
     ch.src0 = int64_t(st->src.size());
     ch.tp0 = int64_t(st->tpt.size());
@@ -853,14 +974,13 @@ int split_prepare(su2_env* env, int S, std::string& err) {
       csz += n;
       umap[key] = id;
       const int mr = trans ? n : k1, nr = trans ? k1 : n;
-      const SlabDesc& mdesc = trans ? st->ddesc[t.dblk] : st->edesc[t.e];
-      const SlabDesc& ndesc = trans ? st->edesc[t.e] : st->ddesc[t.dblk];
+      const int64_t mslab = trans ? dslab(t.dblk) : st->edesc[t.e].slab_off;
+      const int64_t nslab = trans ? st->edesc[t.e].slab_off : dslab(t.dblk);
       // the N tiles of one M tile are neighbouring jobs (they share the M-side tile)
       for (int tr = 0; tr < (mr + 127) / 128; ++tr)
         for (int tc = 0; tc < (nr + sp::kCols - 1) / sp::kCols; ++tc) {
           const int ii = int(st->k1i.size());
-          st->k1i.push_back(Item{mdesc.slab_off + int64_t(tr) * kst2 * S * kSub,
-                                 ndesc.slab_off + btile_off(tc, kst2, S), kst2, 0, -1});
+          st->k1i.push_back(Item{mslab + int64_t(tr) * kst2 * S * kSub, nslab + btile_off(tc, kst2, S), kst2, 0, -1});
           k1jobs.push_back(Job{tsz, mr, nr, ldT, tr, tc, ii, ii + 1, int32_t(eps_off[t.e]),
                                int32_t(zeta_off[t.dblk]), kst2, nmma_of(nr, tc), trans ? sp::kJobTrans : 0});
           k1cost.push_back(kst2);
@@ -923,7 +1043,7 @@ int split_prepare(su2_env* env, int S, std::string& err) {
           const int i0 = int(st->k2i.size());
           int tot = 0;
           for (size_t q = 0; q < mine.size(); ++q) {
-            const int64_t aoff = st->adesc[aid[q]].slab_off + int64_t(trans ? tc : tr) * kst[q] * S * kSub;
+            const int64_t aoff = aslab(aid[q]) + int64_t(trans ? tc : tr) * kst[q] * S * kSub;
             const int64_t toff = tp[q] + btile_off(trans ? tr : tc, kst[q], S);
             st->k2i.push_back(Item{trans ? toff : aoff, trans ? aoff : toff, kst[q], 0, sco[q]});
             tot += kst[q];
@@ -969,6 +1089,10 @@ int split_prepare(su2_env* env, int S, std::string& err) {
   st->t_elems = max_t;
   st->tp_bytes = max_tp;
   st->n_cexp = max_cexp;
+  if (ooc) {
+    st->a_bytes = std::max(max_as, ab);  // identity slabs, then the largest chunk's A slabs
+    st->d_bytes = max_ds;
+  }
   // ---------------------------------------------------------- device memory
   int rc2 = 0;
   if (!rc2) rc2 = dalloc(&st->dA, size_t(st->a_bytes), err);
@@ -1007,20 +1131,59 @@ int split_prepare(su2_env* env, int S, std::string& err) {
   if (!rc2) rc2 = dput(&st->d_small_out, st->small_out, err);
   if (!rc2) rc2 = dput(&st->d_small_seg, st->small_seg, err);
   if (!rc2) rc2 = dalloc(&st->d_small_part, std::max<size_t>(st->small_seg.size(), 1) * kSmallDim * kSmallDim, err);
+  if (!rc2 && ooc) rc2 = dput(&st->d_sdesc, st->sdesc, err);
+  if (!rc2 && ooc) rc2 = dput(&st->d_sunit, st->sunit, err);
+  if (!rc2 && ooc) rc2 = dput(&st->d_resunit_a, st->resunit_a, err);
+  if (!rc2 && ooc) rc2 = dput(&st->d_resunit_d, st->resunit_d, err);
   if (rc2) return rc2;
   // ---------------------------------------------------------- operator slabs (once per site)
   cudaStream_t s = env->ctx->stream;
   const int na = int(st->aunit.size()), nd = int(st->dunit.size());
   fill_kernel<<<256, 256, 0, s>>>(st->d_rho, st->n_rho, kSentinel);
   fill_kernel<<<64, 256, 0, s>>>(st->d_delta, int64_t(st->adesc.size()), INT_MAX);
-  if (na) {
+  if (ooc) {
+    // exponents of every block, as in the resident case: the resident blocks
+    // (and the identities) in place, then each chunk's blocks with its
+    // streamed range in slot c % 2; then rho, delta and the identity slabs
+    OpStream& os = env->os;
+    fill_kernel<<<256, 256, 0, s>>>(st->d_aown, st->n_aown, kSentinel);
+    if (!st->resunit_a.empty())
+      rowexp_kernel<<<unsigned(st->resunit_a.size()), 128, 0, s>>>(st->d_adesc, st->d_resunit_a, os.dbuf, st->d_aown, 1);
+    if (!st->resunit_d.empty())
+      rowexp_kernel<<<unsigned(st->resunit_d.size()), 128, 0, s>>>(st->d_ddesc, st->d_resunit_d, os.dbuf, st->d_zeta, 0);
+    for (size_t c = 0; c < st->chunks.size(); ++c) {
+      const SChunk& ch = st->chunks[c];
+      const int64_t n = os.he[c] - os.hs[c];
+      if (n > 0 &&
+          cudaMemcpyAsync(os.dbuf + os.prefix + int64_t(c & 1) * os.slot, os.host + (os.hs[c] - os.prefix),
+                          size_t(n) * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        err = "out-of-core operators: copy failed";
+        return SU2_ECUDA;
+      }
+      if (ch.sau1 > ch.sau0)
+        rowexp_kernel<<<unsigned(ch.sau1 - ch.sau0), 128, 0, s>>>(st->d_sdesc, st->d_sunit + ch.sau0, os.dbuf,
+                                                                   st->d_aown, 1);
+      if (ch.sdu1 > ch.sdu0)
+        rowexp_kernel<<<unsigned(ch.sdu1 - ch.sdu0), 128, 0, s>>>(st->d_sdesc, st->d_sunit + ch.sdu0, os.dbuf,
+                                                                   st->d_zeta, 0);
+    }
+    if (na) {
+      rho_kernel<<<na, 128, 0, s>>>(st->d_adesc, st->d_aunit, st->d_aown, st->d_rho);
+      delta_kernel<<<na, 128, 0, s>>>(st->d_adesc, st->d_aunit, st->d_aown, st->d_rho, st->d_delta);
+      delta_fix_kernel<<<int((st->adesc.size() + 255) / 256), 256, 0, s>>>(st->d_delta, int(st->adesc.size()));
+      const int64_t ni = int64_t(na) - st->ident_u0;
+      if (ni > 0)
+        slab_fp64_kernel<<<unsigned(ni), 128, 0, s>>>(st->d_adesc, st->d_aunit + st->ident_u0, os.dbuf, st->d_rho,
+                                                       st->d_delta, st->dA, S);
+    }
+  } else if (na) {
     rowexp_kernel<<<na, 128, 0, s>>>(st->d_adesc, st->d_aunit, env->dL, st->d_aown, 1);
     rho_kernel<<<na, 128, 0, s>>>(st->d_adesc, st->d_aunit, st->d_aown, st->d_rho);
     delta_kernel<<<na, 128, 0, s>>>(st->d_adesc, st->d_aunit, st->d_aown, st->d_rho, st->d_delta);
     delta_fix_kernel<<<int((st->adesc.size() + 255) / 256), 256, 0, s>>>(st->d_delta, int(st->adesc.size()));
     slab_fp64_kernel<<<na, 128, 0, s>>>(st->d_adesc, st->d_aunit, env->dL, st->d_rho, st->d_delta, st->dA, S);
   }
-  if (nd) {
+  if (nd && !ooc) {
     rowexp_kernel<<<nd, 128, 0, s>>>(st->d_ddesc, st->d_dunit, env->dR, st->d_zeta, 0);
     slab_fp64_kernel<<<nd, 128, 0, s>>>(st->d_ddesc, st->d_dunit, env->dR, st->d_zeta, st->d_delta, st->dD, S);
   }
@@ -1066,7 +1229,26 @@ int split_apply(su2_env* env, const double* psi, double* F, std::string& err) {
   pf.end(s, slot);
   SPLIT_CHECK("psi slabs");
   const double npairs = S * (S + 1) / 2.0;
-  for (const SChunk& c : st->chunks) {
+  const bool ooc = env->os.on;
+  if (ooc) stream_begin(env->os, s);
+  for (size_t ci = 0; ci < st->chunks.size(); ++ci) {
+    const SChunk& c = st->chunks[ci];
+    if (ooc) {
+      // the chunk's operator slabs, cut as soon as its blocks are on the
+      // device; its slot is then free for the copy of chunk ci + 2
+      stream_wait(env->os, int(ci), s);
+      pf.count(int(c.sau1 > c.sau0) + int(c.sdu1 > c.sdu0));
+      slot = pf.begin(s, 2, 0.0);
+      if (c.sau1 > c.sau0)
+        slab_fp64_kernel<<<unsigned(c.sau1 - c.sau0), 128, 0, s>>>(st->d_sdesc, st->d_sunit + c.sau0, env->os.dbuf,
+                                                                    st->d_rho, st->d_delta, st->dA, S);
+      if (c.sdu1 > c.sdu0)
+        slab_fp64_kernel<<<unsigned(c.sdu1 - c.sdu0), 128, 0, s>>>(st->d_sdesc, st->d_sunit + c.sdu0, env->os.dbuf,
+                                                                    st->d_zeta, st->d_delta, st->dD, S);
+      pf.end(s, slot);
+      stream_release(env->os, int(ci), s);
+      SPLIT_CHECK("operator slabs of the chunk");
+    }
     pf.count(int(c.k1_j1 > c.k1_j0) + int(c.k2_j1 > c.k2_j0) + 5);
     slot = pf.begin(s, 3, c.k1_flops * npairs);
     launch_gemm(sp::MODE_T, s, st, st->d_k1j + c.k1_j0, int(c.k1_j1 - c.k1_j0), st->d_k1i, st->dE, st->dD, st->d_eps,
@@ -1101,6 +1283,7 @@ int split_apply(su2_env* env, const double* psi, double* F, std::string& err) {
     pf.end(s, slot);
     SPLIT_CHECK("K2 split GEMM");
   }
+  if (ooc) stream_end(env->os, s);
   // the small-task class, added after the tensor-core contributions
   if (!st->small_out.empty()) {
     pf.count(2);
@@ -1227,7 +1410,8 @@ void split_free(su2_env* env) {
                 st->d_eunit, st->d_rho, st->d_aown, st->d_delta, st->d_zeta, st->d_eps, st->d_gamma, st->d_cexp,
                 st->dTh, st->dTl, st->dPh, st->dPl, st->d_k1j, st->d_k2j, st->d_k1i, st->d_k2i, st->d_src,
                 st->d_tpt, st->d_tpu, st->d_counter, st->d_phi,
-                st->d_scale, st->d_scoff, st->d_small, st->d_small_out, st->d_small_seg, st->d_small_part};
+                st->d_scale, st->d_scoff, st->d_small, st->d_small_out, st->d_small_seg, st->d_small_part,
+                st->d_sdesc, st->d_sunit, st->d_resunit_a, st->d_resunit_d};
   for (void* p : ps) cudaFree(p);
   delete st;
   env->split = nullptr;

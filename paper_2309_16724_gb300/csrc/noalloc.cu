@@ -61,6 +61,10 @@ extern "C" int su2_apply_heff_static_scratch(su2_ctx* ctx, const su2_env* env, c
                std::to_string(kScratchDoubles * 8);
     return SU2_EINVAL;
   }
+  if (env->os.on) {
+    ctx->err = "the static-scratch entry point takes environments whose operators are all on the device";
+    return SU2_EINVAL;
+  }
   if (cudaSetDevice(ctx->device) != cudaSuccess) {
     ctx->err = "cudaSetDevice failed";
     return SU2_ECUDA;

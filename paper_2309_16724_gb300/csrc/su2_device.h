@@ -95,11 +95,50 @@ struct Profiler {
   }
 };
 
+// tasks whose four dimensions are all at most kSmallDim run in FP64 on CUDA
+// cores in the split path (the small-task class)
+constexpr int kSmallDim = 16;
+
 void launch_heff_fp64(cudaStream_t s, const double* L, const double* R, const double* psi, double* F, double* T,
                       const K1Job* k1, const K2Job* k2, const K2Task* tasks, const Chunk& c, int64_t psi_len,
                       Profiler* prof);
 void launch_diag(cudaStream_t s, const double* L, const double* R, double* d, const DiagJob* jobs, int64_t njobs,
                  const DiagTask* tasks, int64_t psi_len);
+}  // namespace su2
+
+namespace su2 {
+// Out-of-core operator arenas (Sec. III.E-F).  The operator blocks of both
+// sides share one logical arena laid out by the planner: [0, prefix) is
+// resident on the device (blocks shared by several term chunks, blocks of
+// the diagonal and of the small-task class, then the blocks of the first
+// chunks up to the device budget), the rest lies in pinned host memory with
+// the blocks of each chunk contiguous, [hs[c], he[c]).  Per H.psi the
+// streamed range of chunk c is copied on a dedicated IO stream into device
+// slot c % 2 while other chunks compute; events order each copy after the
+// last reader of its slot and each chunk after its copy.
+struct OpStream {
+  bool on = false;
+  std::vector<int> starts;       // term chunk boundaries (shared by the FP64 and split plans)
+  int64_t prefix = 0;            // doubles resident on the device
+  int64_t total = 0;             // doubles of the logical arena
+  std::vector<int64_t> hs, he;   // streamed range of each chunk (logical offsets)
+  int64_t slot = 0;              // doubles per device slot
+  double* dbuf = nullptr;        // device: [0, prefix) resident, then the two slots
+  double* host = nullptr;        // pinned host memory: logical [prefix, total)
+  cudaStream_t io = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join = nullptr;
+  double io_bytes = 0.0;         // bytes copied per H.psi
+  // the diagonals of the blocks the diagonal of H_eff reads (device, kept):
+  // block b of side sd has its diagonal at ddiag[dg_off[sd][b]] (-1: none)
+  std::vector<int64_t> dg_off[2];
+  int64_t dg_total = 0;
+  double* ddiag = nullptr;
+  // device offset of a block at logical offset `off` read by chunk c
+  int64_t dev_off(int64_t off, int c) const {
+    return off < prefix ? off : prefix + int64_t(c & 1) * slot + (off - hs[size_t(c)]);
+  }
+};
 }  // namespace su2
 
 struct su2_ctx {
@@ -149,5 +188,6 @@ struct su2_env {
   su2::DiagTask* ddt = nullptr;
   double *d_in_scratch = nullptr, *d_out_scratch = nullptr;  // for host-buffer calls
   void* split = nullptr;  // split-precision state (opaque)
+  su2::OpStream os;       // out-of-core operator arenas (os.on)
   su2::Profiler prof;
 };

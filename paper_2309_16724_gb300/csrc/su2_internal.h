@@ -61,10 +61,11 @@ struct OpBlock { int op, qo, qi, rows, cols; int64_t off; };
 // block of a synthetic operator generated on the device (counter-based
 // SplitMix64 entries; HAM = 0.1 (X + X^T) + diag(2r/d); ADJOINT from its base)
 struct GenBlock {
-  int64_t off, base_off;
-  int32_t rows, cols, kind, pad;  // kind: 0 random, 1 HAM, 2 adjoint
-  uint64_t key;
-  double scale;                   // 1/sqrt(max(rows, cols)) or the adjoint factor
+  int64_t off;
+  int32_t rows, cols, kind, base_kind;  // kind: 0 random, 1 HAM, 2 adjoint (of a base block of base_kind)
+  uint64_t key;                         // the block's key (adjoint: its base block's key)
+  double scale;                         // 1/sqrt(max(rows, cols)) or the adjoint factor
+  double base_scale;                    // adjoint: the base block's scale
 };
 
 struct SideOps {

@@ -479,7 +479,7 @@ std::string build_side_ops(const OpTable& t, bool left_side, const std::vector<s
         const double s = 1.0 / std::sqrt(double(std::max(ro, ci)));
         const uint64_t key = block_key(H.seed, side, uint64_t(oid), uint64_t(qo), uint64_t(qi));
         if (!host_values) {
-          out.gen.push_back(GenBlock{out.blocks.back().off, 0, ro, ci, 0, 0, key, s});
+          out.gen.push_back(GenBlock{out.blocks.back().off, ro, ci, 0, 0, key, s, 0.0});
           continue;
         }
         double* m = &out.arena[out.blocks.back().off];
@@ -492,7 +492,7 @@ std::string build_side_ops(const OpTable& t, bool left_side, const std::vector<s
         const double s = 1.0 / std::sqrt(double(d));
         const uint64_t key = block_key(H.seed, side, uint64_t(oid), uint64_t(q), uint64_t(q));
         if (!host_values) {
-          out.gen.push_back(GenBlock{out.blocks.back().off, 0, d, d, 1, 0, key, s});
+          out.gen.push_back(GenBlock{out.blocks.back().off, d, d, 1, 0, key, s, 0.0});
           continue;
         }
         double* m = &out.arena[out.blocks.back().off];
@@ -524,6 +524,8 @@ std::string build_side_ops(const OpTable& t, bool left_side, const std::vector<s
     }
   }
   // adjoint tensors, from their base operators
+  std::unordered_map<int64_t, size_t> gen_at;  // arena offset -> generated block
+  for (size_t g = 0; g < out.gen.size(); ++g) gen_at[out.gen[g].off] = g;
   for (int oid = 0; oid < int(ops.size()); ++oid) {
     const BlockOp& op = ops[oid];
     if (op.kind != OP_ADJOINT) continue;
@@ -537,7 +539,11 @@ std::string build_side_ops(const OpTable& t, bool left_side, const std::vector<s
       const int ro = sec[qi].dim, co = sec[qo].dim;
       add_block(out, oid, qi, qo, ro, co);
       if (!host_values) {
-        out.gen.push_back(GenBlock{out.blocks.back().off, out.blocks[src].off, ro, co, 2, 0, 0, f});
+        // generated from the base block's own entries (no arena read), so
+        // that any range of blocks can be generated on its own
+        const GenBlock& b = out.gen[gen_at.at(out.blocks[src].off)];
+        if (b.kind == 2) return "an adjoint of an adjoint operator";
+        out.gen.push_back(GenBlock{out.blocks.back().off, ro, co, 2, b.kind, b.key, f, b.scale});
         continue;
       }
       double* m = &out.arena[out.blocks.back().off];
