@@ -153,7 +153,9 @@ typedef struct {
                               cudaMemcpyAsync per chunk).  The chunk
                               boundaries then bound both the intermediates
                               and the operator bytes of a chunk by
-                              t_budget_bytes (0: 4 GiB).  With a host
+                              t_budget_bytes (0: a quarter of the free
+                              device memory beside resident_bytes, at most
+                              16 GiB; 4 GiB on a host context).  With a host
                               context only the plan is made (its numbers
                               in su2_env_info; the host arenas take its
                               layout).  The static-scratch entry point and

@@ -439,7 +439,17 @@ static int finish_env(su2_ctx* ctx, su2_env* env, const su2_sectors* S, const su
   int64_t budget = (opts && opts->t_budget_bytes > 0) ? opts->t_budget_bytes : (int64_t(2) << 30);
   std::vector<int64_t> old_off[2];
   if (opts && opts->resident_bytes > 0) {
-    const int64_t sb = opts->t_budget_bytes > 0 ? opts->t_budget_bytes : (int64_t(4) << 30);
+    // chunk budget: a quarter of the device memory left beside the resident
+    // part, at most 16 GiB (the resident path's rule), 4 GiB on a host context
+    int64_t sb = int64_t(4) << 30;
+    if (opts->t_budget_bytes > 0) {
+      sb = opts->t_budget_bytes;
+    } else if (ctx->device >= 0) {
+      size_t fr = 0, tot = 0;
+      if (set_device(ctx) == SU2_OK && cudaMemGetInfo(&fr, &tot) == cudaSuccess)
+        sb = std::min<int64_t>(int64_t(16) << 30,
+                               std::max<int64_t>((int64_t(fr) - opts->resident_bytes) / 4, int64_t(1) << 30));
+    }
     std::string err = stream_plan(env, sb, opts->resident_bytes, old_off);
     if (!err.empty()) {
       cudaFree(env->L.dev_ready);
