@@ -541,7 +541,8 @@ def main():
             oms = float(np.median(ots))
             ofl = oi["flops_su2"]
             ooc = {"workload": ocfg.name, "L": ocfg.L, "N": ocfg.N, "D": ocfg.D,
-                   "operators": "synthetic-entry environments, more than the device memory",
+                   "operators": "synthetic-entry environments; the resident split path would need the FP64 "
+                                "operators and their BF16 slices, about twice the device memory",
                    "operator_gb": oi["env_bytes"] / 1e9, "device_gb": dev_total / 1e9,
                    "resident_gb": oi["resident_bytes"] / 1e9, "streamed_gb_per_step": oi["streamed_bytes"] / 1e9,
                    "term_chunks": oi["n_io_chunks"], "tasks": oi["n_tasks"], "flops_su2_per_step": ofl,
