@@ -314,6 +314,10 @@ def main():
     prec = P.SU2_SPLIT_BF16 if args.prec == "split" else P.SU2_FP64
     ctx = P.Context(local, stream=stream)
     t0 = time.time()
+    wall = {}  # seconds since the start of the bench at the end of each section
+
+    def mark(name):
+        wall[name] = round(time.time() - t0, 1)
     split = prec == P.SU2_SPLIT_BF16
     tune = split and args.slices == 0
     sec, env = workload.build(ctx, cfg, prepare_split=split, n_slices=args.slices,
@@ -411,6 +415,7 @@ def main():
         d.close()
     status_ok("the Davidson steps")
 
+    mark("main_environment_and_timed_sections")
     # the native-FP64 path on the same workload: a term shard (the operator
     # terms dealt to shards in longest-processing-time order of their flops),
     # timed with CUDA events; its rate is the shard's flops over its time.
@@ -455,6 +460,7 @@ def main():
         if senv is not env:
             senv.close()
 
+    mark("fp64_path")
     # the ab initio Hamiltonian of the seeded integrals (Eq. 1): block
     # operators renormalised on the GPU (timed), split and FP64 H.psi, the
     # split error, and the split Davidson energy against the FP64 Rayleigh
@@ -510,6 +516,7 @@ def main():
         except Exception as ex:  # reported, not fatal
             ab = {"workload": args.ab_initio_config, "failed": str(ex)}
 
+    mark("ab_initio")
     # out-of-core operators at the scale configuration: more operator bytes
     # than the device holds; the blocks beyond the resident budget lie in
     # pinned host memory and every H.psi streams them per term chunk
@@ -556,6 +563,7 @@ def main():
         except Exception as ex:  # reported, not fatal
             ooc = {"workload": args.out_of_core_config, "failed": str(ex)}
 
+    mark("out_of_core")
     # roofline of the dominant kernel
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     name, (launches, ms, fl) = dom
@@ -578,6 +586,7 @@ def main():
         except Exception as ex:  # reported, not fatal
             cpu = {"value": None, "unit": "TFLOP/s", "cores": 0, "kind": "oracle", "sample": f"failed: {ex}"}
 
+    mark("cpu_baseline")
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -602,6 +611,7 @@ def main():
             "fp64_path": fp64,
             "ab_initio": ab,
             "out_of_core": ooc,
+            "wall_s": wall,
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                     "steps": e2e_steps},
             "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
