@@ -103,6 +103,25 @@ typedef struct {
                          integrals (ij|kl) (chemists' notation) at
                          ((i L + j) L + k) L + l; read during the call.
                          Other models: both NULL                          */
+  const double* mps_left;   /* SU2_MODEL_AB_INITIO, optional host arrays of the
+                               MPS tensors that grow the left / right block
+                               along its bond chain (NULL: the seeded tensors).
+                               Layout: for each step k = 1 .. n of the chain,
+                               for each sector q of bond k in order, its
+                               tensor as a column-major r0 x d_q matrix.  Its
+                               rows stack the (previous-bond sector p, site
+                               state s) pairs that couple to q, p outer and s
+                               inner (s: empty, one electron, two electrons),
+                               each pair d_p rows; N_p + N_s = N_q and the
+                               spins obey the triangle rule.  The left block
+                               grows by orbital k - 1, the right block by
+                               orbital L - k.  The columns should be
+                               orthonormal (left- resp. right-canonical
+                               blocks): H_eff is then the projection of H onto
+                               the MPS basis; the library does not check it.
+                               Read during the call; the two-site sweep takes
+                               mps_right as its initial right blocks.       */
+  const double* mps_right;
 } su2_hamiltonian;
 
 typedef struct {

@@ -47,7 +47,13 @@ class BondChain(C.Structure):
 
 class Hamiltonian(C.Structure):
     _fields_ = [("model", C.c_int32), ("n_left", C.c_int32), ("n_right", C.c_int32),
-                ("J", C.c_double), ("seed", C.c_uint64), ("h", C.c_void_p), ("eri", C.c_void_p)]
+                ("J", C.c_double), ("seed", C.c_uint64), ("h", C.c_void_p), ("eri", C.c_void_p),
+                ("mps_left", C.c_void_p), ("mps_right", C.c_void_p)]
+
+
+def _mps(a):
+    """A float64 contiguous host copy of concatenated MPS tensors (or None)."""
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64).ravel()
 
 
 class EnvOpts(C.Structure):
@@ -285,7 +291,8 @@ class Environment:
 
     def __init__(self, ctx: Context, sectors: Sectors, model, left_chain, right_chain, n_left=0, n_right=0,
                  J=1.0, seed=0, t_budget_bytes=0, n_slices=0, prepare_split=False, autotune=False,
-                 split_tol=0.0, shard=(0, 0), spin_limit=0, h=None, eri=None, resident_bytes=0):
+                 split_tol=0.0, shard=(0, 0), spin_limit=0, h=None, eri=None, resident_bytes=0,
+                 mps_left=None, mps_right=None):
         self.ctx = ctx
         if model == SU2_MODEL_AB_INITIO:
             L = n_left + 2 + n_right
@@ -295,8 +302,10 @@ class Environment:
             eri = np.ascontiguousarray(eri, dtype=np.float64)
             if h.shape != (L, L) or eri.shape != (L, L, L, L):
                 raise Su2Error(SU2_EINVAL, f"integrals must be ({L}, {L}) and ({L},)*4 arrays")
+        ml, mr = _mps(mps_left), _mps(mps_right)
         H = Hamiltonian(model, n_left, n_right, J, seed, None if h is None else h.ctypes.data,
-                        None if eri is None else eri.ctypes.data)
+                        None if eri is None else eri.ctypes.data, None if ml is None else ml.ctypes.data,
+                        None if mr is None else mr.ctypes.data)
         lc, keep1 = _chain(left_chain)
         rc_, keep2 = _chain(right_chain)
         opts = EnvOpts(t_budget_bytes, n_slices, 1 if prepare_split else 0, 1 if autotune else 0, split_tol,
@@ -433,18 +442,21 @@ class Davidson:
 class Sweep:
     """su2_sweep_create / su2_sweep_run: the two-site sweep of the ab initio
     model (S = 0) on the GPU, starting at window 0 moving right with the right
-    blocks of the seeded MPS of `right_chain` (bonds of 0 .. L-2 orbitals)."""
+    blocks of `right_chain` (bonds of 0 .. L-2 orbitals) grown by the seeded MPS
+    tensors, or by the caller's (`mps_right`, the layout of su2_hamiltonian)."""
 
     def __init__(self, ctx: Context, h, eri, right_chain, N, D, prec=SU2_SPLIT_BF16, tol=1e-8, max_iter=400,
-                 n_slices=5, seed=0, guess_seed=1):
+                 n_slices=5, seed=0, guess_seed=1, mps_right=None):
         self.ctx = ctx
         h = np.ascontiguousarray(h, dtype=np.float64)
         eri = np.ascontiguousarray(eri, dtype=np.float64)
         L = h.shape[0]
         if eri.shape != (L, L, L, L) or len(right_chain) != L - 1:
             raise Su2Error(SU2_EINVAL, "integrals or chain of the wrong size")
-        self._keep = (h, eri)
-        H = Hamiltonian(SU2_MODEL_AB_INITIO, 0, L - 2, 1.0, seed, h.ctypes.data, eri.ctypes.data)
+        mr = _mps(mps_right)
+        self._keep = (h, eri, mr)
+        H = Hamiltonian(SU2_MODEL_AB_INITIO, 0, L - 2, 1.0, seed, h.ctypes.data, eri.ctypes.data, None,
+                        None if mr is None else mr.ctypes.data)
         rc_, keep = _chain(right_chain)
         o = SweepOpts(D, prec, tol, max_iter, n_slices, guess_seed)
         hd = C.c_void_p()

@@ -413,16 +413,36 @@ class Builder {
     int64_t arena_size = 0;
   };
 
-  std::string grow(bool left, const std::vector<std::vector<Sector>>& chain, Side& out) {
+  // the caller's MPS tensors of one step (the layout of su2_hamiltonian's
+  // mps_left / mps_right), read from *pos onwards
+  std::vector<std::vector<double>> step_tensors(const std::vector<Sector>& prev, const std::vector<Sector>& cur,
+                                                const double* mps, size_t* pos) const {
+    std::vector<std::vector<double>> Q(cur.size());
+    for (size_t qo = 0; qo < cur.size(); ++qo) {
+      int64_t r0 = 0;
+      for (const Sector& p : prev)
+        for (int si = 0; si < 3; ++si)
+          if (p.N + sN_[si] == cur[qo].N && triangle(p.twoS, sS_[si], cur[qo].twoS)) r0 += p.dim;
+      const size_t n = size_t(r0) * size_t(cur[qo].dim);
+      Q[qo].assign(mps + *pos, mps + *pos + n);
+      *pos += n;
+    }
+    return Q;
+  }
+
+  std::string grow(bool left, const std::vector<std::vector<Sector>>& chain, Side& out, const double* mps = nullptr) {
     out.own.reset(device_ >= 0 ? make_device_backend(device_, stream_, budget_) : make_host_backend());
     out.be = out.own.get();
     Layout old;
     old.sec = chain[0];
     std::vector<int> orbs;
+    size_t pos = 0;
     for (size_t step = 1; step < chain.size(); ++step) {
       const int s = left ? int(step) - 1 : L_ - int(step);
-      std::string err =
-          step_block(left, int(step), s, chain[step - 1], chain[step], nullptr, orbs, old, *out.be, nullptr, 0, nullptr);
+      std::vector<std::vector<double>> Q;
+      if (mps) Q = step_tensors(chain[step - 1], chain[step], mps, &pos);
+      std::string err = step_block(left, int(step), s, chain[step - 1], chain[step], mps ? &Q : nullptr, orbs, old,
+                                   *out.be, nullptr, 0, nullptr);
       if (!err.empty()) return err;
       if (left) orbs.push_back(s);
       else orbs.insert(orbs.begin(), s);
@@ -1204,8 +1224,8 @@ std::string build_abinitio(const su2_hamiltonian& H, const std::vector<std::vect
   if (H.n_left + 2 + H.n_right > 1000) return "too many orbitals";
   try {
     Builder b(H, device, stream, t_budget_bytes);
-    std::string err = b.grow(true, lchain, b.lside);
-    if (err.empty()) err = b.grow(false, rchain, b.rside);
+    std::string err = b.grow(true, lchain, b.lside, H.mps_left);
+    if (err.empty()) err = b.grow(false, rchain, b.rside, H.mps_right);
     if (err.empty()) err = b.assemble(table, L, R, renorm_flops);
     return err;
   } catch (const std::bad_alloc&) {
@@ -1326,12 +1346,15 @@ SweepBlocks* sweep_init(const su2_hamiltonian& H, const std::vector<std::vector<
     w->Lb.resize(size_t(L - 1));
     w->Rb[0].lay.sec = rchain[0];
     w->Lb[0].lay.sec = std::vector<Sector>{Sector{0, 0, 1}};
+    size_t pos = 0;
     for (int k = 1; k < L - 1; ++k) {
       SweepBlocks::Rec& o = w->Rb[size_t(k - 1)];
       Layout lay = o.lay;
       double* out = nullptr;
-      err = w->b->step_block(false, k, L - k, rchain[size_t(k - 1)], rchain[size_t(k)], nullptr, o.orbs, lay, *w->be,
-                             o.arena, o.size, &out);
+      std::vector<std::vector<double>> Q;
+      if (H.mps_right) Q = w->b->step_tensors(rchain[size_t(k - 1)], rchain[size_t(k)], H.mps_right, &pos);
+      err = w->b->step_block(false, k, L - k, rchain[size_t(k - 1)], rchain[size_t(k)], H.mps_right ? &Q : nullptr,
+                             o.orbs, lay, *w->be, o.arena, o.size, &out);
       if (!err.empty()) break;
       SweepBlocks::Rec& r = w->Rb[size_t(k)];
       r.lay = lay;

@@ -4,6 +4,7 @@
   ground-state energy (native FP64 and split paths).
 * Truncated bonds: the energies of every window equal the oracle's sweep
   (its own SVD, truncation and renormalisation) on the same seeded MPS.
+* Initial right blocks grown by the caller's MPS tensors.
 """
 import numpy as np
 import pytest
@@ -54,3 +55,21 @@ def test_truncated_sweep_matches_oracle(ctx, prec, tol):
     assert np.abs(e - eo).max() < tol, (e, eo)
     wl = w[w > 0]
     assert np.allclose(np.sort(wl), np.sort(wo[wo > 0]), rtol=1e-6, atol=1e-12)
+
+
+def test_sweep_from_caller_right_tensors(ctx):
+    """The sweep's initial right blocks grown by the caller's tensors
+    (random orthonormal, bonds that keep every multiplet): every window's
+    energy is still full CI."""
+    import paper_2309_16724_gb300 as P
+    from test_lib_abinitio import random_tensors
+    cfg = synth.Config("sw6", synth.SPATIAL_ORBITAL, 6, 6, 0, 400, 1002)
+    h, eri = synth.integrals(6, 1002)
+    chain = synth.bond_sector_chain(cfg, cfg.L - 2)
+    _, flat = random_tensors(chain, np.random.default_rng(11))
+    sw = P.Sweep(ctx, h, eri, chain, cfg.N, 400, prec=0, tol=1e-10, seed=cfg.seed, mps_right=flat)
+    e, w = sw.run(2 * (cfg.L - 1))
+    sw.close()
+    assert ctx.status() == 0
+    e0 = fci.spin_levels(h, eri, 6, 0)[0]
+    assert np.abs(e - e0).max() < 1e-9

@@ -132,3 +132,62 @@ def test_every_bond_position_equals_full_ci(hctx, n_left):
     assert np.abs(H - H.T).max() <= 1e-13
     assert abs(np.linalg.eigvalsh(H)[0] - fci.spin_levels(h, eri, N, 0)[0]) <= 1e-12
     env.close()
+
+
+def random_tensors(chain, rng):
+    """Random orthonormal MPS tensors along a bond chain: per step the
+    oracle's {sector: (stacked rows, Q)} and the flat array in the layout of
+    su2_hamiltonian's mps_left / mps_right."""
+    from oracle import sweep as osweep
+    sites = synth.site_states(synth.SPATIAL_ORBITAL)
+    steps, flat = [], []
+    for k in range(1, len(chain)):
+        A = {}
+        for qo, (Nq, Sq, d) in enumerate(chain[k]):
+            rows, r0 = osweep._stacks(chain[k - 1], sites, Nq, Sq)
+            Q, _ = np.linalg.qr(rng.standard_normal((r0, d)))
+            A[qo] = (rows, Q)
+            flat.append(Q.ravel(order="F"))
+        steps.append(A)
+    return steps, np.concatenate(flat)
+
+
+@pytest.mark.parametrize("L,N,twoS,D", [(8, 8, 0, 30), (9, 7, 1, 24)])
+def test_caller_mps_tensors_match_oracle(hctx, L, N, twoS, D):
+    """An environment built from the caller's MPS tensors (random orthonormal
+    Q per step, both blocks) equals the oracle's blocks grown with the same
+    tensors: H.psi through the library's task table and operator blocks
+    against the oracle's H_eff."""
+    import paper_2309_16724_gb300 as P
+    cfg = synth.Config("ab", synth.SPATIAL_ORBITAL, L, N, twoS, D, 1002)
+    h, eri = synth.integrals(L, 1002)
+    rng = np.random.default_rng(5)
+    lch, rch = synth.bond_sector_chain(cfg, cfg.n_left), synth.bond_sector_chain(cfg, cfg.n_right)
+    lsteps, lflat = random_tensors(lch, rng)
+    rsteps, rflat = random_tensors(rch, rng)
+    sec = P.Sectors(hctx, lch[-1], rch[-1], cfg.site_kind, N, twoS)
+    env = P.Environment(hctx, sec, P.SU2_MODEL_AB_INITIO, lch, rch, n_left=cfg.n_left, n_right=cfg.n_right,
+                        seed=1002, h=h, eri=eri, mps_left=lflat, mps_right=rflat)
+    strings = abinitio.hamiltonian_strings(h, eri)
+    Lb, Rb = abinitio.LeftBlock(strings, L), abinitio.RightBlock(strings, L)
+    for k, A in enumerate(lsteps, start=1):
+        Lb = Lb.grown(lch[k], A)
+    for k, A in enumerate(rsteps, start=1):
+        Rb = Rb.grown(rch[k], A)
+    table, oenv, ls, rs = abinitio.problem_from_blocks(strings, Lb, Rb)
+    blocks, n = sectors.build_blocks(ls, rs, cfg.site_kind, N, twoS)
+    assert n == sec.psi_len
+    tasks = heff.build_tasks(table, ls, rs, blocks, twoS)
+    apply = lib_apply(env, sec)
+    for seed in (1, 2):
+        psi = synth.gaussian_psi(n, seed)
+        F = heff.apply_heff(table, oenv, tasks, blocks, n, psi)
+        G = apply(psi)
+        assert np.linalg.norm(G - F) <= 1e-13 * np.linalg.norm(F)
+    # the seeded tensors differ from these: the caller's tensors were used
+    env0 = P.Environment(hctx, sec, P.SU2_MODEL_AB_INITIO, lch, rch, n_left=cfg.n_left, n_right=cfg.n_right,
+                         seed=1002, h=h, eri=eri)
+    psi = synth.gaussian_psi(n, 3)
+    assert np.linalg.norm(lib_apply(env0, sec)(psi) - apply(psi)) > 1e-6 * np.linalg.norm(apply(psi))
+    env.close()
+    env0.close()
