@@ -58,6 +58,17 @@ def k2_traffic(workload, slices, stage_k):
     return float(kv["k2_split_traffic_bytes_per_launch"])
 
 
+def workload_config(cfg):
+    """The workload as both arms name it (the same dict on the library's line
+    and on the oracle's): configuration, sizes, operator source and the L2
+    rule between timed steps."""
+    return {"workload": cfg.name, "L": cfg.L, "N": cfg.N, "twoS": cfg.twoS, "D": cfg.D,
+            "operators": "synthetic-entry environments (ab initio normal/complementary term "
+                         "structure, counter-generated entries)" if cfg.site_kind else
+                         "Heisenberg, renormalised from a seeded MPS",
+            "l2": "flushed between steps (256 MB write)"}
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -260,7 +271,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": cfg.name, "L": cfg.L, "N": cfg.N, "twoS": cfg.twoS, "D": cfg.D},
+        "config": workload_config(cfg),
         "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -593,17 +604,13 @@ def main():
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == P.SU2_FP64 else "bf16",
             "data": "synthetic",
-            "config": {"workload": cfg.name, "L": cfg.L, "N": cfg.N, "twoS": cfg.twoS, "D": cfg.D,
-                       "operators": "synthetic-entry environments (ab initio normal/complementary term "
-                                    "structure, counter-generated entries)" if cfg.site_kind else
-                                    "Heisenberg, renormalised from a seeded MPS",
-                       "prec": "fp64" if prec == P.SU2_FP64 else
-                       "bf16 slices on tcgen05, fp32 accumulate (exact per 192-K chunk), float-float/fp64 recombine",
-                       "psi_len": n, "terms": info["n_terms"], "tasks": info["n_tasks"],
-                       "slices": info["split_slices"] if split else None,
-                       "stage_k16": info["split_stage_k"] if split else None,
-                       "autotuned": tune,
-                       "l2": "flushed between steps (256 MB write)"},
+            "config": workload_config(cfg),
+            "path": {"prec": "fp64" if prec == P.SU2_FP64 else
+                     "bf16 slices on tcgen05, fp32 accumulate (exact per 192-K chunk), float-float/fp64 recombine",
+                     "psi_len": n, "terms": info["n_terms"], "tasks": info["n_tasks"],
+                     "slices": info["split_slices"] if split else None,
+                     "stage_k16": info["split_stage_k"] if split else None,
+                     "autotuned": tune},
             "value_u1_equiv": value * info["r_d"],
             "flops_su2_per_step": flops,
             "rel_err_vs_fp64": rel_err_fp64,

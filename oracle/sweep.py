@@ -18,7 +18,24 @@ Readings (the paper gives no sweep algorithm):
   there), and the bond then holds the Schmidt rank when D exceeds it.
 * Moving right, the left block grows with U (the left singular vectors);
   moving left, the right block grows with V.  Each Davidson starts from a
-  seeded Gaussian vector (no wavefunction prediction: slower, equally exact).
+  seeded Gaussian vector, or, with ``predict``, from the wavefunction
+  predicted from the previous window (below).
+* Wavefunction prediction (the standard DMRG guess; the paper does not spell
+  it out).  Moving right from window i, the kept part of the bond matrix is
+  U_k (U_k^T M): the left factor becomes the grown block, and the rest,
+  C = U_k^T M with columns (right sector b, site s2), is expanded over the
+  right block's own MPS tensor, b = [s3 x r'] (rows (r', s3)), into the
+  blocks (k, s2, s3, r') of window i+1 with j_L1 = j_2R = S_b.  Moving left,
+  C = M V_k is expanded over the left block's tensor, a = [a'' x s0], into
+  the blocks (a'', s0, s1, k) of window i-1 with j_L1 = j_2R = S_a.  At total
+  spin 0 the recoupling (j_k (s2 S_b)_j)_0 -> ((j_k s2)_{S_b} S_b)_0 is the
+  6j {j_k s2 S_b; S_b 0 j_k} times (-1)^(j_k+s2+S_b) sqrt((2 S_b+1)(2 j_k+1)),
+  which is 1 by the closed form of a 6j with a zero entry; no operator is
+  reordered, so there is no fermionic sign.  The predicted vector is the
+  truncated state itself, written in the next window's basis: its norm is
+  sqrt(1 - discarded weight) and its Rayleigh quotient in the next window
+  equals that of the truncated state in the window it came from.  At a turn
+  the next window is the same one and the guess is the previous vector.
 * Sweep order: bonds i = 0 .. L-2 (window sites i, i+1) left to right, then
   L-2 .. 0; the initial right blocks come from the seeded MPS of the bond
   recipe.
@@ -90,10 +107,12 @@ def _truncate(svals, D):
     return keep
 
 
-def isometry(psi, blocks, left, right, site_kind, N, D, side):
+def isometry(psi, blocks, left, right, site_kind, N, D, side, with_rest=False):
     """New bond sectors and MPS tensor of the grown block (side 'L': the left
     block grows by site 1 with U; 'R': the right block grows by site 2 with
-    V), and the discarded weight."""
+    V), and the discarded weight.  With ``with_rest`` also the rest of the
+    kept wavefunction per new sector: side 'L': (column stacks, U_k^T M);
+    side 'R': (row stacks, M V_k)."""
     mats = _bond_matrices(psi, blocks, left, right, site_kind, N)
     svd, svals = {}, {}
     for key, (lrows, rrows, M) in mats.items():
@@ -109,57 +128,129 @@ def isometry(psi, blocks, left, right, site_kind, N, D, side):
         new.append((Nb, j, len(idx), (Nq, j), idx))
     new.sort()
     sec = [(Nb, j, d) for (Nb, j, d, _, _) in new]
-    A = {}
+    A, rest = {}, {}
     for qo, (Nb, j, d, key, idx) in enumerate(new):
-        lrows, rrows, _ = mats[key]
+        lrows, rrows, M = mats[key]
         U, V = svd[key]
         if side == "L":
-            A[qo] = (lrows, U[:, sorted(idx)])
+            Uk = U[:, sorted(idx)]
+            A[qo] = (lrows, Uk)
+            rest[qo] = (rrows, Uk.T @ M)
         else:
-            A[qo] = (rrows, V[:, sorted(idx)])
+            Vk = V[:, sorted(idx)]
+            A[qo] = (rrows, Vk)
+            rest[qo] = (lrows, M @ Vk)
+    if with_rest:
+        return sec, A, dropped, rest
     return sec, A, dropped
 
 
-def _solve(strings, Lb, Rb, N, seed, tol):
+def predict_moving_right(rest, right, RA, next_blocks, next_n):
+    """Start vector of window i+1 after the left block grew at window i:
+    rest = isometry(..., 'L', with_rest=True)[3]; right = the right sectors
+    of window i; RA = the MPS tensor of that right block ({b: (rows
+    [(r', s3, r0, d)], G)}, rows stacked (r', s3))."""
+    out = np.zeros(next_n)
+    bidx = sectors.block_index(next_blocks)
+    for qo, (rrows, C) in rest.items():
+        for (b, s2, c0, db) in rrows:
+            Sb = right[b][1]
+            rows_b, G = RA[b]
+            for (rp, s3, r0, drp) in rows_b:
+                i = bidx[(qo, s2, s3, rp, Sb, Sb)]
+                sectors.block_view(out, next_blocks[i])[:] += C[:, c0:c0 + db] @ G[r0:r0 + drp, :].T
+    return out
+
+
+def predict_moving_left(rest, left, LA, next_blocks, next_n):
+    """Start vector of window i-1 after the right block grew at window i:
+    rest = isometry(..., 'R', with_rest=True)[3]; left = the left sectors of
+    window i; LA = the MPS tensor of that left block ({a: (rows
+    [(a'', s0, r0, d)], G)})."""
+    out = np.zeros(next_n)
+    bidx = sectors.block_index(next_blocks)
+    for qo, (lrows, C) in rest.items():
+        for (a, s1, c0, da) in lrows:
+            Sa = left[a][1]
+            rows_a, G = LA[a]
+            for (app, s0, r0, dapp) in rows_a:
+                i = bidx[(app, s0, s1, qo, Sa, Sa)]
+                sectors.block_view(out, next_blocks[i])[:] += G[r0:r0 + dapp, :] @ C[c0:c0 + da, :]
+    return out
+
+
+def window(strings, Lb, Rb, N):
+    """The two-site problem between blocks Lb and Rb: (apply, diag, blocks,
+    psi length, left sectors, right sectors)."""
     table, env, ls, rs = abinitio.problem_from_blocks(strings, Lb, Rb)
     blocks, n = sectors.build_blocks(ls, rs, synth.SPATIAL_ORBITAL, N, 0)
     tasks = heff.build_tasks(table, ls, rs, blocks, 0)
     apply = lambda v: heff.apply_heff(table, env, tasks, blocks, n, v)
     diag = heff.diag_heff(table, env, tasks, blocks, n)
-    theta, x, res, it = davidson.davidson(apply, diag, synth.gaussian_psi(n, seed), tol=tol)
-    return theta, x, blocks, ls, rs
+    return apply, diag, blocks, n, ls, rs
 
 
-def sweep(cfg, D, n_half, tol=1e-9, h=None, eri=None):
+def _solve(strings, Lb, Rb, N, seed, tol, x0=None):
+    apply, diag, blocks, n, ls, rs = window(strings, Lb, Rb, N)
+    if x0 is None or not np.linalg.norm(x0) > 0:
+        x0 = synth.gaussian_psi(n, seed)
+    rq0 = float(x0 @ apply(x0) / (x0 @ x0))
+    theta, x, res, it = davidson.davidson(apply, diag, x0, tol=tol)
+    return theta, x, blocks, ls, rs, it, rq0
+
+
+def sweep(cfg, D, n_half, tol=1e-9, h=None, eri=None, predict=False, stats=None):
     """Energies of every two-site step of n_half half-sweeps (S = 0), with the
     initial right blocks from cfg's seeded MPS; returns (energies, discarded
-    weights)."""
+    weights).  With ``predict`` every window after the first starts from the
+    wavefunction predicted from the previous one.  A list ``stats`` receives
+    (Davidson iterations, Rayleigh quotient of the start vector) per step."""
     assert cfg.twoS == 0 and cfg.site_kind == synth.SPATIAL_ORBITAL
     if h is None:
         h, eri = synth.integrals(cfg.L, cfg.seed)
     strings = abinitio.hamiltonian_strings(h, eri)
     L, N = cfg.L, cfg.N
     chain = synth.bond_sector_chain(cfg, L - 2)
+    # R[m]: right block of the last m orbitals; RA[m] / LA[m]: the MPS tensor
+    # that grew R[m] from R[m-1] / Lbs[m] from Lbs[m-1]
     R = [abinitio.RightBlock(strings, L)]
+    RA = [None] * (L - 1)
     for k in range(1, L - 1):
         A = envmod.mps_tensor(cfg.seed, envmod.SIDE_MPS_R, k, chain[k - 1], chain[k], synth.SPATIAL_ORBITAL)
         R.append(R[-1].grown(chain[k], A))
+        RA[k] = A
     Lbs = [abinitio.LeftBlock(strings, L)] + [None] * (L - 2)
+    LA = [None] * (L - 1)
     energies, discarded = [], []
     step = 0
+    guess = None
     for half in range(n_half):
         order = range(0, L - 1) if half % 2 == 0 else range(L - 2, -1, -1)
         for i in order:
             Lb, Rb = Lbs[i], R[L - 2 - i]
-            theta, x, blocks, ls, rs = _solve(strings, Lb, Rb, N, cfg.seed + 1000 + step, tol)
+            theta, x, blocks, ls, rs, it, rq0 = _solve(strings, Lb, Rb, N, cfg.seed + 1000 + step, tol,
+                                                       guess if predict else None)
+            if stats is not None:
+                stats.append((it, rq0))
             step += 1
             energies.append(theta)
+            guess = x   # at a turn the next window is this one
             if half % 2 == 0 and i < L - 2:
-                sec, A, w = isometry(x, blocks, ls, rs, synth.SPATIAL_ORBITAL, N, D, "L")
+                sec, A, w, rest = isometry(x, blocks, ls, rs, synth.SPATIAL_ORBITAL, N, D, "L", with_rest=True)
                 Lbs[i + 1] = Lb.grown(sec, A)
+                LA[i + 1] = A
                 discarded.append(w)
+                if predict:
+                    nb, nn = sectors.build_blocks(Lbs[i + 1].sectors, R[L - 3 - i].sectors,
+                                                  synth.SPATIAL_ORBITAL, N, 0)
+                    guess = predict_moving_right(rest, rs, RA[L - 2 - i], nb, nn)
             elif half % 2 == 1 and i > 0:
-                sec, A, w = isometry(x, blocks, ls, rs, synth.SPATIAL_ORBITAL, N, D, "R")
+                sec, A, w, rest = isometry(x, blocks, ls, rs, synth.SPATIAL_ORBITAL, N, D, "R", with_rest=True)
                 R[L - 1 - i] = Rb.grown(sec, A)
+                RA[L - 1 - i] = A
                 discarded.append(w)
+                if predict:
+                    nb, nn = sectors.build_blocks(Lbs[i - 1].sectors, R[L - 1 - i].sectors,
+                                                  synth.SPATIAL_ORBITAL, N, 0)
+                    guess = predict_moving_left(rest, ls, LA[i], nb, nn)
     return np.array(energies), np.array(discarded)

@@ -8,6 +8,11 @@
 * The SVD isometries: kept columns are orthonormal, the kept sectors hold at
   most D multiplets, and with D large enough nothing is discarded and the
   bond matrices are reproduced.
+* Wavefunction prediction: the predicted start vector of the next window is
+  the truncated state written in that window's basis (its norm and its
+  Rayleigh quotient are those of the truncated state, for any vector and
+  any truncation); with exact bonds it is the converged eigenvector; a
+  right block expanded with a wrong tensor breaks the identity.
 """
 import numpy as np
 
@@ -59,3 +64,153 @@ def test_isometry_orthonormal_and_truncated():
         rows, U = A[qo]
         M = mats[(Nb, j)][2]
         assert np.allclose(U @ (U.T @ M), M, atol=1e-12)
+
+
+# ---------------------------------------------------------------- wavefunction prediction
+# The predicted start vector of the next window is the truncated state of
+# the previous one written in the next window's basis, so (for any vector,
+# converged or not) its squared norm is 1 - discarded weight and its
+# Rayleigh quotient in the next window equals that of the truncated state in
+# the window it came from.  Both windows' H_eff are projections P^T H P of
+# the same Hamiltonian onto spaces that contain that state.
+
+def _from_bond_matrices(mats, blocks, n):
+    """Inverse of the bond-matrix view: {(N_L1, j): (left stacks, right
+    stacks, M)} back into the flat two-site vector."""
+    out = np.zeros(n)
+    bidx = sectors.block_index(blocks)
+    for (Nq, j), (lrows, rrows, M) in mats.items():
+        for (a, s1, r0, da) in lrows:
+            for (b, s2, c0, db) in rrows:
+                sectors.block_view(out, blocks[bidx[(a, s1, s2, b, j, j)]])[:] = M[r0:r0 + da, c0:c0 + db]
+    return out
+
+
+def _truncated(psi, blocks, n, ls, rs, N, sec, A, rest, side):
+    mats = sweep._bond_matrices(psi, blocks, ls, rs, synth.SPATIAL_ORBITAL, N)
+    kept = {}
+    for qo, (Nb, j, d) in enumerate(sec):
+        key = (Nb, j) if side == "L" else (N - Nb, j)
+        lrows, rrows, M = mats[key]
+        Q, C = A[qo][1], rest[qo][1]
+        kept[key] = (lrows, rrows, Q @ C if side == "L" else C @ Q.T)
+    for key, (lrows, rrows, M) in mats.items():
+        if key not in kept:
+            kept[key] = (lrows, rrows, np.zeros_like(M))
+    return _from_bond_matrices(kept, blocks, n)
+
+
+def _rq(apply, v):
+    return float(v @ apply(v) / (v @ v))
+
+
+def _prediction_chain(L, N, D, seed, plant=None):
+    """Walks windows 0 .. L-2 moving right and back moving left with seeded
+    (unconverged) vectors, growing blocks with the truncated isometries;
+    returns per transition (|guess|^2, 1 - w, RQ of the guess in the next
+    window, RQ of the truncated state in its own window)."""
+    from oracle import abinitio
+    from oracle import env as envmod
+    cfg = synth.Config("pred", synth.SPATIAL_ORBITAL, L, N, 0, D, seed)
+    h, eri = synth.integrals(L, seed)
+    strings = abinitio.hamiltonian_strings(h, eri)
+    chain = synth.bond_sector_chain(cfg, L - 2)
+    R, RA = [abinitio.RightBlock(strings, L)], [None] * (L - 1)
+    for k in range(1, L - 1):
+        RA[k] = envmod.mps_tensor(seed, envmod.SIDE_MPS_R, k, chain[k - 1], chain[k], synth.SPATIAL_ORBITAL)
+        R.append(R[-1].grown(chain[k], RA[k]))
+    Lbs, LA = [abinitio.LeftBlock(strings, L)] + [None] * (L - 2), [None] * (L - 1)
+    out = []
+    for i in range(0, L - 2):
+        apply, _, blocks, n, ls, rs = sweep.window(strings, Lbs[i], R[L - 2 - i], N)
+        psi = synth.gaussian_psi(n, 50 + i)
+        sec, A, w, rest = sweep.isometry(psi, blocks, ls, rs, synth.SPATIAL_ORBITAL, N, D, "L", with_rest=True)
+        Lbs[i + 1] = Lbs[i].grown(sec, A)
+        LA[i + 1] = A
+        apply2, _, nb, nn, _, _ = sweep.window(strings, Lbs[i + 1], R[L - 3 - i], N)
+        RAi = RA[L - 2 - i] if plant is None else plant(RA[L - 2 - i])
+        g = sweep.predict_moving_right(rest, rs, RAi, nb, nn)
+        t = _truncated(psi, blocks, n, ls, rs, N, sec, A, rest, "L")
+        out.append((g @ g, 1.0 - w, _rq(apply2, g), _rq(apply, t)))
+    for i in range(L - 2, 0, -1):
+        apply, _, blocks, n, ls, rs = sweep.window(strings, Lbs[i], R[L - 2 - i], N)
+        psi = synth.gaussian_psi(n, 80 + i)
+        sec, A, w, rest = sweep.isometry(psi, blocks, ls, rs, synth.SPATIAL_ORBITAL, N, D, "R", with_rest=True)
+        R[L - 1 - i] = R[L - 2 - i].grown(sec, A)
+        RA[L - 1 - i] = A
+        apply2, _, nb, nn, _, _ = sweep.window(strings, Lbs[i - 1], R[L - 1 - i], N)
+        g = sweep.predict_moving_left(rest, ls, LA[i], nb, nn)
+        t = _truncated(psi, blocks, n, ls, rs, N, sec, A, rest, "R")
+        out.append((g @ g, 1.0 - w, _rq(apply2, g), _rq(apply, t)))
+    return out
+
+
+def test_prediction_is_the_truncated_state_in_the_next_window():
+    # D = 5 truncates every inner bond of the seven-orbital chain
+    res = _prediction_chain(7, 6, 5, 1003)
+    assert len(res) == 2 * 5
+    assert max(1.0 - w for (_, w, _, _) in res) > 1e-3     # weight was discarded
+    for (g2, w, e_next, e_trunc) in res:
+        assert abs(g2 - w) <= 1e-12
+        assert abs(e_next - e_trunc) <= 1e-11 * abs(e_trunc)
+
+
+def test_prediction_with_a_wrong_right_tensor_fails():
+    # a planted mistake: the right block expanded with its tensor's columns
+    # in the wrong order (still an isometry, a different state)
+    def swap(RA):
+        out = {}
+        for b, (rows, G) in RA.items():
+            out[b] = (rows, G[:, ::-1].copy())
+        return out
+    res = _prediction_chain(6, 6, 5, 1003, plant=swap)
+    assert max(abs(e - t) for (_, _, e, t) in res[:4]) > 1e-4
+
+
+def test_prediction_with_exact_bonds_is_an_eigenvector():
+    # bonds keep every multiplet: the converged vector of window 1, predicted
+    # into window 2, is the same eigenstate
+    from oracle import abinitio, davidson
+    from oracle import env as envmod
+    L, N, seed = 6, 6, 1002
+    cfg = synth.Config("sw6", synth.SPATIAL_ORBITAL, L, N, 0, 400, seed)
+    h, eri = synth.integrals(L, seed)
+    strings = abinitio.hamiltonian_strings(h, eri)
+    chain = synth.bond_sector_chain(cfg, L - 2)
+    R, RA = [abinitio.RightBlock(strings, L)], [None] * (L - 1)
+    for k in range(1, L - 1):
+        RA[k] = envmod.mps_tensor(seed, envmod.SIDE_MPS_R, k, chain[k - 1], chain[k], synth.SPATIAL_ORBITAL)
+        R.append(R[-1].grown(chain[k], RA[k]))
+    Lb = abinitio.LeftBlock(strings, L)
+    apply, diag, blocks, n, ls, rs = sweep.window(strings, Lb, R[L - 2], N)
+    theta, x, res, _ = davidson.davidson(apply, diag, synth.gaussian_psi(n, 3), tol=1e-11)
+    sec, A, w, rest = sweep.isometry(x, blocks, ls, rs, synth.SPATIAL_ORBITAL, N, 400, "L", with_rest=True)
+    assert abs(w) < 1e-20
+    Lb1 = Lb.grown(sec, A)
+    apply2, _, nb, nn, _, _ = sweep.window(strings, Lb1, R[L - 3], N)
+    g = sweep.predict_moving_right(rest, rs, RA[L - 2], nb, nn)
+    assert abs(np.linalg.norm(g) - 1.0) < 1e-12
+    assert np.linalg.norm(apply2(g) - theta * g) < 1e-9
+    assert abs(theta - fci.spin_levels(h, eri, N, 0)[0]) < 1e-9
+
+
+def test_predicted_sweep_same_energies_fewer_iterations():
+    # exact bonds: after the first window every predicted start vector is the
+    # converged eigenvector, so Davidson stops after its first iteration
+    cfg = synth.Config("sw6", synth.SPATIAL_ORBITAL, 6, 6, 0, 400, 1002)
+    st = []
+    E, w = sweep.sweep(cfg, 400, 2, predict=True, stats=st)
+    h, eri = synth.integrals(6, 1002)
+    assert np.abs(E - fci.spin_levels(h, eri, 6, 0)[0]).max() < 1e-9
+    assert st[0][0] > 10 and all(it == 1 for (it, _) in st[1:])
+    # truncated bonds: the same energies and discarded weights as the sweep
+    # from seeded start vectors, in fewer iterations
+    cfg = synth.Config("sw7", synth.SPATIAL_ORBITAL, 7, 6, 0, 6, 1002)
+    s0, s1 = [], []
+    E0, w0 = sweep.sweep(cfg, 6, 2, stats=s0)
+    E1, w1 = sweep.sweep(cfg, 6, 2, predict=True, stats=s1)
+    assert np.abs(E1 - E0).max() < 1e-8
+    assert np.abs(w1 - w0).max() < 1e-8
+    assert sum(s[0] for s in s1) < sum(s[0] for s in s0)
+    # the turn's start vector is the previous window's eigenvector
+    assert s1[cfg.L - 1][0] == 1
