@@ -356,8 +356,12 @@ int su2_davidson_destroy(su2_dav* dav);
  * singular vectors (renormalisation on the device, Sec. IV.D).  The sweep
  * starts at window 0 moving right with the right blocks of a seeded MPS
  * (right_chain: the bonds of 0 .. L-2 orbitals, L = n_left + 2 + n_right)
- * and turns at the ends; every window's Davidson starts from a seeded vector
- * (no wavefunction prediction).  Device contexts only. */
+ * and turns at the ends.  The first window's Davidson starts from a seeded
+ * vector; with `predict` every later window starts from the wavefunction
+ * predicted from the previous one (the kept part of its bond matrix expanded
+ * over the adjacent block's MPS tensor: the truncated state written in the
+ * next window's basis; at a turn, the previous eigenvector), else from a
+ * seeded vector too.  Device contexts only. */
 typedef struct su2_sweep su2_sweep;
 typedef struct {
   int32_t D;             /* multiplets kept per bond                        */
@@ -366,13 +370,17 @@ typedef struct {
   int32_t max_iter;      /* Davidson iterations per window (0: 400)         */
   int32_t n_slices;      /* BF16 slices of the split path (0: 5)            */
   uint64_t guess_seed;   /* seed of the Davidson start vectors              */
+  int32_t predict;       /* 1: start each window from the predicted vector  */
 } su2_sweep_opts;
 int su2_sweep_create(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond_chain* right_chain, int32_t N,
                      const su2_sweep_opts* opts, su2_sweep** out);
 /* Runs n_steps windows; energies[k] is the Davidson energy of the k-th
  * window run, discarded[k] the weight (sum of sigma^2) dropped by its
- * truncation (0 at a turn); either may be NULL. */
-int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies, double* discarded);
+ * truncation (0 at a turn), iterations[k] its Davidson iterations and
+ * start_energies[k] the Rayleigh quotient of its start vector (the first
+ * iteration's Ritz value); any of the four may be NULL. */
+int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies, double* discarded,
+                  int32_t* iterations, double* start_energies);
 int su2_sweep_destroy(su2_sweep* sw);
 
 /* Group order of the paper's hash-based semi-dynamic scheduling (Sec.

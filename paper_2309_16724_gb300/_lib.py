@@ -74,7 +74,7 @@ class EnvInfo(C.Structure):
 
 class SweepOpts(C.Structure):
     _fields_ = [("D", C.c_int32), ("prec", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
-                ("n_slices", C.c_int32), ("guess_seed", C.c_uint64)]
+                ("n_slices", C.c_int32), ("guess_seed", C.c_uint64), ("predict", C.c_int32)]
 
 
 class DavOpts(C.Structure):
@@ -129,7 +129,7 @@ def lib():
         L.su2_hash_group.argtypes = [C.c_int32, C.c_int32, C.c_int64, C.c_int64, C.POINTER(C.c_int64)]
         L.su2_sweep_create.argtypes = [vp, C.POINTER(Hamiltonian), C.POINTER(BondChain), C.c_int32,
                                        C.POINTER(SweepOpts), C.POINTER(vp)]
-        L.su2_sweep_run.argtypes = [vp, vp, C.c_int32, vp, vp]
+        L.su2_sweep_run.argtypes = [vp, vp, C.c_int32, vp, vp, vp, vp]
         L.su2_sweep_destroy.argtypes = [vp]
         for name in SYMBOLS:
             if name != "su2_last_error":
@@ -446,7 +446,7 @@ class Sweep:
     tensors, or by the caller's (`mps_right`, the layout of su2_hamiltonian)."""
 
     def __init__(self, ctx: Context, h, eri, right_chain, N, D, prec=SU2_SPLIT_BF16, tol=1e-8, max_iter=400,
-                 n_slices=5, seed=0, guess_seed=1, mps_right=None):
+                 n_slices=5, seed=0, guess_seed=1, mps_right=None, predict=False):
         self.ctx = ctx
         h = np.ascontiguousarray(h, dtype=np.float64)
         eri = np.ascontiguousarray(eri, dtype=np.float64)
@@ -458,18 +458,23 @@ class Sweep:
         H = Hamiltonian(SU2_MODEL_AB_INITIO, 0, L - 2, 1.0, seed, h.ctypes.data, eri.ctypes.data, None,
                         None if mr is None else mr.ctypes.data)
         rc_, keep = _chain(right_chain)
-        o = SweepOpts(D, prec, tol, max_iter, n_slices, guess_seed)
+        o = SweepOpts(D, prec, tol, max_iter, n_slices, guess_seed, 1 if predict else 0)
         hd = C.c_void_p()
         ctx.check(lib().su2_sweep_create(ctx.h, C.byref(H), C.byref(rc_), N, C.byref(o), C.byref(hd)))
         self.h = hd
         self.L = L
 
-    def run(self, n_steps):
-        """(energies, discarded weights) of the next n_steps windows."""
+    def run(self, n_steps, stats=False):
+        """(energies, discarded weights) of the next n_steps windows; with
+        `stats` also their Davidson iterations and the Rayleigh quotients of
+        their start vectors."""
         e = np.zeros(n_steps)
         w = np.zeros(n_steps)
-        self.ctx.check(lib().su2_sweep_run(self.ctx.h, self.h, n_steps, e.ctypes.data, w.ctypes.data))
-        return e, w
+        it = np.zeros(n_steps, dtype=np.int32)
+        e0 = np.zeros(n_steps)
+        self.ctx.check(lib().su2_sweep_run(self.ctx.h, self.h, n_steps, e.ctypes.data, w.ctypes.data,
+                                           it.ctypes.data, e0.ctypes.data))
+        return (e, w, it, e0) if stats else (e, w)
 
     def close(self):
         if self.h:

@@ -1149,6 +1149,7 @@ struct su2_sweep {
   su2_sweep_opts o{};
   int pos = 0, dir = 1;  // next window and direction
   int64_t steps = 0;
+  std::vector<double> guess;  // predicted start vector of the next window (empty: seeded)
 };
 
 extern "C" {
@@ -1192,7 +1193,8 @@ int su2_sweep_create(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond_chai
   return SU2_OK;
 }
 
-int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies, double* discarded) {
+int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies, double* discarded,
+                  int32_t* iterations, double* start_energies) {
   if (!ctx || !sw || sw->ctx != ctx || n_steps < 0) return fail(ctx, SU2_EINVAL, "null argument");
   int rc = set_device(ctx);
   if (rc) return rc;
@@ -1228,11 +1230,19 @@ int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies
     eo.n_slices = sw->o.n_slices;
     rc = finish_env(ctx, env, &S, &eo);
     if (rc) return rc;
-    // Davidson from a seeded start vector
+    // Davidson from the predicted start vector, else from a seeded one
     const int64_t n = S.psi_len;
     std::vector<double> h(static_cast<size_t>(n));
-    const uint64_t key = block_key(sw->o.guess_seed, 9, uint64_t(sw->steps), 0, 0);
-    for (int64_t x = 0; x < n; ++x) h[size_t(x)] = uniform_elem(key, uint64_t(x));
+    double gn = 0.0;
+    if (sw->o.predict && int64_t(sw->guess.size()) == n)
+      for (double v : sw->guess) gn += v * v;
+    if (gn > 0.0) {
+      h.swap(sw->guess);
+    } else {
+      const uint64_t key = block_key(sw->o.guess_seed, 9, uint64_t(sw->steps), 0, 0);
+      for (int64_t x = 0; x < n; ++x) h[size_t(x)] = uniform_elem(key, uint64_t(x));
+    }
+    sw->guess.clear();
     double* d0 = nullptr;
     double* dx = nullptr;
     rc = dev_alloc(ctx, &d0, size_t(n));
@@ -1240,12 +1250,14 @@ int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies
     if (!rc && cudaMemcpy(d0, h.data(), size_t(n) * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
       rc = fail(ctx, SU2_ECUDA, "upload");
     su2_dav* dav = nullptr;
-    double theta = 0.0, res = 0.0;
+    double theta = 0.0, res = 0.0, theta0 = 0.0;
     int32_t its = 0;
     if (!rc) {
       su2_dav_opts dop{sw->o.tol, 24, 2, sw->o.max_iter, sw->o.prec, 0};
       rc = su2_davidson_create(ctx, env, d0, &dop, &dav);
     }
+    // the first iteration's Ritz value is the Rayleigh quotient of the start vector
+    if (!rc) rc = su2_davidson_step(ctx, dav, &theta0, &res);
     if (!rc) {
       rc = su2_davidson_solve(ctx, dav, &theta, &res, &its);
       if (rc == SU2_ENOTCONV) rc = SU2_OK;  // the energy of the last iterate is reported
@@ -1260,15 +1272,23 @@ int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies
     delete env;
     if (rc) return rc;
     if (energies) energies[k] = theta;
-    // truncate and grow the block on the side the sweep moves to
+    if (iterations) iterations[k] = its;
+    if (start_energies) start_energies[k] = theta0;
+    // truncate and grow the block on the side the sweep moves to; predict
+    // the next window's start vector (at a turn the next window is this one)
     double w = 0.0;
     const bool grow = sw->dir > 0 ? i < L - 2 : i > 0;
     if (grow) {
       std::vector<Sector> cur;
-      std::vector<std::vector<double>> Q;
-      err = sweep_split(S.blocks, h.data(), S.left, S.right, sw->N, sw->o.D, sw->dir > 0, cur, Q, &w);
+      std::vector<std::vector<double>> Q, rest;
+      err = sweep_split(S.blocks, h.data(), S.left, S.right, sw->N, sw->o.D, sw->dir > 0, cur, Q, &w,
+                        sw->o.predict ? &rest : nullptr);
       if (err.empty()) err = sweep_grow(sw->w, i, sw->dir > 0, cur, Q);
+      if (err.empty() && sw->o.predict)
+        err = sweep_predict(sw->w, i, sw->dir > 0, S.left, S.right, sw->N, cur, rest, sw->guess);
       if (!err.empty()) return fail(ctx, SU2_EINVAL, err);
+    } else if (sw->o.predict) {
+      sw->guess = h;
     }
     if (discarded) discarded[k] = w;
     sw->steps += 1;

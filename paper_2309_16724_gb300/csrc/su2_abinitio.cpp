@@ -430,6 +430,32 @@ class Builder {
     return Q;
   }
 
+  // the seeded MPS tensor of sector qo at growth step `step` (side 2: left,
+  // 3: right): the Q factor of a counter-generated r0 x d matrix
+  std::vector<double> seeded_tensor(uint64_t side, int step, int qo, int r0, int d) const {
+    std::vector<double> G(size_t(r0) * d);
+    const uint64_t key = block_key(H_.seed, side, uint64_t(step), uint64_t(qo), 0);
+    for (int c = 0; c < d; ++c)
+      for (int r = 0; r < r0; ++r) G[size_t(r) + size_t(c) * r0] = uniform_elem(key, uint64_t(r) + uint64_t(c) * r0);
+    orthonormalize(G, r0, d);
+    return G;
+  }
+
+  // the seeded MPS tensors of one step (per new sector, stacked rows x dim)
+  std::vector<std::vector<double>> seeded_tensors(bool left, int step, const std::vector<Sector>& prev,
+                                                  const std::vector<Sector>& cur) const {
+    std::vector<std::vector<double>> Q(cur.size());
+    for (size_t qo = 0; qo < cur.size(); ++qo) {
+      int r0 = 0;
+      for (const Sector& p : prev)
+        for (int si = 0; si < 3; ++si)
+          if (p.N + sN_[si] == cur[qo].N && triangle(p.twoS, sS_[si], cur[qo].twoS)) r0 += p.dim;
+      if (r0 < cur[qo].dim) return {};
+      Q[qo] = seeded_tensor(left ? 2 : 3, step, int(qo), r0, cur[qo].dim);
+    }
+    return Q;
+  }
+
   std::string grow(bool left, const std::vector<std::vector<Sector>>& chain, Side& out, const double* mps = nullptr) {
     out.own.reset(device_ >= 0 ? make_device_backend(device_, stream_, budget_) : make_host_backend());
     out.be = out.own.get();
@@ -501,10 +527,7 @@ class Builder {
         if ((*Qin)[size_t(qo)].size() != G.size()) return "MPS tensor does not match the stacked rows of its sector";
         G = (*Qin)[size_t(qo)];
       } else {
-        const uint64_t key = block_key(H_.seed, side, uint64_t(step), uint64_t(qo), 0);
-        for (int c = 0; c < d; ++c)
-          for (int r = 0; r < r0; ++r) G[size_t(r) + size_t(c) * r0] = uniform_elem(key, uint64_t(r) + uint64_t(c) * r0);
-        orthonormalize(G, r0, d);
+        G = seeded_tensor(side, step, qo, r0, d);
       }
       qoff[qo] = int64_t(st.q.size());
       // Q^T (d x r0), column-major
@@ -1248,6 +1271,10 @@ struct SweepBlocks {
   std::unique_ptr<Builder> b;
   std::unique_ptr<RenormBackend> be;
   std::vector<Rec> Lb, Rb;
+  // the MPS tensor that grew Lb[k] from Lb[k-1] (Rb[k] from Rb[k-1]): per
+  // sector of the new bond, its stacked rows (previous sector, site state) x
+  // dim, column-major; read by the wavefunction prediction
+  std::vector<std::vector<std::vector<double>>> Lq, Rq;
   int L = 0, device = 0;
   ~SweepBlocks() {
     if (device >= 0) cudaSetDevice(device);
@@ -1344,6 +1371,8 @@ SweepBlocks* sweep_init(const su2_hamiltonian& H, const std::vector<std::vector<
     w->be.reset(make_device_backend(device, stream, budget));
     w->Rb.resize(size_t(L - 1));
     w->Lb.resize(size_t(L - 1));
+    w->Rq.resize(size_t(L - 1));
+    w->Lq.resize(size_t(L - 1));
     w->Rb[0].lay.sec = rchain[0];
     w->Lb[0].lay.sec = std::vector<Sector>{Sector{0, 0, 1}};
     size_t pos = 0;
@@ -1353,9 +1382,15 @@ SweepBlocks* sweep_init(const su2_hamiltonian& H, const std::vector<std::vector<
       double* out = nullptr;
       std::vector<std::vector<double>> Q;
       if (H.mps_right) Q = w->b->step_tensors(rchain[size_t(k - 1)], rchain[size_t(k)], H.mps_right, &pos);
-      err = w->b->step_block(false, k, L - k, rchain[size_t(k - 1)], rchain[size_t(k)], H.mps_right ? &Q : nullptr,
-                             o.orbs, lay, *w->be, o.arena, o.size, &out);
+      else Q = w->b->seeded_tensors(false, k, rchain[size_t(k - 1)], rchain[size_t(k)]);
+      if (Q.size() != rchain[size_t(k)].size()) {
+        err = "bond dimension exceeds the states available from the previous bond";
+        break;
+      }
+      err = w->b->step_block(false, k, L - k, rchain[size_t(k - 1)], rchain[size_t(k)], &Q, o.orbs, lay, *w->be,
+                             o.arena, o.size, &out);
       if (!err.empty()) break;
+      w->Rq[size_t(k)] = std::move(Q);
       SweepBlocks::Rec& r = w->Rb[size_t(k)];
       r.lay = lay;
       r.orbs = o.orbs;
@@ -1405,7 +1440,8 @@ std::string sweep_env(SweepBlocks* w, int i, OpTable& table, SideOps& Lops, Side
 
 std::string sweep_split(const std::vector<Block>& blocks, const double* psi, const std::vector<Sector>& lsec,
                         const std::vector<Sector>& rsec, int N, int D, bool left, std::vector<Sector>& new_sec,
-                        std::vector<std::vector<double>>& Q, double* discarded) {
+                        std::vector<std::vector<double>>& Q, double* discarded,
+                        std::vector<std::vector<double>>* rest) {
   std::vector<int> sN, sS;
   site_states(SU2_SITE_ORBITAL, sN, sS);
   struct Stk {
@@ -1434,8 +1470,8 @@ std::string sweep_split(const std::vector<Block>& blocks, const double* psi, con
   }
   struct Sec {
     int Nq, j;
-    std::vector<double> U, sv;
-    int rows;
+    std::vector<double> U, sv, M;  // M: the bond matrix (nr x nc, column-major)
+    int rows, nr, nc;
   };
   std::vector<Sec> all;
   double total = 0.0;
@@ -1457,6 +1493,8 @@ std::string sweep_split(const std::vector<Block>& blocks, const double* psi, con
     Sec sc;
     sc.Nq = Nq;
     sc.j = j;
+    sc.nr = nr;
+    sc.nc = nc;
     if (left) {
       svd_left(nr, nc, M, sc.U, sc.sv);
       sc.rows = nr;
@@ -1468,6 +1506,7 @@ std::string sweep_split(const std::vector<Block>& blocks, const double* psi, con
       sc.rows = nc;
     }
     for (double x : sc.sv) total += x * x;
+    if (rest) sc.M = std::move(M);
     all.push_back(std::move(sc));
   }
   // keep the D largest sigma^2; ties to the lower (N, 2S) sector, then the lower index
@@ -1509,12 +1548,37 @@ std::string sweep_split(const std::vector<Block>& blocks, const double* psi, con
   std::sort(order.begin(), order.end());
   new_sec.clear();
   Q.clear();
+  if (rest) rest->clear();
   for (const auto& o : order) {
     const Sec& sc = all[size_t(o.second)];
     const int d = nkeep[o.second];  // the d largest of this sector (descending order)
     new_sec.push_back(Sector{o.first.first, o.first.second, d});
     Q.emplace_back(sc.U.begin(), sc.U.begin() + size_t(sc.rows) * d);
     orthonormalize(Q.back(), sc.rows, d);  // removes the rounding of the rotations (the columns are already orthonormal to ~1e-15)
+    if (!rest) continue;
+    // the rest of the kept wavefunction: Q^T M (d x nc) moving right, M Q
+    // (nr x d) moving left, column-major
+    const std::vector<double>& q = Q.back();
+    const int nr = sc.nr, nc = sc.nc;
+    std::vector<double> C;
+    if (left) {
+      C.assign(size_t(d) * nc, 0.0);
+      for (int c = 0; c < nc; ++c)
+        for (int k = 0; k < d; ++k) {
+          double acc = 0.0;
+          for (int r = 0; r < nr; ++r) acc += q[size_t(r) + size_t(k) * nr] * sc.M[size_t(r) + size_t(c) * nr];
+          C[size_t(k) + size_t(c) * d] = acc;
+        }
+    } else {
+      C.assign(size_t(nr) * d, 0.0);
+      for (int k = 0; k < d; ++k)
+        for (int c = 0; c < nc; ++c) {
+          const double qv = q[size_t(c) + size_t(k) * nc];
+          if (qv == 0.0) continue;
+          for (int r = 0; r < nr; ++r) C[size_t(r) + size_t(k) * nr] += sc.M[size_t(r) + size_t(c) * nr] * qv;
+        }
+    }
+    rest->push_back(std::move(C));
   }
   if (discarded) *discarded = dropped;
   return new_sec.empty() ? "the wavefunction is zero" : "";
@@ -1542,6 +1606,100 @@ std::string sweep_grow(SweepBlocks* w, int i, bool left, const std::vector<Secto
   else n.orbs.insert(n.orbs.begin(), s);
   n.arena = out;
   n.size = lay.size;
+  if (left) w->Lq[size_t(i + 1)] = Q;
+  else w->Rq[size_t(L - 1 - i)] = Q;
+  return "";
+}
+
+// Wavefunction prediction (S = 0).  Moving right from window i the kept
+// wavefunction is Q (Q^T M) per bond sector: Q became the grown left block,
+// and C = Q^T M, with columns stacked (right sector b, site s2), is expanded
+// over the right block's MPS tensor, b = [s3 x r'] with rows stacked (r', s3),
+// into the blocks (k, s2, s3, r', S_b, S_b) of window i+1.  Moving left,
+// C = M Q (rows (left sector a, site s1)) is expanded over the left block's
+// tensor, a = [a'' x s0], into the blocks (a'', s0, s1, k, S_a, S_a) of
+// window i-1.  The recoupling (j_k (s2 S_b)_j)_0 -> ((j_k s2)_(S_b) S_b)_0 of
+// total spin 0 has the factor (-1)^(j_k+s2+S_b) sqrt((2S_b+1)(2j_k+1)) times
+// the 6j {j_k s2 S_b; S_b 0 j_k}, which is 1; no operator changes places, so
+// no fermionic sign enters.  The guess is laid out in the next window's
+// block order (build_blocks of its sectors).
+std::string sweep_predict(SweepBlocks* w, int i, bool right, const std::vector<Sector>& lsec,
+                          const std::vector<Sector>& rsec, int N, const std::vector<Sector>& cur,
+                          const std::vector<std::vector<double>>& rest, std::vector<double>& guess) {
+  const int L = w->L;
+  const int nx = right ? i + 1 : i - 1;
+  if (nx < 0 || nx > L - 2) return "no window to predict";
+  const std::vector<Sector>& nl = w->Lb[size_t(nx)].lay.sec;
+  const std::vector<Sector>& nr = w->Rb[size_t(L - 2 - nx)].lay.sec;
+  const auto& T = right ? w->Rq[size_t(L - 2 - i)] : w->Lq[size_t(i)];
+  const std::vector<Sector>& tsec = right ? rsec : lsec;            // sectors the tensor produces
+  const std::vector<Sector>& tprev = right ? nr : nl;                // its previous bond
+  if (T.size() != tsec.size()) return "the MPS tensor of the adjacent block is not known";
+  std::vector<Block> nb;
+  int64_t nlen = 0;
+  std::string err = build_blocks(nl, nr, SU2_SITE_ORBITAL, N, 0, nb, nlen);
+  if (!err.empty()) return err;
+  std::map<std::tuple<int, int, int, int, int>, int> bidx;
+  for (int x = 0; x < int(nb.size()); ++x) bidx[{nb[x].a, nb[x].s1, nb[x].s2, nb[x].b, nb[x].jL1}] = x;
+  std::vector<int> sN, sS;
+  site_states(SU2_SITE_ORBITAL, sN, sS);
+  struct Stk {
+    int q, s, r0, d;
+  };
+  auto stacks = [&](const std::vector<Sector>& sec, int Nq, int j, int& tot) {
+    std::vector<Stk> v;
+    tot = 0;
+    for (int qp = 0; qp < int(sec.size()); ++qp)
+      for (int si = 0; si < 3; ++si)
+        if (sec[qp].N + sN[si] == Nq && triangle(sec[qp].twoS, sS[si], j)) {
+          v.push_back(Stk{qp, si, tot, sec[qp].dim});
+          tot += sec[qp].dim;
+        }
+    return v;
+  };
+  guess.assign(size_t(nlen), 0.0);
+  for (int qo = 0; qo < int(cur.size()); ++qo) {
+    const int j = cur[qo].twoS, d = cur[qo].dim;
+    const int Nq = right ? cur[qo].N : N - cur[qo].N;  // particles left of the bond between the two sites
+    int tot = 0;
+    // right: C's columns (b, s2) over the right sectors of window i; left:
+    // C's rows (a, s1) over its left sectors
+    const auto st = right ? stacks(rsec, N - Nq, j, tot) : stacks(lsec, Nq, j, tot);
+    const std::vector<double>& C = rest[size_t(qo)];
+    if (C.size() != size_t(tot) * d) return "prediction: the kept wavefunction does not match its stacks";
+    for (const Stk& x : st) {
+      const int S = tsec[size_t(x.q)].twoS, dq = tsec[size_t(x.q)].dim;
+      int trows = 0;
+      const auto tst = stacks(tprev, tsec[size_t(x.q)].N, S, trows);
+      const std::vector<double>& G = T[size_t(x.q)];
+      if (G.size() != size_t(trows) * dq) return "prediction: an MPS tensor does not match its stacks";
+      for (const Stk& y : tst) {
+        // right: block (qo, s2 = x.s, s3 = y.s, r' = y.q); left: (a'' = y.q, s0 = y.s, s1 = x.s, qo)
+        const auto it = right ? bidx.find({qo, x.s, y.s, y.q, S}) : bidx.find({y.q, y.s, x.s, qo, S});
+        if (it == bidx.end()) return "prediction: a block of the next window is missing";
+        const Block& B = nb[size_t(it->second)];
+        double* out = guess.data() + B.offset;
+        if (right) {
+          // out (d x dr') += C[:, x.r0 : x.r0 + db] G[y.r0 : y.r0 + dr', :]^T
+          for (int c = 0; c < B.cols; ++c)
+            for (int m = 0; m < dq; ++m) {
+              const double g = G[size_t(y.r0 + c) + size_t(m) * trows];
+              if (g == 0.0) continue;
+              const double* cc = &C[size_t(x.r0 + m) * d];
+              for (int r = 0; r < B.rows; ++r) out[r + int64_t(c) * B.rows] += cc[r] * g;
+            }
+        } else {
+          // out (da'' x d) += G[y.r0 : y.r0 + da'', :] C[x.r0 : x.r0 + da, :]
+          for (int c = 0; c < B.cols; ++c)
+            for (int m = 0; m < dq; ++m) {
+              const double cv = C[size_t(x.r0 + m) + size_t(c) * tot];
+              if (cv == 0.0) continue;
+              for (int r = 0; r < B.rows; ++r) out[r + int64_t(c) * B.rows] += G[size_t(y.r0 + r) + size_t(m) * trows] * cv;
+            }
+        }
+      }
+    }
+  }
   return "";
 }
 

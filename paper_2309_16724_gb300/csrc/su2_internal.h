@@ -125,9 +125,15 @@ std::string sweep_env(SweepBlocks* w, int i, OpTable& table, SideOps& L, SideOps
                       std::vector<Sector>& rsec);
 std::string sweep_split(const std::vector<Block>& blocks, const double* psi, const std::vector<Sector>& lsec,
                         const std::vector<Sector>& rsec, int N, int D, bool left, std::vector<Sector>& new_sec,
-                        std::vector<std::vector<double>>& Q, double* discarded);
+                        std::vector<std::vector<double>>& Q, double* discarded,
+                        std::vector<std::vector<double>>* rest = nullptr);
 std::string sweep_grow(SweepBlocks* w, int i, bool left, const std::vector<Sector>& cur,
                        const std::vector<std::vector<double>>& Q);
+// start vector of the next window (i+1 when `right`, else i-1) predicted
+// from window i's kept wavefunction (`rest` of sweep_split, after sweep_grow)
+std::string sweep_predict(SweepBlocks* w, int i, bool right, const std::vector<Sector>& lsec,
+                          const std::vector<Sector>& rsec, int N, const std::vector<Sector>& cur,
+                          const std::vector<std::vector<double>>& rest, std::vector<double>& guess);
 
 // counter-based generator (SplitMix64, Steele/Lea/Flood 2014)
 uint64_t splitmix(uint64_t x);

@@ -5,6 +5,10 @@
 * Truncated bonds: the energies of every window equal the oracle's sweep
   (its own SVD, truncation and renormalisation) on the same seeded MPS.
 * Initial right blocks grown by the caller's MPS tensors.
+* Wavefunction prediction: with bonds that keep every multiplet each
+  predicted start vector is the eigenvector (one or two Davidson
+  iterations); with truncated bonds the energies and the Rayleigh quotients
+  of the predicted start vectors equal the oracle's predicted sweep.
 """
 import numpy as np
 import pytest
@@ -73,3 +77,39 @@ def test_sweep_from_caller_right_tensors(ctx):
     assert ctx.status() == 0
     e0 = fci.spin_levels(h, eri, 6, 0)[0]
     assert np.abs(e - e0).max() < 1e-9
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_predicted_sweep_with_exact_bonds(ctx, prec):
+    import paper_2309_16724_gb300 as P
+    cfg = synth.Config("sw6", synth.SPATIAL_ORBITAL, 6, 6, 0, 400, 1002)
+    h, eri = synth.integrals(6, 1002)
+    chain = synth.bond_sector_chain(cfg, cfg.L - 2)
+    sw = P.Sweep(ctx, h, eri, chain, cfg.N, 400, prec=prec, tol=1e-10, seed=cfg.seed, predict=True)
+    e, w, it, e0 = sw.run(2 * (cfg.L - 1), stats=True)
+    sw.close()
+    assert ctx.status() == 0
+    efci = fci.spin_levels(h, eri, 6, 0)[0]
+    assert np.abs(e - efci).max() < 1e-9
+    assert it[0] > 10 and it[1:].max() <= (2 if prec == 0 else 3), it
+    assert np.abs(e0[1:] - efci).max() < 1e-9
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-8)])
+def test_predicted_sweep_matches_oracle(ctx, prec, tol):
+    import paper_2309_16724_gb300 as P
+    cfg = synth.Config("sw7", synth.SPATIAL_ORBITAL, 7, 6, 0, 6, 1002)
+    h, eri = synth.integrals(cfg.L, cfg.seed)
+    chain = synth.bond_sector_chain(cfg, cfg.L - 2)
+    sw = P.Sweep(ctx, h, eri, chain, cfg.N, 6, prec=prec, tol=1e-10, seed=cfg.seed, predict=True)
+    e, w, it, e0 = sw.run(2 * (cfg.L - 1), stats=True)
+    sw.close()
+    assert ctx.status() == 0
+    so = []
+    eo, wo = osweep.sweep(cfg, 6, 2, tol=1e-10, predict=True, stats=so)
+    assert np.abs(e - eo).max() < tol, (e, eo)
+    # the start vectors after the first window are the predicted ones on
+    # both sides (the first is seeded differently)
+    rq = np.array([x[1] for x in so])
+    assert np.abs(e0[1:] - rq[1:]).max() < 1e-7, (e0, rq)
+    assert it[cfg.L - 1] <= 2  # the turn starts from the previous eigenvector
