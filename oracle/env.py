@@ -197,39 +197,41 @@ def heisenberg_block_ops(cfg, n_sites, mps_side, J=1.0):
     S' = [s x 1]^1.  Returns (sectors, {'H': blocks, 'S': blocks}).
     """
     sk = synth.SPIN_HALF
-    sites = synth.site_states(sk)
-    so = model.site_ops(sk)
     chain = synth.bond_sector_chain(cfg, n_sites)
     left = mps_side == SIDE_MPS_L
     H, S = None, None
     for k in range(1, n_sites + 1):
-        prev, cur = chain[k - 1], chain[k]
-        A = mps_tensor(cfg.seed, mps_side, k, prev, cur, sk)
-        Hn, Sn = {}, {}
-        for qo, (rows_o, Qo) in A.items():
-            for qi, (rows_i, Qi) in A.items():
-                So_, Si_ = cur[qo][1], cur[qi][1]
-                if cur[qo][0] != cur[qi][0]:
-                    continue
-                if So_ == Si_:
-                    M = np.zeros((Qo.shape[0], Qi.shape[0]))
-                    if H is not None:
-                        M += _coupled_op(prev, sites, None, rows_o, rows_i, So_, Si_, H, 0, 0,
-                                         so["I"], left, 0)
-                    if S is not None:
-                        if left:
-                            M += -math.sqrt(3.0) * J * _coupled_op(prev, sites, None, rows_o, rows_i,
-                                                                   So_, Si_, S, 2, 0, so["S"], True, 0)
-                        else:
-                            M += -math.sqrt(3.0) * J * _coupled_op(prev, sites, None, rows_o, rows_i,
-                                                                   So_, Si_, S, 2, 0, so["S"], False, 0)
-                    Hn[(qo, qi)] = Qo.T @ M @ Qi
-                if triangle(Si_, 2, So_):
-                    M = _coupled_op(prev, sites, None, rows_o, rows_i, So_, Si_, None, 0, 0,
-                                    so["S"], left, 2)
-                    Sn[(qo, qi)] = Qo.T @ M @ Qi
-        H, S = Hn, Sn
+        A = mps_tensor(cfg.seed, mps_side, k, chain[k - 1], chain[k], sk)
+        H, S = heisenberg_step(chain[k - 1], chain[k], A, H, S, left, J)
     return chain[n_sites], {"H": H, "S": S}
+
+
+def heisenberg_step(prev, cur, A, H, S, left, J=1.0):
+    """One growth step of a Heisenberg block by a spin-1/2 site: the block's
+    {H, S} on bond ``prev`` (None for the empty block) projected by the MPS
+    tensor A (``mps_tensor``'s layout) onto bond ``cur``."""
+    sites = synth.site_states(synth.SPIN_HALF)
+    so = model.site_ops(synth.SPIN_HALF)
+    Hn, Sn = {}, {}
+    for qo, (rows_o, Qo) in A.items():
+        for qi, (rows_i, Qi) in A.items():
+            So_, Si_ = cur[qo][1], cur[qi][1]
+            if cur[qo][0] != cur[qi][0]:
+                continue
+            if So_ == Si_:
+                M = np.zeros((Qo.shape[0], Qi.shape[0]))
+                if H is not None:
+                    M += _coupled_op(prev, sites, None, rows_o, rows_i, So_, Si_, H, 0, 0,
+                                     so["I"], left, 0)
+                if S is not None:
+                    M += -math.sqrt(3.0) * J * _coupled_op(prev, sites, None, rows_o, rows_i,
+                                                           So_, Si_, S, 2, 0, so["S"], left, 0)
+                Hn[(qo, qi)] = Qo.T @ M @ Qi
+            if triangle(Si_, 2, So_):
+                M = _coupled_op(prev, sites, None, rows_o, rows_i, So_, Si_, None, 0, 0,
+                                so["S"], left, 2)
+                Sn[(qo, qi)] = Qo.T @ M @ Qi
+    return Hn, Sn
 
 
 def casimir_ops(table, sectors, side_name):

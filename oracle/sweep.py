@@ -1,5 +1,5 @@
 """Two-site sweep of SU(2) spin-adapted DMRG (Sec. II) on the ab initio
-Hamiltonian: at every bond the lowest eigenpair of H_eff (Davidson), the
+Hamiltonian (orbital sites) or the spin-1/2 Heisenberg chain: at every bond the lowest eigenpair of H_eff (Davidson), the
 singular value decomposition of the reduced two-site wavefunction per bond
 sector, truncation to D multiplets, and the block grown by one orbital with
 the kept singular vectors (renormalisation, Sec. II.C).
@@ -40,16 +40,17 @@ Readings (the paper gives no sweep algorithm):
   L-2 .. 0; the initial right blocks come from the seeded MPS of the bond
   recipe.
 
-Parity: pinned by full CI (with bonds that keep every multiplet every step's
-energy is the ground-state energy) and by the variational bound with
-truncated bonds.
+Parity: pinned by full CI and exact diagonalisation (with bonds that keep
+every multiplet every step's energy is the ground-state energy) and by the
+variational bound with truncated bonds; the prediction by the identities of
+the truncated state it represents.
 """
 from __future__ import annotations
 
 import numpy as np
 
 import synth
-from . import abinitio, davidson, heff, sectors
+from . import abinitio, davidson, heff, model, sectors
 from . import env as envmod
 from .su2 import triangle
 
@@ -190,8 +191,42 @@ def window(strings, Lb, Rb, N):
     return apply, diag, blocks, n, ls, rs
 
 
-def _solve(strings, Lb, Rb, N, seed, tol, x0=None):
-    apply, diag, blocks, n, ls, rs = window(strings, Lb, Rb, N)
+class HeisenbergBlock:
+    """Operators {H, S} of a block of spin-1/2 sites (None for the empty
+    block) on its bond sectors; grown one site at a time (the left block by
+    [block x site], the right block by [site x block], Sec. II.C)."""
+
+    def __init__(self, sectors_, H=None, S=None, J=1.0):
+        self.sectors, self.H, self.S, self.J = sectors_, H, S, J
+
+    def grown(self, cur, A, left):
+        H, S = envmod.heisenberg_step(self.sectors, cur, A, self.H, self.S, left, self.J)
+        return HeisenbergBlock(cur, H, S, self.J)
+
+
+def heisenberg_window(Lb, Rb, N, J=1.0):
+    """The two-site problem of the spin-1/2 Heisenberg chain between blocks
+    Lb and Rb: (apply, diag, blocks, psi length, left sectors, right
+    sectors)."""
+    table = model.heisenberg_table(J)
+    env = {}
+    for side, b, ops in (("L", Lb, table.left_ops), ("R", Rb, table.right_ops)):
+        for oid, op in enumerate(ops):
+            if op.kind != model.MPS_RENORM:
+                continue
+            vals = (b.H if op.name == "H" else b.S) or {}
+            env[(side, oid)] = {(qo, qi): vals.get((qo, qi), np.zeros((b.sectors[qo][2], b.sectors[qi][2])))
+                                for (qo, qi) in envmod.allowed_blocks(op, b.sectors)}
+    ls, rs = Lb.sectors, Rb.sectors
+    blocks, n = sectors.build_blocks(ls, rs, synth.SPIN_HALF, N, 0)
+    tasks = heff.build_tasks(table, ls, rs, blocks, 0)
+    apply = lambda v: heff.apply_heff(table, env, tasks, blocks, n, v)
+    diag = heff.diag_heff(table, env, tasks, blocks, n)
+    return apply, diag, blocks, n, ls, rs
+
+
+def _solve(win, seed, tol, x0=None):
+    apply, diag, blocks, n, ls, rs = win
     if x0 is None or not np.linalg.norm(x0) > 0:
         x0 = synth.gaussian_psi(n, seed)
     rq0 = float(x0 @ apply(x0) / (x0 @ x0))
@@ -199,27 +234,39 @@ def _solve(strings, Lb, Rb, N, seed, tol, x0=None):
     return theta, x, blocks, ls, rs, it, rq0
 
 
-def sweep(cfg, D, n_half, tol=1e-9, h=None, eri=None, predict=False, stats=None):
+def sweep(cfg, D, n_half, tol=1e-9, h=None, eri=None, predict=False, stats=None, J=1.0):
     """Energies of every two-site step of n_half half-sweeps (S = 0), with the
     initial right blocks from cfg's seeded MPS; returns (energies, discarded
-    weights).  With ``predict`` every window after the first starts from the
-    wavefunction predicted from the previous one.  A list ``stats`` receives
-    (Davidson iterations, Rayleigh quotient of the start vector) per step."""
-    assert cfg.twoS == 0 and cfg.site_kind == synth.SPATIAL_ORBITAL
-    if h is None:
-        h, eri = synth.integrals(cfg.L, cfg.seed)
-    strings = abinitio.hamiltonian_strings(h, eri)
+    weights).  The model follows cfg's site kind: the ab initio Hamiltonian
+    of the integrals (h, eri; default: cfg's seeded ones) on orbital sites,
+    or the Heisenberg chain with coupling J on spin-1/2 sites.  With
+    ``predict`` every window after the first starts from the wavefunction
+    predicted from the previous one.  A list ``stats`` receives (Davidson
+    iterations, Rayleigh quotient of the start vector) per step."""
+    assert cfg.twoS == 0
+    kind = cfg.site_kind
     L, N = cfg.L, cfg.N
+    if kind == synth.SPATIAL_ORBITAL:
+        if h is None:
+            h, eri = synth.integrals(cfg.L, cfg.seed)
+        strings = abinitio.hamiltonian_strings(h, eri)
+        R = [abinitio.RightBlock(strings, L)]
+        Lbs = [abinitio.LeftBlock(strings, L)] + [None] * (L - 2)
+        grow = lambda b, sec, A, left: b.grown(sec, A)
+        make_window = lambda Lb, Rb: window(strings, Lb, Rb, N)
+    else:
+        R = [HeisenbergBlock([(0, 0, 1)], J=J)]
+        Lbs = [HeisenbergBlock([(0, 0, 1)], J=J)] + [None] * (L - 2)
+        grow = lambda b, sec, A, left: b.grown(sec, A, left)
+        make_window = lambda Lb, Rb: heisenberg_window(Lb, Rb, N, J)
     chain = synth.bond_sector_chain(cfg, L - 2)
-    # R[m]: right block of the last m orbitals; RA[m] / LA[m]: the MPS tensor
+    # R[m]: right block of the last m sites; RA[m] / LA[m]: the MPS tensor
     # that grew R[m] from R[m-1] / Lbs[m] from Lbs[m-1]
-    R = [abinitio.RightBlock(strings, L)]
     RA = [None] * (L - 1)
     for k in range(1, L - 1):
-        A = envmod.mps_tensor(cfg.seed, envmod.SIDE_MPS_R, k, chain[k - 1], chain[k], synth.SPATIAL_ORBITAL)
-        R.append(R[-1].grown(chain[k], A))
+        A = envmod.mps_tensor(cfg.seed, envmod.SIDE_MPS_R, k, chain[k - 1], chain[k], kind)
+        R.append(grow(R[-1], chain[k], A, False))
         RA[k] = A
-    Lbs = [abinitio.LeftBlock(strings, L)] + [None] * (L - 2)
     LA = [None] * (L - 1)
     energies, discarded = [], []
     step = 0
@@ -228,7 +275,7 @@ def sweep(cfg, D, n_half, tol=1e-9, h=None, eri=None, predict=False, stats=None)
         order = range(0, L - 1) if half % 2 == 0 else range(L - 2, -1, -1)
         for i in order:
             Lb, Rb = Lbs[i], R[L - 2 - i]
-            theta, x, blocks, ls, rs, it, rq0 = _solve(strings, Lb, Rb, N, cfg.seed + 1000 + step, tol,
+            theta, x, blocks, ls, rs, it, rq0 = _solve(make_window(Lb, Rb), cfg.seed + 1000 + step, tol,
                                                        guess if predict else None)
             if stats is not None:
                 stats.append((it, rq0))
@@ -236,21 +283,19 @@ def sweep(cfg, D, n_half, tol=1e-9, h=None, eri=None, predict=False, stats=None)
             energies.append(theta)
             guess = x   # at a turn the next window is this one
             if half % 2 == 0 and i < L - 2:
-                sec, A, w, rest = isometry(x, blocks, ls, rs, synth.SPATIAL_ORBITAL, N, D, "L", with_rest=True)
-                Lbs[i + 1] = Lb.grown(sec, A)
+                sec, A, w, rest = isometry(x, blocks, ls, rs, kind, N, D, "L", with_rest=True)
+                Lbs[i + 1] = grow(Lb, sec, A, True)
                 LA[i + 1] = A
                 discarded.append(w)
                 if predict:
-                    nb, nn = sectors.build_blocks(Lbs[i + 1].sectors, R[L - 3 - i].sectors,
-                                                  synth.SPATIAL_ORBITAL, N, 0)
+                    nb, nn = sectors.build_blocks(Lbs[i + 1].sectors, R[L - 3 - i].sectors, kind, N, 0)
                     guess = predict_moving_right(rest, rs, RA[L - 2 - i], nb, nn)
             elif half % 2 == 1 and i > 0:
-                sec, A, w, rest = isometry(x, blocks, ls, rs, synth.SPATIAL_ORBITAL, N, D, "R", with_rest=True)
-                R[L - 1 - i] = Rb.grown(sec, A)
+                sec, A, w, rest = isometry(x, blocks, ls, rs, kind, N, D, "R", with_rest=True)
+                R[L - 1 - i] = grow(Rb, sec, A, False)
                 RA[L - 1 - i] = A
                 discarded.append(w)
                 if predict:
-                    nb, nn = sectors.build_blocks(Lbs[i - 1].sectors, R[L - 1 - i].sectors,
-                                                  synth.SPATIAL_ORBITAL, N, 0)
+                    nb, nn = sectors.build_blocks(Lbs[i - 1].sectors, R[L - 1 - i].sectors, kind, N, 0)
                     guess = predict_moving_left(rest, ls, LA[i], nb, nn)
     return np.array(energies), np.array(discarded)
