@@ -346,17 +346,21 @@ int su2_energy(const su2_dav* dav, double* E);
 int su2_davidson_vector(su2_ctx* ctx, su2_dav* dav, double* x_dev);
 int su2_davidson_destroy(su2_dav* dav);
 
-/* Two-site sweep of the ab initio model (Sec. II; total spin 0): at every
- * window (sites i, i+1) the environment is assembled from blocks kept on the
- * device, the lowest eigenpair of H_eff found by Davidson (split or FP64
- * H.psi), the reduced two-site wavefunction decomposed per bond sector by a
- * singular value decomposition (on the host), the D largest singular values
- * kept (ties to the lower (N, 2S) sector, then the lower index), and the
- * block on the side the sweep moves to grown by one orbital with the kept
- * singular vectors (renormalisation on the device, Sec. IV.D).  The sweep
- * starts at window 0 moving right with the right blocks of a seeded MPS
- * (right_chain: the bonds of 0 .. L-2 orbitals, L = n_left + 2 + n_right)
- * and turns at the ends.  The first window's Davidson starts from a seeded
+/* Two-site sweep (Sec. II; total spin 0) of the ab initio model
+ * (SU2_MODEL_AB_INITIO with its integrals) or of the spin-1/2 Heisenberg
+ * chain (SU2_MODEL_HEISENBERG, coupling J; h and eri unused): at every
+ * window (sites i, i+1) the environment is assembled from the blocks of
+ * every length the sweep keeps, the lowest eigenpair of H_eff found by
+ * Davidson (split or FP64 H.psi), the reduced two-site wavefunction
+ * decomposed per bond sector by a singular value decomposition (on the
+ * host), the D largest singular values kept (ties to the lower (N, 2S)
+ * sector, then the lower index), and the block on the side the sweep moves
+ * to grown by one site with the kept singular vectors (ab initio blocks:
+ * kept and renormalised on the device, Sec. IV.D; Heisenberg blocks {H, S}:
+ * on the host).  The sweep starts at window 0 moving right with the right
+ * blocks of a seeded MPS, or of the caller's tensors (H->mps_right), on
+ * right_chain (the bonds of 0 .. L-2 sites, L = n_left + 2 + n_right) and
+ * turns at the ends.  The first window's Davidson starts from a seeded
  * vector; with `predict` every later window starts from the wavefunction
  * predicted from the previous one (the kept part of its bond matrix expanded
  * over the adjacent block's MPS tensor: the truncated state written in the

@@ -440,23 +440,31 @@ class Davidson:
 
 
 class Sweep:
-    """su2_sweep_create / su2_sweep_run: the two-site sweep of the ab initio
-    model (S = 0) on the GPU, starting at window 0 moving right with the right
-    blocks of `right_chain` (bonds of 0 .. L-2 orbitals) grown by the seeded MPS
-    tensors, or by the caller's (`mps_right`, the layout of su2_hamiltonian)."""
+    """su2_sweep_create / su2_sweep_run: the two-site sweep (S = 0) on the
+    GPU, of the ab initio model of the integrals (h, eri) or, with h = eri =
+    None, of the spin-1/2 Heisenberg chain of len(right_chain) + 1 sites with
+    coupling J; it starts at window 0 moving right with the right blocks of
+    `right_chain` (bonds of 0 .. L-2 sites) grown by the seeded MPS tensors,
+    or by the caller's (`mps_right`, the layout of su2_hamiltonian)."""
 
     def __init__(self, ctx: Context, h, eri, right_chain, N, D, prec=SU2_SPLIT_BF16, tol=1e-8, max_iter=400,
-                 n_slices=5, seed=0, guess_seed=1, mps_right=None, predict=False):
+                 n_slices=5, seed=0, guess_seed=1, mps_right=None, predict=False, J=1.0):
         self.ctx = ctx
-        h = np.ascontiguousarray(h, dtype=np.float64)
-        eri = np.ascontiguousarray(eri, dtype=np.float64)
-        L = h.shape[0]
-        if eri.shape != (L, L, L, L) or len(right_chain) != L - 1:
-            raise Su2Error(SU2_EINVAL, "integrals or chain of the wrong size")
         mr = _mps(mps_right)
-        self._keep = (h, eri, mr)
-        H = Hamiltonian(SU2_MODEL_AB_INITIO, 0, L - 2, 1.0, seed, h.ctypes.data, eri.ctypes.data, None,
-                        None if mr is None else mr.ctypes.data)
+        if h is None and eri is None:
+            L = len(right_chain) + 1
+            self._keep = (mr,)
+            H = Hamiltonian(SU2_MODEL_HEISENBERG, 0, L - 2, J, seed, None, None, None,
+                            None if mr is None else mr.ctypes.data)
+        else:
+            h = np.ascontiguousarray(h, dtype=np.float64)
+            eri = np.ascontiguousarray(eri, dtype=np.float64)
+            L = h.shape[0]
+            if eri.shape != (L, L, L, L) or len(right_chain) != L - 1:
+                raise Su2Error(SU2_EINVAL, "integrals or chain of the wrong size")
+            self._keep = (h, eri, mr)
+            H = Hamiltonian(SU2_MODEL_AB_INITIO, 0, L - 2, 1.0, seed, h.ctypes.data, eri.ctypes.data, None,
+                            None if mr is None else mr.ctypes.data)
         rc_, keep = _chain(right_chain)
         o = SweepOpts(D, prec, tol, max_iter, n_slices, guess_seed, 1 if predict else 0)
         hd = C.c_void_p()

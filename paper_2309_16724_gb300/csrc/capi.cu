@@ -1150,6 +1150,12 @@ struct su2_sweep {
   int pos = 0, dir = 1;  // next window and direction
   int64_t steps = 0;
   std::vector<double> guess;  // predicted start vector of the next window (empty: seeded)
+  // Heisenberg chain (spin-1/2 sites): blocks and the MPS tensors that grew
+  // them, on the host (hL[i]: the first i sites, hR[k]: the last k sites)
+  bool heis = false;
+  su2_hamiltonian H{};
+  std::vector<HeisBlock> hL, hR;
+  std::vector<std::vector<std::vector<double>>> hLq, hRq;
 };
 
 extern "C" {
@@ -1159,7 +1165,9 @@ int su2_sweep_create(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond_chai
   if (!ctx || !H || !right_chain || !opts || !out) return fail(ctx, SU2_EINVAL, "null argument");
   *out = nullptr;
   if (ctx->device < 0) return fail(ctx, SU2_EINVAL, "the sweep needs a device context");
-  if (H->model != SU2_MODEL_AB_INITIO || !H->h || !H->eri) return fail(ctx, SU2_EINVAL, "the sweep needs the ab initio model");
+  const bool heis = H->model == SU2_MODEL_HEISENBERG;
+  if (!heis && (H->model != SU2_MODEL_AB_INITIO || !H->h || !H->eri))
+    return fail(ctx, SU2_EINVAL, "the sweep needs the ab initio model (with its integrals) or the Heisenberg chain");
   if (opts->D < 1 || N < 0) return fail(ctx, SU2_EINVAL, "D must be >= 1");
   if (opts->prec != SU2_FP64 && opts->prec != SU2_SPLIT_BF16) return fail(ctx, SU2_EINVAL, "unknown precision");
   std::vector<std::vector<Sector>> rch;
@@ -1184,8 +1192,47 @@ int su2_sweep_create(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond_chai
   if (sw->o.max_iter <= 0) sw->o.max_iter = 400;
   if (sw->o.n_slices <= 0) sw->o.n_slices = 5;
   std::string err;
-  sw->w = sweep_init(*H, rch, ctx->device, ctx->stream, 0, err);
-  if (!sw->w) {
+  if (heis) {
+    // initial right blocks grown site by site by the caller's tensors or the seeded ones
+    const int L = sw->L;
+    sw->heis = true;
+    sw->H = *H;
+    sw->H.h = sw->H.eri = sw->H.mps_left = sw->H.mps_right = nullptr;
+    if (int(rch.size()) != L - 1) err = "the initial right chain must hold the bonds of 0 .. L-2 sites";
+    sw->hL.resize(size_t(L - 1));
+    sw->hR.resize(size_t(L - 1));
+    sw->hLq.resize(size_t(L - 1));
+    sw->hRq.resize(size_t(L - 1));
+    if (err.empty()) sw->hR[0].sec = rch[0];
+    std::vector<int> sN, sS;
+    site_states(SU2_SITE_SPIN_HALF, sN, sS);
+    size_t pos = 0;
+    for (int k = 1; k < L - 1 && err.empty(); ++k) {
+      const auto& prev = rch[size_t(k - 1)];
+      const auto& cur = rch[size_t(k)];
+      std::vector<std::vector<double>> Q(cur.size());
+      for (size_t qo = 0; qo < cur.size() && err.empty(); ++qo) {
+        int r0 = 0;
+        for (const Sector& p : prev)
+          for (size_t si = 0; si < sN.size(); ++si)
+            if (p.N + sN[si] == cur[qo].N && triangle(p.twoS, sS[si], cur[qo].twoS)) r0 += p.dim;
+        if (r0 < cur[qo].dim) {
+          err = "bond dimension exceeds the states available from the previous bond";
+        } else if (H->mps_right) {
+          const size_t n = size_t(r0) * size_t(cur[qo].dim);
+          Q[qo].assign(H->mps_right + pos, H->mps_right + pos + n);
+          pos += n;
+        } else {
+          Q[qo] = seeded_mps_tensor(H->seed, 3, k, int(qo), r0, cur[qo].dim);
+        }
+      }
+      if (err.empty()) err = heis_grow(sw->hR[size_t(k - 1)], cur, Q, false, H->J, sw->hR[size_t(k)]);
+      sw->hRq[size_t(k)] = std::move(Q);
+    }
+  } else {
+    sw->w = sweep_init(*H, rch, ctx->device, ctx->stream, 0, err);
+  }
+  if (!err.empty()) {
     delete sw;
     return fail(ctx, SU2_EINVAL, err);
   }
@@ -1201,16 +1248,28 @@ int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies
   const int L = sw->L;
   for (int k = 0; k < n_steps; ++k) {
     const int i = sw->pos;
+    const int kind = sw->heis ? SU2_SITE_SPIN_HALF : SU2_SITE_ORBITAL;
     su2_sectors S;
-    S.site_kind = SU2_SITE_ORBITAL;
+    S.site_kind = kind;
     S.N = sw->N;
     S.twoS = 0;
     su2_env* env = new (std::nothrow) su2_env();
     if (!env) return fail(ctx, SU2_ENOMEM, "host allocation");
     env->ctx = ctx;
     env->device = ctx->device;
-    std::string err = sweep_env(sw->w, i, env->table, env->L, env->R, S.left, S.right);
-    if (err.empty()) build_blocks(S.left, S.right, SU2_SITE_ORBITAL, sw->N, 0, S.blocks, S.psi_len);
+    std::string err;
+    if (sw->heis) {
+      const HeisBlock& lb = sw->hL[size_t(i)];
+      const HeisBlock& rb = sw->hR[size_t(L - 2 - i)];
+      env->table = make_table(sw->H, kind);
+      err = heis_side_ops(env->table, true, lb, env->L);
+      if (err.empty()) err = heis_side_ops(env->table, false, rb, env->R);
+      S.left = lb.sec;
+      S.right = rb.sec;
+    } else {
+      err = sweep_env(sw->w, i, env->table, env->L, env->R, S.left, S.right);
+    }
+    if (err.empty()) build_blocks(S.left, S.right, kind, sw->N, 0, S.blocks, S.psi_len);
     if (err.empty() && S.psi_len == 0) err = "no two-site state with the target particle number";
     if (err.empty()) {
       env->psi_len = S.psi_len;
@@ -1282,10 +1341,27 @@ int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies
       std::vector<Sector> cur;
       std::vector<std::vector<double>> Q, rest;
       err = sweep_split(S.blocks, h.data(), S.left, S.right, sw->N, sw->o.D, sw->dir > 0, cur, Q, &w,
-                        sw->o.predict ? &rest : nullptr);
-      if (err.empty()) err = sweep_grow(sw->w, i, sw->dir > 0, cur, Q);
-      if (err.empty() && sw->o.predict)
-        err = sweep_predict(sw->w, i, sw->dir > 0, S.left, S.right, sw->N, cur, rest, sw->guess);
+                        sw->o.predict ? &rest : nullptr, kind);
+      if (err.empty() && sw->heis) {
+        // the grown block on the host, then the next window's guess
+        if (sw->dir > 0) {
+          err = heis_grow(sw->hL[size_t(i)], cur, Q, true, sw->H.J, sw->hL[size_t(i + 1)]);
+          sw->hLq[size_t(i + 1)] = Q;
+          if (err.empty() && sw->o.predict)
+            err = predict_guess(true, S.left, S.right, sw->hL[size_t(i + 1)].sec, sw->hR[size_t(L - 3 - i)].sec,
+                                sw->hRq[size_t(L - 2 - i)], sw->N, kind, cur, rest, sw->guess);
+        } else {
+          err = heis_grow(sw->hR[size_t(L - 2 - i)], cur, Q, false, sw->H.J, sw->hR[size_t(L - 1 - i)]);
+          sw->hRq[size_t(L - 1 - i)] = Q;
+          if (err.empty() && sw->o.predict)
+            err = predict_guess(false, S.left, S.right, sw->hL[size_t(i - 1)].sec, sw->hR[size_t(L - 1 - i)].sec,
+                                sw->hLq[size_t(i)], sw->N, kind, cur, rest, sw->guess);
+        }
+      } else if (err.empty()) {
+        err = sweep_grow(sw->w, i, sw->dir > 0, cur, Q);
+        if (err.empty() && sw->o.predict)
+          err = sweep_predict(sw->w, i, sw->dir > 0, S.left, S.right, sw->N, cur, rest, sw->guess);
+      }
       if (!err.empty()) return fail(ctx, SU2_EINVAL, err);
     } else if (sw->o.predict) {
       sw->guess = h;
@@ -1307,7 +1383,7 @@ int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies
 int su2_sweep_destroy(su2_sweep* sw) {
   if (!sw) return SU2_EINVAL;
   if (sw->device >= 0) cudaSetDevice(sw->device);
-  sweep_free(sw->w);
+  if (sw->w) sweep_free(sw->w);
   delete sw;
   return SU2_OK;
 }

@@ -433,12 +433,7 @@ class Builder {
   // the seeded MPS tensor of sector qo at growth step `step` (side 2: left,
   // 3: right): the Q factor of a counter-generated r0 x d matrix
   std::vector<double> seeded_tensor(uint64_t side, int step, int qo, int r0, int d) const {
-    std::vector<double> G(size_t(r0) * d);
-    const uint64_t key = block_key(H_.seed, side, uint64_t(step), uint64_t(qo), 0);
-    for (int c = 0; c < d; ++c)
-      for (int r = 0; r < r0; ++r) G[size_t(r) + size_t(c) * r0] = uniform_elem(key, uint64_t(r) + uint64_t(c) * r0);
-    orthonormalize(G, r0, d);
-    return G;
+    return seeded_mps_tensor(H_.seed, side, step, qo, r0, d);
   }
 
   // the seeded MPS tensors of one step (per new sector, stacked rows x dim)
@@ -1441,9 +1436,10 @@ std::string sweep_env(SweepBlocks* w, int i, OpTable& table, SideOps& Lops, Side
 std::string sweep_split(const std::vector<Block>& blocks, const double* psi, const std::vector<Sector>& lsec,
                         const std::vector<Sector>& rsec, int N, int D, bool left, std::vector<Sector>& new_sec,
                         std::vector<std::vector<double>>& Q, double* discarded,
-                        std::vector<std::vector<double>>* rest) {
+                        std::vector<std::vector<double>>* rest, int site_kind) {
   std::vector<int> sN, sS;
-  site_states(SU2_SITE_ORBITAL, sN, sS);
+  site_states(site_kind, sN, sS);
+  const int ns = int(sN.size());
   struct Stk {
     int q, s, r0, d;
   };
@@ -1451,7 +1447,7 @@ std::string sweep_split(const std::vector<Block>& blocks, const double* psi, con
     std::vector<Stk> v;
     tot = 0;
     for (int qp = 0; qp < int(sec.size()); ++qp)
-      for (int si = 0; si < 3; ++si)
+      for (int si = 0; si < ns; ++si)
         if (sec[qp].N + sN[si] == Nq && triangle(sec[qp].twoS, sS[si], j)) {
           v.push_back(Stk{qp, si, tot, sec[qp].dim});
           tot += sec[qp].dim;
@@ -1629,20 +1625,26 @@ std::string sweep_predict(SweepBlocks* w, int i, bool right, const std::vector<S
   const int L = w->L;
   const int nx = right ? i + 1 : i - 1;
   if (nx < 0 || nx > L - 2) return "no window to predict";
-  const std::vector<Sector>& nl = w->Lb[size_t(nx)].lay.sec;
-  const std::vector<Sector>& nr = w->Rb[size_t(L - 2 - nx)].lay.sec;
-  const auto& T = right ? w->Rq[size_t(L - 2 - i)] : w->Lq[size_t(i)];
+  return predict_guess(right, lsec, rsec, w->Lb[size_t(nx)].lay.sec, w->Rb[size_t(L - 2 - nx)].lay.sec,
+                       right ? w->Rq[size_t(L - 2 - i)] : w->Lq[size_t(i)], N, SU2_SITE_ORBITAL, cur, rest, guess);
+}
+
+std::string predict_guess(bool right, const std::vector<Sector>& lsec, const std::vector<Sector>& rsec,
+                          const std::vector<Sector>& nl, const std::vector<Sector>& nr,
+                          const std::vector<std::vector<double>>& T, int N, int site_kind,
+                          const std::vector<Sector>& cur, const std::vector<std::vector<double>>& rest,
+                          std::vector<double>& guess) {
   const std::vector<Sector>& tsec = right ? rsec : lsec;            // sectors the tensor produces
   const std::vector<Sector>& tprev = right ? nr : nl;                // its previous bond
   if (T.size() != tsec.size()) return "the MPS tensor of the adjacent block is not known";
   std::vector<Block> nb;
   int64_t nlen = 0;
-  std::string err = build_blocks(nl, nr, SU2_SITE_ORBITAL, N, 0, nb, nlen);
+  std::string err = build_blocks(nl, nr, site_kind, N, 0, nb, nlen);
   if (!err.empty()) return err;
   std::map<std::tuple<int, int, int, int, int>, int> bidx;
   for (int x = 0; x < int(nb.size()); ++x) bidx[{nb[x].a, nb[x].s1, nb[x].s2, nb[x].b, nb[x].jL1}] = x;
   std::vector<int> sN, sS;
-  site_states(SU2_SITE_ORBITAL, sN, sS);
+  site_states(site_kind, sN, sS);
   struct Stk {
     int q, s, r0, d;
   };
@@ -1650,7 +1652,7 @@ std::string sweep_predict(SweepBlocks* w, int i, bool right, const std::vector<S
     std::vector<Stk> v;
     tot = 0;
     for (int qp = 0; qp < int(sec.size()); ++qp)
-      for (int si = 0; si < 3; ++si)
+      for (int si = 0; si < int(sN.size()); ++si)
         if (sec[qp].N + sN[si] == Nq && triangle(sec[qp].twoS, sS[si], j)) {
           v.push_back(Stk{qp, si, tot, sec[qp].dim});
           tot += sec[qp].dim;

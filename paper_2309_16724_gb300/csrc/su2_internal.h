@@ -1,6 +1,7 @@
 // Internal data structures of the su2dmrg library (host side).
 #pragma once
 #include <cstdint>
+#include <map>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -55,6 +56,10 @@ SiteOp site_adjoint(const SiteOp& op, int site_kind);
 OpTable make_table(const su2_hamiltonian& H, int site_kind);
 // Q factor (positive diagonal of R) of a rows x cols column-major matrix
 void orthonormalize(std::vector<double>& G, int rows, int cols);
+// the seeded MPS tensor of sector qo at growth step `step` (side 2: left
+// blocks, 3: right blocks): the Q factor of the counter-generated r0 x d
+// matrix keyed by (seed, side, step, qo)
+std::vector<double> seeded_mps_tensor(uint64_t seed, uint64_t side, int step, int qo, int r0, int d);
 
 // ---------------------------------------------------------------- operators
 struct OpBlock { int op, qo, qi, rows, cols; int64_t off; };
@@ -113,6 +118,21 @@ std::string build_abinitio(const su2_hamiltonian& H, const std::vector<std::vect
 double u1_counted_flops(const OpTable& t, const std::vector<Sector>& left, const std::vector<Sector>& right, int N,
                         int twoS);
 
+// Heisenberg block (spin-1/2 sites): its bond sectors and the reduced blocks
+// (qo, qi) of H and of the edge spin S, column-major; grown = false for the
+// empty block (no operators)
+struct HeisBlock {
+  std::vector<Sector> sec{Sector{0, 0, 1}};
+  std::map<std::pair<int, int>, std::vector<double>> H, S;
+  bool grown = false;
+};
+// one growth step by a site (left: [block x site]; right: [site x block])
+// with the MPS tensor Q (per sector of `cur`, stacked rows x dim)
+std::string heis_grow(const HeisBlock& old, const std::vector<Sector>& cur, const std::vector<std::vector<double>>& Q,
+                      bool left, double J, HeisBlock& out);
+// the operators of the Heisenberg table on one side from a block (host values)
+std::string heis_side_ops(const OpTable& t, bool left_side, const HeisBlock& b, SideOps& out);
+
 // two-site sweep of the ab initio model (device contexts): blocks of every
 // length kept on the device; the environment at window i (sites i, i+1);
 // the per-sector SVD of an S = 0 two-site wavefunction with truncation to D
@@ -126,7 +146,7 @@ std::string sweep_env(SweepBlocks* w, int i, OpTable& table, SideOps& L, SideOps
 std::string sweep_split(const std::vector<Block>& blocks, const double* psi, const std::vector<Sector>& lsec,
                         const std::vector<Sector>& rsec, int N, int D, bool left, std::vector<Sector>& new_sec,
                         std::vector<std::vector<double>>& Q, double* discarded,
-                        std::vector<std::vector<double>>* rest = nullptr);
+                        std::vector<std::vector<double>>* rest = nullptr, int site_kind = SU2_SITE_ORBITAL);
 std::string sweep_grow(SweepBlocks* w, int i, bool left, const std::vector<Sector>& cur,
                        const std::vector<std::vector<double>>& Q);
 // start vector of the next window (i+1 when `right`, else i-1) predicted
@@ -134,6 +154,14 @@ std::string sweep_grow(SweepBlocks* w, int i, bool left, const std::vector<Secto
 std::string sweep_predict(SweepBlocks* w, int i, bool right, const std::vector<Sector>& lsec,
                           const std::vector<Sector>& rsec, int N, const std::vector<Sector>& cur,
                           const std::vector<std::vector<double>>& rest, std::vector<double>& guess);
+// the same from explicit data: the next window's bond sectors (nl, nr) and
+// the MPS tensor T of the block adjacent to window i on the side the sweep
+// moves to (its right block moving right, its left block moving left)
+std::string predict_guess(bool right, const std::vector<Sector>& lsec, const std::vector<Sector>& rsec,
+                          const std::vector<Sector>& nl, const std::vector<Sector>& nr,
+                          const std::vector<std::vector<double>>& T, int N, int site_kind,
+                          const std::vector<Sector>& cur, const std::vector<std::vector<double>>& rest,
+                          std::vector<double>& guess);
 
 // counter-based generator (SplitMix64, Steele/Lea/Flood 2014)
 uint64_t splitmix(uint64_t x);

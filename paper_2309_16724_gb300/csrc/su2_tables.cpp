@@ -323,6 +323,15 @@ void orthonormalize(std::vector<double>& G, int rows, int cols) {
   }
 }
 
+std::vector<double> seeded_mps_tensor(uint64_t seed, uint64_t side, int step, int qo, int r0, int d) {
+  std::vector<double> G(size_t(r0) * d);
+  const uint64_t key = block_key(seed, side, uint64_t(step), uint64_t(qo), 0);
+  for (int c = 0; c < d; ++c)
+    for (int r = 0; r < r0; ++r) G[size_t(r) + size_t(c) * r0] = uniform_elem(key, uint64_t(r) + uint64_t(c) * r0);
+  orthonormalize(G, r0, d);
+  return G;
+}
+
 namespace {
 
 struct Mat {
@@ -360,91 +369,104 @@ struct Stack {  // one (previous sector, site state) slot of a stacked MPS tenso
   int qp, s, r0, d;
 };
 
-// Renormalised Heisenberg block operators {H, S} grown over the bond chain.
+// One growth step of a Heisenberg block: its {H, S} on bond `prev` (have =
+// false for the empty block) projected by the MPS tensor Q (per new sector,
+// the stacked rows (previous sector, site state) x dim) onto bond `cur`.
 // left: block x site with the W9j^(l) factor; right: site x block, W9j^(r).
-std::string heisenberg_ops(const std::vector<std::vector<Sector>>& chain, bool left, const su2_hamiltonian& H,
-                           std::map<std::pair<int, int>, Mat>& Hout, std::map<std::pair<int, int>, Mat>& Sout) {
+void heis_step(const std::vector<Sector>& prev, const std::vector<Sector>& cur, const std::vector<Mat>& Q, bool left,
+               double J, bool have, std::map<std::pair<int, int>, Mat>& Hc, std::map<std::pair<int, int>, Mat>& Sc) {
   const int kind = SU2_SITE_SPIN_HALF;
   std::vector<int> sN, sS;
   site_states(kind, sN, sS);
   const SiteOp I = site_op(kind, "I"), Sop = site_op(kind, "S");
-  const uint64_t side = left ? 2 : 3;
+  std::vector<std::vector<Stack>> rows(cur.size());
+  for (int qo = 0; qo < int(cur.size()); ++qo) {
+    int r0 = 0;
+    for (int qp = 0; qp < int(prev.size()); ++qp)
+      for (int s = 0; s < int(sN.size()); ++s)
+        if (prev[qp].N + sN[s] == cur[qo].N && triangle(prev[qp].twoS, sS[s], cur[qo].twoS)) {
+          rows[qo].push_back(Stack{qp, s, r0, prev[qp].dim});
+          r0 += prev[qp].dim;
+        }
+  }
+  // coupled-basis reduced matrix of [O x s]^K (left) / [s x O]^K (right)
+  auto coupled = [&](int qo, int qi, const std::map<std::pair<int, int>, Mat>* O, int kO, const SiteOp& so, int K) {
+    Mat M(Q[qo].r, Q[qi].r);
+    const int Sout = cur[qo].twoS, Sin = cur[qi].twoS;
+    for (const Stack& ro : rows[qo])
+      for (const Stack& ri : rows[qi]) {
+        const double sv = so.red[ro.s][ri.s];
+        if (sv == 0.0) continue;
+        const Mat* Ob = nullptr;
+        if (O) {
+          auto it = O->find({ro.qp, ri.qp});
+          if (it == O->end()) continue;
+          Ob = &it->second;
+        } else if (ro.qp != ri.qp) {
+          continue;
+        }
+        const int Sli = prev[ri.qp].twoS, Slo = prev[ro.qp].twoS;
+        const double cf = left ? ctilde(Sli, sS[ri.s], Sin, kO, so.k, K, Slo, sS[ro.s], Sout)
+                               : ctilde(sS[ri.s], Sli, Sin, so.k, kO, K, sS[ro.s], Slo, Sout);
+        if (cf == 0.0) continue;
+        const double f = cf * sv;
+        for (int c = 0; c < ri.d; ++c)
+          for (int r = 0; r < ro.d; ++r) M(ro.r0 + r, ri.r0 + c) += f * (Ob ? (*Ob)(r, c) : (r == c ? 1.0 : 0.0));
+      }
+    return M;
+  };
+  std::map<std::pair<int, int>, Mat> Hn, Sn;
+  for (int qo = 0; qo < int(cur.size()); ++qo)
+    for (int qi = 0; qi < int(cur.size()); ++qi) {
+      if (cur[qo].N != cur[qi].N) continue;
+      if (cur[qo].twoS == cur[qi].twoS) {
+        Mat M(Q[qo].r, Q[qi].r);
+        if (have) {
+          Mat X = coupled(qo, qi, &Hc, 0, I, 0);
+          for (size_t i = 0; i < M.a.size(); ++i) M.a[i] += X.a[i];
+          X = coupled(qo, qi, &Sc, 2, Sop, 0);
+          const double c = -std::sqrt(3.0) * J;
+          for (size_t i = 0; i < M.a.size(); ++i) M.a[i] += c * X.a[i];
+        }
+        Hn[{qo, qi}] = ab(atb(Q[qo], M), Q[qi]);
+      }
+      if (triangle(cur[qi].twoS, 2, cur[qo].twoS)) {
+        Mat X = coupled(qo, qi, nullptr, 0, Sop, 2);
+        Sn[{qo, qi}] = ab(atb(Q[qo], X), Q[qi]);
+      }
+    }
+  Hc.swap(Hn);
+  Sc.swap(Sn);
+}
+
+// the stacked rows (previous sector, site state) of every sector of `cur`
+std::vector<int> stacked_rows(const std::vector<Sector>& prev, const std::vector<Sector>& cur, int kind) {
+  std::vector<int> sN, sS;
+  site_states(kind, sN, sS);
+  std::vector<int> r(cur.size(), 0);
+  for (size_t qo = 0; qo < cur.size(); ++qo)
+    for (const Sector& p : prev)
+      for (size_t s = 0; s < sN.size(); ++s)
+        if (p.N + sN[s] == cur[qo].N && triangle(p.twoS, sS[s], cur[qo].twoS)) r[qo] += p.dim;
+  return r;
+}
+
+// Renormalised Heisenberg block operators {H, S} grown over the bond chain
+// by the seeded MPS tensors.
+std::string heisenberg_ops(const std::vector<std::vector<Sector>>& chain, bool left, const su2_hamiltonian& H,
+                           std::map<std::pair<int, int>, Mat>& Hout, std::map<std::pair<int, int>, Mat>& Sout) {
   std::map<std::pair<int, int>, Mat> Hc, Sc;
-  bool have_H = false, have_S = false;
   for (size_t k = 1; k < chain.size(); ++k) {
-    const auto& prev = chain[k - 1];
     const auto& cur = chain[k];
-    std::vector<std::vector<Stack>> rows(cur.size());
+    const std::vector<int> r0 = stacked_rows(chain[k - 1], cur, SU2_SITE_SPIN_HALF);
     std::vector<Mat> Q(cur.size());
     for (int qo = 0; qo < int(cur.size()); ++qo) {
-      int r0 = 0;
-      for (int qp = 0; qp < int(prev.size()); ++qp)
-        for (int s = 0; s < int(sN.size()); ++s)
-          if (prev[qp].N + sN[s] == cur[qo].N && triangle(prev[qp].twoS, sS[s], cur[qo].twoS)) {
-            rows[qo].push_back(Stack{qp, s, r0, prev[qp].dim});
-            r0 += prev[qp].dim;
-          }
       const int d = cur[qo].dim;
-      if (r0 < d) return "bond dimension exceeds the states available from the previous bond";
-      Mat G(r0, d);
-      const uint64_t key = block_key(H.seed, side, uint64_t(k), uint64_t(qo), 0);
-      for (int c = 0; c < d; ++c)
-        for (int r = 0; r < r0; ++r) G(r, c) = uniform_elem(key, uint64_t(r) + uint64_t(c) * r0);
-      orthonormalize(G.a, r0, d);
-      Q[qo] = G;
+      if (r0[qo] < d) return "bond dimension exceeds the states available from the previous bond";
+      Q[qo] = Mat(r0[qo], d);
+      Q[qo].a = seeded_mps_tensor(H.seed, left ? 2 : 3, int(k), qo, r0[qo], d);
     }
-    // coupled-basis reduced matrix of [O x s]^K (left) / [s x O]^K (right)
-    auto coupled = [&](int qo, int qi, const std::map<std::pair<int, int>, Mat>* O, int kO, const SiteOp& so,
-                       int K) {
-      Mat M(Q[qo].r, Q[qi].r);
-      const int Sout = cur[qo].twoS, Sin = cur[qi].twoS;
-      for (const Stack& ro : rows[qo])
-        for (const Stack& ri : rows[qi]) {
-          const double sv = so.red[ro.s][ri.s];
-          if (sv == 0.0) continue;
-          const Mat* Ob = nullptr;
-          if (O) {
-            auto it = O->find({ro.qp, ri.qp});
-            if (it == O->end()) continue;
-            Ob = &it->second;
-          } else if (ro.qp != ri.qp) {
-            continue;
-          }
-          const int Sli = prev[ri.qp].twoS, Slo = prev[ro.qp].twoS;
-          const double cf = left ? ctilde(Sli, sS[ri.s], Sin, kO, so.k, K, Slo, sS[ro.s], Sout)
-                                 : ctilde(sS[ri.s], Sli, Sin, so.k, kO, K, sS[ro.s], Slo, Sout);
-          if (cf == 0.0) continue;
-          const double f = cf * sv;
-          for (int c = 0; c < ri.d; ++c)
-            for (int r = 0; r < ro.d; ++r) M(ro.r0 + r, ri.r0 + c) += f * (Ob ? (*Ob)(r, c) : (r == c ? 1.0 : 0.0));
-        }
-      return M;
-    };
-    std::map<std::pair<int, int>, Mat> Hn, Sn;
-    for (int qo = 0; qo < int(cur.size()); ++qo)
-      for (int qi = 0; qi < int(cur.size()); ++qi) {
-        if (cur[qo].N != cur[qi].N) continue;
-        if (cur[qo].twoS == cur[qi].twoS) {
-          Mat M(Q[qo].r, Q[qi].r);
-          if (have_H) {
-            Mat X = coupled(qo, qi, &Hc, 0, I, 0);
-            for (size_t i = 0; i < M.a.size(); ++i) M.a[i] += X.a[i];
-          }
-          if (have_S) {
-            Mat X = coupled(qo, qi, &Sc, 2, Sop, 0);
-            const double c = -std::sqrt(3.0) * H.J;
-            for (size_t i = 0; i < M.a.size(); ++i) M.a[i] += c * X.a[i];
-          }
-          Hn[{qo, qi}] = ab(atb(Q[qo], M), Q[qi]);
-        }
-        if (triangle(cur[qi].twoS, 2, cur[qo].twoS)) {
-          Mat X = coupled(qo, qi, nullptr, 0, Sop, 2);
-          Sn[{qo, qi}] = ab(atb(Q[qo], X), Q[qi]);
-        }
-      }
-    Hc.swap(Hn);
-    Sc.swap(Sn);
-    have_H = have_S = true;
+    heis_step(chain[k - 1], cur, Q, left, H.J, k > 1, Hc, Sc);
   }
   Hout.swap(Hc);
   Sout.swap(Sc);
@@ -550,6 +572,56 @@ std::string build_side_ops(const OpTable& t, bool left_side, const std::vector<s
       const double* s = &out.arena[out.blocks[src].off];  // co x ro  (rows qo, cols qi)
       for (int c = 0; c < co; ++c)
         for (int r = 0; r < ro; ++r) m[r + size_t(c) * ro] = f * s[c + size_t(r) * co];
+    }
+  }
+  return "";
+}
+
+std::string heis_grow(const HeisBlock& old, const std::vector<Sector>& cur, const std::vector<std::vector<double>>& Q,
+                      bool left, double J, HeisBlock& out) {
+  const std::vector<int> r0 = stacked_rows(old.sec, cur, SU2_SITE_SPIN_HALF);
+  if (Q.size() != cur.size()) return "MPS tensor does not match the new bond";
+  std::vector<Mat> Qm(cur.size());
+  for (size_t qo = 0; qo < cur.size(); ++qo) {
+    if (r0[qo] < cur[qo].dim) return "bond dimension exceeds the states available from the previous bond";
+    if (Q[qo].size() != size_t(r0[qo]) * cur[qo].dim) return "MPS tensor does not match the stacked rows of its sector";
+    Qm[qo] = Mat(r0[qo], cur[qo].dim);
+    Qm[qo].a = Q[qo];
+  }
+  std::map<std::pair<int, int>, Mat> Hc, Sc;
+  for (const auto& kv : old.H) {
+    Mat m(old.sec[kv.first.first].dim, old.sec[kv.first.second].dim);
+    m.a = kv.second;
+    Hc[kv.first] = std::move(m);
+  }
+  for (const auto& kv : old.S) {
+    Mat m(old.sec[kv.first.first].dim, old.sec[kv.first.second].dim);
+    m.a = kv.second;
+    Sc[kv.first] = std::move(m);
+  }
+  heis_step(old.sec, cur, Qm, left, J, old.grown, Hc, Sc);
+  HeisBlock nb;
+  nb.sec = cur;
+  nb.grown = true;
+  for (auto& kv : Hc) nb.H[kv.first] = std::move(kv.second.a);
+  for (auto& kv : Sc) nb.S[kv.first] = std::move(kv.second.a);
+  out = std::move(nb);
+  return "";
+}
+
+std::string heis_side_ops(const OpTable& t, bool left_side, const HeisBlock& b, SideOps& out) {
+  const auto& ops = left_side ? t.lops : t.rops;
+  out = SideOps();
+  out.host_values = true;
+  for (int oid = 0; oid < int(ops.size()); ++oid) {
+    const BlockOp& op = ops[oid];
+    if (op.kind == OP_IDENTITY) continue;
+    if (op.kind != OP_MPS_RENORM) return "a Heisenberg block holds only its H and S operators";
+    const auto& src = (op.name == "H") ? b.H : b.S;
+    for (auto [qo, qi] : allowed(op, b.sec)) {
+      add_block(out, oid, qo, qi, b.sec[qo].dim, b.sec[qi].dim);
+      auto it = src.find({qo, qi});
+      if (it != src.end()) std::copy(it->second.begin(), it->second.end(), &out.arena[out.blocks.back().off]);
     }
   }
   return "";

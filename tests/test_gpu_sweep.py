@@ -1,4 +1,5 @@
-"""The library's two-site sweep on the GPU (ab initio model, S = 0).
+"""The library's two-site sweep on the GPU (ab initio model and Heisenberg
+chain, S = 0).
 
 * Bonds that keep every multiplet: every window's energy is the full-CI
   ground-state energy (native FP64 and split paths).
@@ -9,6 +10,9 @@
   predicted start vector is the eigenvector (one or two Davidson
   iterations); with truncated bonds the energies and the Rayleigh quotients
   of the predicted start vectors equal the oracle's predicted sweep.
+* The spin-1/2 Heisenberg chain (L = 12, D = 32, four sweeps): every window
+  from the second half-sweep on equals exact diagonalisation; with D = 4
+  the energies equal the oracle's sweep.
 """
 import numpy as np
 import pytest
@@ -113,3 +117,41 @@ def test_predicted_sweep_matches_oracle(ctx, prec, tol):
     rq = np.array([x[1] for x in so])
     assert np.abs(e0[1:] - rq[1:]).max() < 1e-7, (e0, rq)
     assert it[cfg.L - 1] <= 2  # the turn starts from the previous eigenvector
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_heisenberg_sweep_c1_equals_exact_diagonalisation(ctx, prec):
+    """The spin-1/2 Heisenberg chain, L = 12, D = 32, four sweeps from the
+    seeded MPS with wavefunction prediction: from the second half-sweep on
+    every window holds the exact ground state."""
+    import paper_2309_16724_gb300 as P
+    from oracle import ed
+    cfg = synth.CONFIGS["heis12"]
+    chain = synth.bond_sector_chain(cfg, cfg.L - 2)
+    sw = P.Sweep(ctx, None, None, chain, cfg.N, cfg.D, prec=prec, tol=1e-10, seed=cfg.seed, predict=True)
+    e, w, it, e0 = sw.run(8 * (cfg.L - 1), stats=True)
+    sw.close()
+    assert ctx.status() == 0
+    E0 = ed.heisenberg_levels(12, 0)[0]
+    assert e.min() >= E0 - 1e-9
+    assert np.abs(e[cfg.L - 1:] - E0).max() < 1e-9
+    assert np.all(np.abs(w) < 1e-16)
+    assert it[cfg.L - 1:].max() <= (2 if prec == 0 else 3), it
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-8)])
+def test_heisenberg_truncated_sweep_matches_oracle(ctx, prec, tol):
+    import paper_2309_16724_gb300 as P
+    cfg = synth.CONFIGS["heis12"]
+    chain = synth.bond_sector_chain(cfg, cfg.L - 2)
+    sw = P.Sweep(ctx, None, None, chain, cfg.N, 4, prec=prec, tol=1e-10, seed=cfg.seed, predict=True)
+    e, w, it, e0 = sw.run(4 * (cfg.L - 1), stats=True)
+    sw.close()
+    assert ctx.status() == 0
+    so = []
+    eo, wo = osweep.sweep(cfg, 4, 4, tol=1e-10, predict=True, stats=so)
+    assert np.abs(e - eo).max() < tol, (e, eo)
+    rq = np.array([x[1] for x in so])
+    assert np.abs(e0[1:] - rq[1:]).max() < 1e-7, (e0, rq)
+    wl = w[w > 0]
+    assert np.allclose(np.sort(wl), np.sort(wo[wo > 0]), rtol=1e-5, atol=1e-12)
