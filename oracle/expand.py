@@ -16,6 +16,13 @@ Oracle module (test infrastructure only).
    same seeded MPS; H_eff = P^T H P is formed with the plain Heisenberg
    Hamiltonian and applied to psi.  This pins the renormalised block
    operators as well.
+3. ``abinitio_full_projection``: the same for the ab initio Hamiltonian:
+   the multiplets of both blocks and the two-site basis written out with
+   Clebsch-Gordan couplings as vectors of the determinant space (one bit
+   per spin-orbital, creators in ascending order, so that block x site
+   products need no sign), H the full-CI matrix of the N-electron, S_z = S
+   space; P^T H P pins the normal/complementary operators on truncated
+   bonds too.
 """
 from __future__ import annotations
 
@@ -270,3 +277,107 @@ def heisenberg_full_projection(cfg, blocks, left, right, psi, J=1.0):
                 basis.append(v)
     P = np.array(basis).T                      # dim x psi_len, column-major block order
     return P.T @ H_apply(P @ psi), P
+
+
+# ---------------------------------------------------------------------------
+# ab initio: explicit block bases in the determinant space of the orbitals
+
+# the site multiplets of a spatial orbital as vectors over its four
+# occupation patterns (bit 0: spin-up, bit 1: spin-down; the doubly occupied
+# pattern is c+_up c+_dn |0>), keyed by (site state, twoM)
+_ORB_SITE = {(0, 0): np.eye(4)[0], (1, 1): np.eye(4)[1], (1, -1): np.eye(4)[2], (2, 0): np.eye(4)[3]}
+
+
+def _orbital_block_states(seed, chain, n_orb, mps_side):
+    """Explicit vectors of the multiplets (all M) of a block of n_orb orbitals
+    grown by the seeded MPS over ``chain``: dict (sector, row, twoM) ->
+    vector over the block's 4^n_orb occupation patterns, pattern bit
+    2 j + s for local orbital j (left block: local = global orbital; right
+    block: local 0 is its leftmost orbital).  Every factor is a product of
+    creators in ascending spin-orbital order, so the product of a block
+    state and a site state on a higher orbital is the determinant of the
+    union of their patterns, with no sign."""
+    sk = synth.SPATIAL_ORBITAL
+    sites = synth.site_states(sk)
+    left = mps_side == envmod.SIDE_MPS_L
+    states = {(0, 0, 0): np.array([1.0])}
+    for k in range(1, n_orb + 1):
+        prev, cur = chain[k - 1], chain[k]
+        A = envmod.mps_tensor(seed, mps_side, k, prev, cur, sk)
+        new = {}
+        for qo, (rows, Q) in A.items():
+            So = cur[qo][1]
+            for M in range(-So, So + 1, 2):
+                vecs = []
+                for (qp, s, r0, dp) in rows:
+                    Sp, ts = prev[qp][1], sites[s][1]
+                    for r in range(dp):
+                        v = np.zeros(4 ** k)
+                        for mp in range(-Sp, Sp + 1, 2):
+                            ms = M - mp
+                            if abs(ms) > ts:
+                                continue
+                            if left:     # [block x site]: the site is the highest orbital
+                                c = cg(Sp, mp, ts, ms, So, M)
+                                term = np.kron(_ORB_SITE[(s, ms)], states[(qp, r, mp)])
+                            else:        # [site x block]: the site is the lowest orbital
+                                c = cg(ts, ms, Sp, mp, So, M)
+                                term = np.kron(states[(qp, r, mp)], _ORB_SITE[(s, ms)])
+                            if c != 0.0:
+                                v += c * term
+                        vecs.append(v)
+                W = np.array(vecs).T @ Q
+                for r in range(Q.shape[1]):
+                    new[(qo, r, M)] = W[:, r]
+        states = new
+    return chain[n_orb], states
+
+
+def abinitio_full_projection(cfg, blocks, n, h, eri):
+    """H_eff = P^T H P of the ab initio Hamiltonian (Eq. 1) for the seeded
+    MPS of cfg at its middle bond, with P the explicit two-site basis
+    (((L s1) j_L1 (s2 R) j_2R) S, M = S) in the N-electron, S_z = S
+    determinant space, and H the full-CI matrix of that space.  Small L."""
+    from . import fci
+    L, N, twoS = cfg.L, cfg.N, cfg.twoS
+    nl, nr = cfg.n_left, cfg.n_right
+    lsec, Ls = _orbital_block_states(cfg.seed, synth.bond_sector_chain(cfg, nl), nl, envmod.SIDE_MPS_L)
+    rsec, Rs = _orbital_block_states(cfg.seed, synth.bond_sector_chain(cfg, nr), nr, envmod.SIDE_MPS_R)
+    sites = synth.site_states(synth.SPATIAL_ORBITAL)
+    H, dets = fci.hamiltonian_sector(h, eri, N, twoS)
+    dets = np.array(dets, dtype=np.int64)
+    P = np.zeros((4 ** L, n))
+    for B in blocks:
+        Sa, Sb = lsec[B.a][1], rsec[B.b][1]
+        t1, t2 = sites[B.s1][1], sites[B.s2][1]
+        for ra in range(B.rows):
+            for rb in range(B.cols):
+                v = np.zeros(4 ** L)
+                for mL in range(-B.jL1, B.jL1 + 1, 2):
+                    mR = twoS - mL
+                    if abs(mR) > B.j2R:
+                        continue
+                    cS = cg(B.jL1, mL, B.j2R, mR, twoS, twoS)
+                    if cS == 0.0:
+                        continue
+                    for ma in range(-Sa, Sa + 1, 2):
+                        m1 = mL - ma
+                        if abs(m1) > t1:
+                            continue
+                        cl = cg(Sa, ma, t1, m1, B.jL1, mL)
+                        if cl == 0.0:
+                            continue
+                        left = np.kron(_ORB_SITE[(B.s1, m1)], Ls[(B.a, ra, ma)])
+                        for mb in range(-Sb, Sb + 1, 2):
+                            m2 = mR - mb
+                            if abs(m2) > t2:
+                                continue
+                            cr = cg(t2, m2, Sb, mb, B.j2R, mR)
+                            if cr == 0.0:
+                                continue
+                            right = np.kron(Rs[(B.b, rb, mb)], _ORB_SITE[(B.s2, m2)])
+                            # pattern: left orbitals below the right ones
+                            v += cS * cl * cr * np.kron(right, left)
+                P[:, B.offset + ra + rb * B.rows] = v
+    P = P[dets, :]
+    return P.T @ H @ P, P
