@@ -6,7 +6,9 @@ The default workload is the L = N = 48, D = 4096 ab initio configuration
 (qc48).  Beside the split-precision value the line carries the native-FP64
 path's rate on the same workload (a term shard of it, timed), the split/FP64
 ratio and the split error against the FP64 result on that shard, and the
-oracle timed on the host cores on a flop-weighted sample.
+oracle timed on the host cores on a flop-weighted sample; besides, the ab
+initio block (qc32 from the seeded integrals), the out-of-core block (qc64)
+and two sweeps with wavefunction prediction (the Heisenberg chain and qc16).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME]
                   [--prec split|fp64] [--impl ours|reference]
@@ -301,6 +303,7 @@ def main():
                     help="GB of operator blocks kept on the device in the out-of-core block")
     ap.add_argument("--out-of-core-steps", type=int, default=2, help="timed H.psi of the out-of-core block")
     ap.add_argument("--no-out-of-core", action="store_true", help="skip the out-of-core block")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the sweep block")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -575,6 +578,42 @@ def main():
             ooc = {"workload": args.out_of_core_config, "failed": str(ex)}
 
     mark("out_of_core")
+    # two-site sweeps with wavefunction prediction on the split path: the
+    # Heisenberg chain L = 12, D = 32, four sweeps (every window from the
+    # second half-sweep on holds the ground state), and the L = N = 16 ab
+    # initio Hamiltonian of the seeded integrals, D = 512, one full sweep
+    sweeps = None
+    if split and rank == 0 and not args.no_sweep:
+        sweeps = {}
+        for name, n_steps in (("heis12", 8 * 11), ("qc16", 2 * 15)):
+            try:
+                scfg = synth.CONFIGS[name]
+                chain = synth.bond_sector_chain(scfg, scfg.L - 2)
+                if scfg.site_kind == synth.SPIN_HALF:
+                    hh = ee = None
+                else:
+                    hh, ee = synth.integrals(scfg.L, scfg.seed)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                sw = P.Sweep(ctx, hh, ee, chain, scfg.N, scfg.D, prec=P.SU2_SPLIT_BF16, tol=1e-8, seed=scfg.seed,
+                             predict=True)
+                e, w, it, _ = sw.run(n_steps, stats=True)
+                sw.close()
+                torch.cuda.synchronize()
+                status_ok(f"the {name} sweep")
+                half = scfg.L - 1
+                sweeps[name] = {"L": scfg.L, "N": scfg.N, "D": scfg.D, "windows": n_steps,
+                                "half_sweeps": n_steps // half, "s": time.perf_counter() - t1,
+                                "davidson_iterations": int(it.sum()), "energy_last": float(e[-1]),
+                                "energy_min": float(e.min()),
+                                "energy_spread_after_first_half": float(e[half:].max() - e[half:].min()),
+                                "max_discarded_weight": float(w.max()),
+                                "operators": ("Heisenberg, J = 1" if hh is None else
+                                              "ab initio from the seeded integrals, renormalised on the GPU")}
+            except Exception as ex:  # reported, not fatal
+                sweeps[name] = {"failed": str(ex)}
+
+    mark("sweeps")
     # roofline of the dominant kernel
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     name, (launches, ms, fl) = dom
@@ -618,6 +657,7 @@ def main():
             "fp64_path": fp64,
             "ab_initio": ab,
             "out_of_core": ooc,
+            "sweeps": sweeps,
             "wall_s": wall,
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                     "steps": e2e_steps},

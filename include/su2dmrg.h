@@ -42,9 +42,13 @@ enum su2_status {
 /* Arithmetic of the sector GEMMs of H.psi. */
 enum su2_prec {
   SU2_FP64 = 0,        /* native FP64 (CUDA-core DFMA)                       */
-  SU2_SPLIT_BF16 = 1   /* FP64 operands cut into BF16 slices, tcgen05 tensor
+  SU2_SPLIT_BF16 = 1,  /* FP64 operands cut into BF16 slices, tcgen05 tensor
                           cores with FP32 accumulation, exact per K-chunk,
                           recombined to FP64                                  */
+  SU2_SPLIT_FP8 = 2    /* reserved, not built: FP8 E4M3 slices would need
+                          about ten slices and 55 slice products per 16 K
+                          against 15 for BF16 (slower at twice the rate);
+                          every call rejects it with SU2_EINVAL              */
 };
 
 enum su2_site_kind { SU2_SITE_SPIN_HALF = 0, SU2_SITE_ORBITAL = 1 };
@@ -342,6 +346,13 @@ int su2_davidson_step(su2_ctx* ctx, su2_dav* dav, double* theta, double* resnorm
 int su2_davidson_solve(su2_ctx* ctx, su2_dav* dav, double* theta, double* resnorm,
                        int32_t* iterations);
 int su2_energy(const su2_dav* dav, double* E);
+/* The energy as an expectation value (a10's check of the Davidson
+ * eigenvalue): H.x recomputed on the path `prec` for the current Ritz vector
+ * x, *rq = <x|Hx> / <x|x> and, if resnorm is not NULL, *resnorm =
+ * ||Hx - rq x|| / ||x||.  Synchronises the context stream; allocates two
+ * device vectors of psi_len for the call.  SU2_EINVAL for an unknown
+ * precision; the device status word as su2_apply_heff_host. */
+int su2_energy_check(su2_ctx* ctx, su2_dav* dav, int32_t prec, double* rq, double* resnorm);
 /* Current Ritz vector (unit norm, largest-magnitude entry positive). */
 int su2_davidson_vector(su2_ctx* ctx, su2_dav* dav, double* x_dev);
 int su2_davidson_destroy(su2_dav* dav);

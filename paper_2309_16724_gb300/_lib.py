@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsu2dmrg.so")
 
 SU2_OK, SU2_EINVAL, SU2_ENOMEM, SU2_ECUDA, SU2_ETIMEOUT, SU2_ENOTCONV = range(6)
-SU2_FP64, SU2_SPLIT_BF16 = 0, 1
+SU2_FP64, SU2_SPLIT_BF16, SU2_SPLIT_FP8 = 0, 1, 2   # FP8: reserved, rejected by the library
 SU2_SITE_SPIN_HALF, SU2_SITE_ORBITAL = 0, 1
 (SU2_MODEL_HEISENBERG, SU2_MODEL_QC_SKELETON, SU2_MODEL_CASIMIR_S2, SU2_MODEL_CASIMIR_N,
  SU2_MODEL_AB_INITIO) = range(5)
@@ -24,7 +24,7 @@ SYMBOLS = [
     "su2_ctx_create", "su2_ctx_destroy", "su2_last_error", "su2_ctx_status", "su2_ctx_wait", "su2_build_sectors", "su2_sectors_query",
     "su2_sectors_destroy", "su2_build_environment", "su2_env_query", "su2_env_tasks", "su2_env_terms", "su2_env_operator_block", "su2_env_destroy",
     "su2_apply_heff", "su2_apply_heff_host", "su2_apply_heff_static_scratch", "su2_diag_heff", "su2_davidson_create", "su2_davidson_step",
-    "su2_davidson_solve", "su2_energy", "su2_davidson_vector", "su2_davidson_destroy",
+    "su2_davidson_solve", "su2_energy", "su2_energy_check", "su2_davidson_vector", "su2_davidson_destroy",
     "su2_profile_enable", "su2_profile_reset", "su2_profile_read", "su2_hash_group",
     "su2_sweep_create", "su2_sweep_run", "su2_sweep_destroy",
 ]
@@ -121,6 +121,7 @@ def lib():
                                          C.POINTER(C.c_int32)]
         L.su2_energy.argtypes = [vp, C.POINTER(C.c_double)]
         L.su2_davidson_vector.argtypes = [vp, vp, vp]
+        L.su2_energy_check.argtypes = [vp, vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.su2_davidson_destroy.argtypes = [vp]
         L.su2_profile_enable.argtypes = [vp, C.c_int32]
         L.su2_profile_reset.argtypes = [vp]
@@ -423,6 +424,13 @@ class Davidson:
         e = C.c_double()
         self.ctx.check(lib().su2_energy(self.h, C.byref(e)))
         return e.value
+
+    def energy_check(self, prec=SU2_FP64):
+        """(<x|Hx>/<x|x>, ||Hx - rq x||/||x||) of the current Ritz vector x,
+        H.x recomputed on the path `prec` (su2_energy_check)."""
+        rq, res = C.c_double(), C.c_double()
+        self.ctx.check(lib().su2_energy_check(self.ctx.h, self.h, prec, C.byref(rq), C.byref(res)))
+        return rq.value, res.value
 
     def vector(self, out):
         self.ctx.check(lib().su2_davidson_vector(self.ctx.h, self.h, _vec(self.ctx, out, self.n, "device")))

@@ -709,6 +709,7 @@ int su2_apply_heff(su2_ctx* ctx, const su2_env* env_c, const double* psi_in, dou
     rc = split_apply(env, psi_in, psi_out, err);
     return rc ? fail(ctx, rc, err) : SU2_OK;
   }
+  if (prec == SU2_SPLIT_FP8) return fail(ctx, SU2_EINVAL, "FP8 slices are not built (SU2_SPLIT_FP8 is reserved)");
   if (prec != SU2_FP64) return fail(ctx, SU2_EINVAL, "unknown precision");
   CUDA_TRY(ctx, cudaMemsetAsync(psi_out, 0, size_t(n) * sizeof(double), ctx->stream));
   if (env->os.on) stream_begin(env->os, ctx->stream);
@@ -863,6 +864,11 @@ int su2_davidson_create(su2_ctx* ctx, const su2_env* env, const double* psi0, co
     if (opts->max_iter > 0) d->o.max_iter = opts->max_iter;
     d->o.prec = opts->prec;
     d->use_graph = opts->use_graph != 0;
+  }
+  if (d->o.prec != SU2_FP64 && d->o.prec != SU2_SPLIT_BF16) {
+    const bool fp8 = d->o.prec == SU2_SPLIT_FP8;
+    delete d;
+    return fail(ctx, SU2_EINVAL, fp8 ? "FP8 slices are not built (SU2_SPLIT_FP8 is reserved)" : "unknown precision");
   }
   if (d->use_graph && env->os.on) {
     delete d;
@@ -1093,6 +1099,50 @@ int su2_energy(const su2_dav* d, double* E) {
   if (!d || !E) return SU2_EINVAL;
   *E = d->theta;
   return SU2_OK;
+}
+
+int su2_energy_check(su2_ctx* ctx, su2_dav* d, int32_t prec, double* rq, double* resnorm) {
+  if (!ctx || !d || d->ctx != ctx || !rq) return fail(ctx, SU2_EINVAL, "null argument");
+  if (prec != SU2_FP64 && prec != SU2_SPLIT_BF16) return fail(ctx, SU2_EINVAL, "unknown precision");
+  int rc = set_device(ctx);
+  if (rc) return rc;
+  cudaStream_t s = ctx->stream;
+  const int64_t n = d->n;
+  double* hx = nullptr;
+  double* r = nullptr;
+  rc = dev_alloc(ctx, &hx, size_t(n));
+  if (!rc) rc = dev_alloc(ctx, &r, size_t(n));
+  if (!rc) rc = su2_apply_heff(ctx, d->env, d->x, hx, prec);
+  double xs[2] = {0.0, 0.0}, rr = 0.0;
+  if (!rc) {
+    dav_multidot(s, d->x, n, 1, d->x, n, d->partial, d->scal, 1.0);   // <x|x>
+    dav_multidot(s, d->x, n, 1, hx, n, d->partial, d->scal + 1, 1.0);  // <x|Hx>
+    if (cudaMemcpyAsync(xs, d->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      rc = fail(ctx, SU2_ECUDA, "energy check: reading the dot products");
+  }
+  if (!rc) rc = device_status_rc(ctx);
+  if (!rc && !(xs[0] > 0.0)) rc = fail(ctx, SU2_EINVAL, "energy check: the Ritz vector is zero");
+  if (!rc) {
+    *rq = xs[1] / xs[0];
+    if (resnorm) {
+      // ||Hx - rq x|| / ||x||
+      if (cudaMemcpyAsync(d->scal + 2, rq, sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        rc = fail(ctx, SU2_ECUDA, "energy check: upload");
+      if (!rc) {
+        dav_residual(s, d->x, hx, d->scal + 2, n, r);
+        dav_multidot(s, r, n, 1, r, n, d->partial, d->scal + 3, 1.0);
+        if (cudaMemcpyAsync(&rr, d->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+          rc = fail(ctx, SU2_ECUDA, "energy check: reading the residual");
+      }
+      if (!rc) *resnorm = std::sqrt(std::max(0.0, rr) / xs[0]);
+    }
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(hx);
+  cudaFree(r);
+  return rc;
 }
 
 int su2_davidson_vector(su2_ctx* ctx, su2_dav* d, double* x_dev) {

@@ -133,6 +133,41 @@ def test_davidson_heisenberg_equals_exact_diagonalisation(ctx):
     assert abs(dav.energy() - th) == 0.0
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_energy_check_is_the_expectation_value(ctx, prec):
+    """su2_energy_check: <x|Hx>/<x|x> of the converged Ritz vector, H.x
+    recomputed, equals the Davidson energy and exact diagonalisation, and
+    its residual is the solve's."""
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    cfg = synth.CONFIGS["heis12"]
+    sec, env = workload.build(ctx, cfg, prepare_split=True, n_slices=5)
+    psi0 = torch.from_numpy(synth.gaussian_psi(sec.psi_len, synth.psi_seed(cfg))).cuda()
+    dav = P.Davidson(ctx, env, psi0, tol=1e-10, prec=prec)
+    th, res, it, ok = dav.solve()
+    assert ok
+    rq, rres = dav.energy_check(prec)
+    assert abs(rq - th) <= 1e-12 * abs(th)
+    assert abs(rq - oed.heisenberg_levels(12, 0)[0]) < 1e-10
+    assert rres <= 2e-10
+    # the other path gives the same expectation value within the split error
+    rq2, _ = dav.energy_check(1 - prec)
+    assert abs(rq2 - rq) <= 1e-10 * abs(rq)
+
+
+def test_fp8_slices_are_rejected(ctx):
+    import paper_2309_16724_gb300 as P
+    from paper_2309_16724_gb300 import workload
+    sec, env = workload.build(ctx, SMALL[2])
+    x = torch.from_numpy(synth.gaussian_psi(sec.psi_len, 1)).cuda()
+    with pytest.raises(P.Su2Error) as ei:
+        P.apply_heff(ctx, env, x, torch.empty_like(x), P.SU2_SPLIT_FP8)
+    assert ei.value.code == P._lib.SU2_EINVAL and "FP8" in str(ei.value)
+    with pytest.raises(P.Su2Error) as ei:
+        P.Davidson(ctx, env, x, prec=P.SU2_SPLIT_FP8)
+    assert ei.value.code == P._lib.SU2_EINVAL and "FP8" in str(ei.value)
+
+
 def test_davidson_matches_oracle(ctx):
     import paper_2309_16724_gb300 as P
     from paper_2309_16724_gb300 import workload
