@@ -107,7 +107,8 @@ typedef struct {
                          integrals (ij|kl) (chemists' notation) at
                          ((i L + j) L + k) L + l; read during the call.
                          Other models: both NULL                          */
-  const double* mps_left;   /* SU2_MODEL_AB_INITIO, optional host arrays of the
+  const double* mps_left;   /* SU2_MODEL_AB_INITIO (and mps_right of the
+                               Heisenberg sweep), optional host arrays of the
                                MPS tensors that grow the left / right block
                                along its bond chain (NULL: the seeded tensors).
                                Layout: for each step k = 1 .. n of the chain,
@@ -115,7 +116,8 @@ typedef struct {
                                tensor as a column-major r0 x d_q matrix.  Its
                                rows stack the (previous-bond sector p, site
                                state s) pairs that couple to q, p outer and s
-                               inner (s: empty, one electron, two electrons),
+                               inner (orbital sites s: empty, one electron,
+                               two electrons; spin-1/2 sites: one state),
                                each pair d_p rows; N_p + N_s = N_q and the
                                spins obey the triangle rule.  The left block
                                grows by orbital k - 1, the right block by
@@ -396,6 +398,21 @@ int su2_sweep_create(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond_chai
  * iteration's Ritz value); any of the four may be NULL. */
 int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies, double* discarded,
                   int32_t* iterations, double* start_energies);
+/* Checkpoint of a sweep that stands at the start of a right-moving
+ * half-sweep (before its first window, or after a left-moving half-sweep
+ * turned at window 0): the bond chain of its right blocks (bonds of 0 ..
+ * L-2 sites, *n_bonds = L - 1) and the MPS tensors that grew them, in the
+ * layout of su2_hamiltonian.mps_right.  A sweep created from that chain and
+ * those tensors, with the same Hamiltonian, N and options, continues where
+ * this one stands (its first window starts from a seeded vector).  With
+ * bond_offset, sectors and mps all NULL the call returns the sizes
+ * (*n_sectors over all bonds, *n_values doubles); otherwise it fills the
+ * caller's arrays, whose capacities the caller passes in *n_bonds (entries
+ * of bond_offset minus one), *n_sectors and *n_values.  Host arrays; no
+ * device work.  SU2_EINVAL anywhere else in the sweep or for arrays that
+ * are too small. */
+int su2_sweep_checkpoint(su2_ctx* ctx, su2_sweep* sw, int32_t* n_bonds, int32_t* n_sectors, int64_t* n_values,
+                         int32_t* bond_offset, su2_sector* sectors, double* mps);
 int su2_sweep_destroy(su2_sweep* sw);
 
 /* Group order of the paper's hash-based semi-dynamic scheduling (Sec.

@@ -26,7 +26,7 @@ SYMBOLS = [
     "su2_apply_heff", "su2_apply_heff_host", "su2_apply_heff_static_scratch", "su2_diag_heff", "su2_davidson_create", "su2_davidson_step",
     "su2_davidson_solve", "su2_energy", "su2_energy_check", "su2_davidson_vector", "su2_davidson_destroy",
     "su2_profile_enable", "su2_profile_reset", "su2_profile_read", "su2_hash_group",
-    "su2_sweep_create", "su2_sweep_run", "su2_sweep_destroy",
+    "su2_sweep_create", "su2_sweep_run", "su2_sweep_checkpoint", "su2_sweep_destroy",
 ]
 
 
@@ -131,6 +131,8 @@ def lib():
         L.su2_sweep_create.argtypes = [vp, C.POINTER(Hamiltonian), C.POINTER(BondChain), C.c_int32,
                                        C.POINTER(SweepOpts), C.POINTER(vp)]
         L.su2_sweep_run.argtypes = [vp, vp, C.c_int32, vp, vp, vp, vp]
+        L.su2_sweep_checkpoint.argtypes = [vp, vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                           C.POINTER(C.c_int64), vp, vp, vp]
         L.su2_sweep_destroy.argtypes = [vp]
         for name in SYMBOLS:
             if name != "su2_last_error":
@@ -491,6 +493,21 @@ class Sweep:
         self.ctx.check(lib().su2_sweep_run(self.ctx.h, self.h, n_steps, e.ctypes.data, w.ctypes.data,
                                            it.ctypes.data, e0.ctypes.data))
         return (e, w, it, e0) if stats else (e, w)
+
+    def checkpoint(self):
+        """(right chain, MPS tensors) at the start of a right-moving
+        half-sweep (su2_sweep_checkpoint): Sweep(..., right_chain=chain,
+        mps_right=tensors) continues from there."""
+        nb, ns, nv = C.c_int32(), C.c_int32(), C.c_int64()
+        self.ctx.check(lib().su2_sweep_checkpoint(self.ctx.h, self.h, C.byref(nb), C.byref(ns), C.byref(nv),
+                                                  None, None, None))
+        off = np.zeros(nb.value + 1, dtype=np.int32)
+        sec = (Sector * max(1, ns.value))()
+        mps = np.zeros(max(1, nv.value))
+        self.ctx.check(lib().su2_sweep_checkpoint(self.ctx.h, self.h, C.byref(nb), C.byref(ns), C.byref(nv),
+                                                  off.ctypes.data, C.cast(sec, C.c_void_p), mps.ctypes.data))
+        chain = [[(sec[i].N, sec[i].twoS, sec[i].dim) for i in range(off[k], off[k + 1])] for k in range(nb.value)]
+        return chain, mps[:nv.value].copy()
 
     def close(self):
         if self.h:

@@ -1430,6 +1430,51 @@ int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies
   return SU2_OK;
 }
 
+int su2_sweep_checkpoint(su2_ctx* ctx, su2_sweep* sw, int32_t* n_bonds, int32_t* n_sectors, int64_t* n_values,
+                         int32_t* bond_offset, su2_sector* sectors, double* mps) {
+  if (!ctx || !sw || sw->ctx != ctx || !n_bonds || !n_sectors || !n_values)
+    return fail(ctx, SU2_EINVAL, "null argument");
+  if (sw->pos != 0 || sw->dir != 1)
+    return fail(ctx, SU2_EINVAL, "a checkpoint is taken at the start of a right-moving half-sweep (window 0)");
+  std::vector<std::vector<Sector>> chain;
+  std::vector<std::vector<std::vector<double>>> tensors;
+  if (sw->heis) {
+    for (size_t k = 0; k < sw->hR.size(); ++k) {
+      chain.push_back(sw->hR[k].sec);
+      tensors.push_back(k > 0 ? sw->hRq[k] : std::vector<std::vector<double>>());
+    }
+  } else {
+    const std::string err = sweep_right_state(sw->w, chain, tensors);
+    if (!err.empty()) return fail(ctx, SU2_EINVAL, err);
+  }
+  int32_t ns = 0;
+  int64_t nv = 0;
+  for (size_t k = 0; k < chain.size(); ++k) {
+    ns += int32_t(chain[k].size());
+    for (const auto& q : tensors[k]) nv += int64_t(q.size());
+  }
+  const bool sizes_only = !bond_offset && !sectors && !mps;
+  if (!sizes_only && (!bond_offset || !sectors || !mps)) return fail(ctx, SU2_EINVAL, "null output array");
+  if (!sizes_only && (*n_bonds < int32_t(chain.size()) || *n_sectors < ns || *n_values < nv))
+    return fail(ctx, SU2_EINVAL, "output arrays smaller than the checkpoint");
+  *n_bonds = int32_t(chain.size());
+  *n_sectors = ns;
+  *n_values = nv;
+  if (sizes_only) return SU2_OK;
+  int32_t at = 0;
+  int64_t pos = 0;
+  for (size_t k = 0; k < chain.size(); ++k) {
+    bond_offset[k] = at;
+    for (const Sector& q : chain[k]) sectors[at++] = su2_sector{q.N, q.twoS, q.dim};
+    for (const auto& q : tensors[k]) {
+      std::copy(q.begin(), q.end(), mps + pos);
+      pos += int64_t(q.size());
+    }
+  }
+  bond_offset[chain.size()] = at;
+  return SU2_OK;
+}
+
 int su2_sweep_destroy(su2_sweep* sw) {
   if (!sw) return SU2_EINVAL;
   if (sw->device >= 0) cudaSetDevice(sw->device);

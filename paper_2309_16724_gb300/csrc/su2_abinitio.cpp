@@ -1619,6 +1619,18 @@ std::string sweep_grow(SweepBlocks* w, int i, bool left, const std::vector<Secto
 // the 6j {j_k s2 S_b; S_b 0 j_k}, which is 1; no operator changes places, so
 // no fermionic sign enters.  The guess is laid out in the next window's
 // block order (build_blocks of its sectors).
+std::string sweep_right_state(SweepBlocks* w, std::vector<std::vector<Sector>>& chain,
+                              std::vector<std::vector<std::vector<double>>>& tensors) {
+  chain.clear();
+  tensors.clear();
+  for (size_t k = 0; k < w->Rb.size(); ++k) {
+    if (k > 0 && w->Rq[k].size() != w->Rb[k].lay.sec.size()) return "a right block's MPS tensor is not known";
+    chain.push_back(w->Rb[k].lay.sec);
+    tensors.push_back(k > 0 ? w->Rq[k] : std::vector<std::vector<double>>());
+  }
+  return "";
+}
+
 std::string sweep_predict(SweepBlocks* w, int i, bool right, const std::vector<Sector>& lsec,
                           const std::vector<Sector>& rsec, int N, const std::vector<Sector>& cur,
                           const std::vector<std::vector<double>>& rest, std::vector<double>& guess) {

@@ -149,6 +149,10 @@ std::string sweep_split(const std::vector<Block>& blocks, const double* psi, con
                         std::vector<std::vector<double>>* rest = nullptr, int site_kind = SU2_SITE_ORBITAL);
 std::string sweep_grow(SweepBlocks* w, int i, bool left, const std::vector<Sector>& cur,
                        const std::vector<std::vector<double>>& Q);
+// the bonds of the right blocks (0 .. L-2 orbitals) and the MPS tensors
+// that grew them (tensors[0] empty), for a checkpoint of the sweep
+std::string sweep_right_state(SweepBlocks* w, std::vector<std::vector<Sector>>& chain,
+                              std::vector<std::vector<std::vector<double>>>& tensors);
 // start vector of the next window (i+1 when `right`, else i-1) predicted
 // from window i's kept wavefunction (`rest` of sweep_split, after sweep_grow)
 std::string sweep_predict(SweepBlocks* w, int i, bool right, const std::vector<Sector>& lsec,

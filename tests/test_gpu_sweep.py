@@ -10,6 +10,9 @@ chain, S = 0).
   predicted start vector is the eigenvector (one or two Davidson
   iterations); with truncated bonds the energies and the Rayleigh quotients
   of the predicted start vectors equal the oracle's predicted sweep.
+* Checkpoint and resume: a sweep created from the right chain and MPS
+  tensors checkpointed after one full sweep repeats the energies of the
+  sweep that went on.
 * The spin-1/2 Heisenberg chain (L = 12, D = 32, four sweeps): every window
   from the second half-sweep on equals exact diagonalisation; with D = 4
   the energies equal the oracle's sweep.
@@ -155,3 +158,35 @@ def test_heisenberg_truncated_sweep_matches_oracle(ctx, prec, tol):
     assert np.abs(e0[1:] - rq[1:]).max() < 1e-7, (e0, rq)
     wl = w[w > 0]
     assert np.allclose(np.sort(wl), np.sort(wo[wo > 0]), rtol=1e-5, atol=1e-12)
+
+
+@pytest.mark.parametrize("model", ["abinitio", "heisenberg"])
+def test_sweep_checkpoint_resumes(ctx, model):
+    """A sweep resumed from the checkpoint taken after one full sweep (its
+    right blocks' bond chain and MPS tensors) gives the same energies and
+    discarded weights as the sweep that went on."""
+    import paper_2309_16724_gb300 as P
+    if model == "abinitio":
+        cfg = synth.Config("sw7", synth.SPATIAL_ORBITAL, 7, 6, 0, 6, 1002)
+        h, eri = synth.integrals(cfg.L, cfg.seed)
+        D = 6
+    else:
+        cfg = synth.CONFIGS["heis12"]
+        h = eri = None
+        D = 6
+    chain = synth.bond_sector_chain(cfg, cfg.L - 2)
+    a = P.Sweep(ctx, h, eri, chain, cfg.N, D, prec=0, tol=1e-10, seed=cfg.seed, predict=True)
+    a.run(1)
+    with pytest.raises(P.Su2Error):
+        a.checkpoint()          # not at the start of a right-moving half-sweep
+    a.run(2 * (cfg.L - 1) - 1)  # the rest of one full sweep: back at window 0
+    rchain, mps = a.checkpoint()
+    assert len(rchain) == cfg.L - 1 and mps.size > 0
+    ea, wa = a.run(2 * (cfg.L - 1))
+    a.close()
+    b = P.Sweep(ctx, h, eri, rchain, cfg.N, D, prec=0, tol=1e-10, seed=cfg.seed, predict=True, mps_right=mps)
+    eb, wb = b.run(2 * (cfg.L - 1))
+    b.close()
+    assert ctx.status() == 0
+    assert np.abs(ea - eb).max() < 1e-8, (ea, eb)
+    assert np.allclose(wa, wb, rtol=1e-5, atol=1e-12)
