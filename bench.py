@@ -606,7 +606,7 @@ def main():
                                 "half_sweeps": n_steps // half, "s": time.perf_counter() - t1,
                                 "davidson_iterations": int(it.sum()), "energy_last": float(e[-1]),
                                 "energy_min": float(e.min()),
-                                "energy_spread_after_first_half": float(e[half:].max() - e[half:].min()),
+                                "energy_end_of_each_half_sweep": [float(x) for x in e[half - 1::half]],
                                 "max_discarded_weight": float(w.max()),
                                 "operators": ("Heisenberg, J = 1" if hh is None else
                                               "ab initio from the seeded integrals, renormalised on the GPU")}
