@@ -7,10 +7,15 @@ the kept singular vectors (renormalisation, Sec. II.C).
 Oracle module (test infrastructure only).  Plain Python/NumPy, FP64.
 
 Readings (the paper gives no sweep algorithm):
-* Total spin S = 0: every two-site block has j_L1 = j_2R = j, so the
-  reduced wavefunction of the bond sector (N_L1, j) is one matrix with rows
-  (left sector a, site s1) and columns (site s2, right sector b), stacked as
-  in ``env.mps_tensor`` (previous sector outer, site state inner).
+* The reduced wavefunction across the bond between the two sites, for the
+  block that grows: moving right, one matrix per left sector (N_L1, j_L1)
+  with rows (left sector a, site s1) and columns (site s2, right sector b)
+  of every j_2R that couples with j_L1 to the target S, j_2R ascending (the
+  coupled states [(a s1)_jL1 x (s2 b)_j2R]^S are orthonormal, so its
+  singular values carry the weights of the left multiplets); moving left,
+  one matrix per right sector (N_2R, j_2R), rows concatenated over j_L1.
+  Stacks as in ``env.mps_tensor`` (previous sector outer, site state
+  inner).  At S = 0, j_L1 = j_2R and each matrix is one block row/column.
 * Truncation keeps the D largest sigma^2 (one per multiplet) over all
   sectors; ties go to the lower (N, 2S) sector, then the lower index.
   Singular values with sigma^2 <= 1e-24 of the total weight are never kept:
@@ -27,11 +32,13 @@ Readings (the paper gives no sweep algorithm):
   right block's own MPS tensor, b = [s3 x r'] (rows (r', s3)), into the
   blocks (k, s2, s3, r') of window i+1 with j_L1 = j_2R = S_b.  Moving left,
   C = M V_k is expanded over the left block's tensor, a = [a'' x s0], into
-  the blocks (a'', s0, s1, k) of window i-1 with j_L1 = j_2R = S_a.  At total
-  spin 0 the recoupling (j_k (s2 S_b)_j)_0 -> ((j_k s2)_{S_b} S_b)_0 is the
-  6j {j_k s2 S_b; S_b 0 j_k} times (-1)^(j_k+s2+S_b) sqrt((2 S_b+1)(2 j_k+1)),
-  which is 1 by the closed form of a 6j with a zero entry; no operator is
-  reordered, so there is no fermionic sign.  The predicted vector is the
+  the blocks (a'', s0, s1, k) of window i-1 with j_L1 = j_2R = S_a.  The
+  spins are recoupled: (j_k (s2 S_b)_j2R)_S -> ((j_k s2)_j' S_b)_S with
+  (-1)^(j_k+s2+S_b+S) sqrt((2j'+1)(2j_2R+1)) {j_k s2 j'; S_b S j_2R}, and
+  moving left ((S_a s1)_jL1 j_k)_S -> (S_a (s1 j_k)_j'')_S likewise; at
+  S = 0 the only term has j' = S_b (j'' = S_a) and the factor is exactly 1
+  (closed form of a 6j with a zero entry).  No operator is reordered, so
+  there is no fermionic sign.  The predicted vector is the
   truncated state itself, written in the next window's basis: its norm is
   sqrt(1 - discarded weight) and its Rayleigh quotient in the next window
   equals that of the truncated state in the window it came from.  At a turn
@@ -52,7 +59,7 @@ import numpy as np
 import synth
 from . import abinitio, davidson, heff, model, sectors
 from . import env as envmod
-from .su2 import triangle
+from .su2 import sixj, triangle
 
 
 def _stacks(prev, sites, Nq, Sq):
@@ -67,23 +74,48 @@ def _stacks(prev, sites, Nq, Sq):
     return rows, r0
 
 
-def _bond_matrices(psi, blocks, left, right, site_kind, N):
-    """{(N_L1, j): (left stacks, right stacks, matrix)} of an S = 0 two-site
-    wavefunction across the bond between the two sites."""
+def _bond_matrices(psi, blocks, left, right, site_kind, N, twoS=0, side="L"):
+    """The two-site wavefunction across the bond between the two sites, one
+    matrix per sector of the block that grows.  side 'L' (the left block
+    grows): key (N_L1, j_L1), rows the left stacks (a, s1) of that sector,
+    columns the right stacks (b, s2) of every j_2R coupling with j_L1 to S,
+    j_2R ascending: [(j_2R, b, s2, c0, d_b)].  side 'R': key (N_2R, j_2R),
+    columns its right stacks, rows the left stacks of every j_L1, ascending:
+    [(j_L1, a, s1, r0, d_a)].  Returns {key: (rows, cols, M)} with the stacks
+    of the growing side in ``_stacks``' 4-tuple form.  At S = 0 both forms
+    hold a single spin, j_L1 = j_2R."""
     sites = synth.site_states(site_kind)
     bidx = sectors.block_index(blocks)
-    keys = sorted({(left[B.a][0] + sites[B.s1][0], B.jL1) for B in blocks})
+    if side == "L":
+        keys = sorted({(left[B.a][0] + sites[B.s1][0], B.jL1) for B in blocks})
+    else:
+        keys = sorted({(right[B.b][0] + sites[B.s2][0], B.j2R) for B in blocks})
     out = {}
-    for (Nq, j) in keys:
-        lrows, nr = _stacks(left, sites, Nq, j)
-        rrows, nc = _stacks(right, sites, N - Nq, j)
-        M = np.zeros((nr, nc))
-        for (a, s1, r0, da) in lrows:
-            for (b, s2, c0, db) in rrows:
-                i = bidx.get((a, s1, s2, b, j, j))
-                if i is not None:
-                    M[r0:r0 + da, c0:c0 + db] = sectors.block_view(psi, blocks[i])
-        out[(Nq, j)] = (lrows, rrows, M)
+    for key in keys:
+        Nk, j = key
+        own, nown = _stacks(left if side == "L" else right, sites, Nk, j)
+        other, n_other = [], 0
+        No = N - Nk
+        for jo in range(abs(j - twoS), j + twoS + 1, 2):
+            st, n = _stacks(right if side == "L" else left, sites, No, jo)
+            other += [(jo, q, s_, n_other + o, d) for (q, s_, o, d) in st]
+            n_other += n
+        if side == "L":
+            M = np.zeros((nown, n_other))
+            for (a, s1, r0, da) in own:
+                for (jo, b, s2, c0, db) in other:
+                    i = bidx.get((a, s1, s2, b, j, jo))
+                    if i is not None:
+                        M[r0:r0 + da, c0:c0 + db] = sectors.block_view(psi, blocks[i])
+            out[key] = (own, other, M)
+        else:
+            M = np.zeros((n_other, nown))
+            for (jo, a, s1, r0, da) in other:
+                for (b, s2, c0, db) in own:
+                    i = bidx.get((a, s1, s2, b, jo, j))
+                    if i is not None:
+                        M[r0:r0 + da, c0:c0 + db] = sectors.block_view(psi, blocks[i])
+            out[key] = (other, own, M)
     return out
 
 
@@ -108,13 +140,13 @@ def _truncate(svals, D):
     return keep
 
 
-def isometry(psi, blocks, left, right, site_kind, N, D, side, with_rest=False):
+def isometry(psi, blocks, left, right, site_kind, N, D, side, with_rest=False, twoS=0):
     """New bond sectors and MPS tensor of the grown block (side 'L': the left
     block grows by site 1 with U; 'R': the right block grows by site 2 with
     V), and the discarded weight.  With ``with_rest`` also the rest of the
-    kept wavefunction per new sector: side 'L': (column stacks, U_k^T M);
-    side 'R': (row stacks, M V_k)."""
-    mats = _bond_matrices(psi, blocks, left, right, site_kind, N)
+    kept wavefunction per new sector: side 'L': (column stacks (j_2R, b, s2,
+    c0, d)), U_k^T M); side 'R': (row stacks (j_L1, a, s1, r0, d), M V_k)."""
+    mats = _bond_matrices(psi, blocks, left, right, site_kind, N, twoS, side)
     svd, svals = {}, {}
     for key, (lrows, rrows, M) in mats.items():
         U, s, Vt = np.linalg.svd(M, full_matrices=False)
@@ -124,9 +156,8 @@ def isometry(psi, blocks, left, right, site_kind, N, D, side, with_rest=False):
     # discarded weight: the sigma^2 not kept, summed directly
     dropped = sum(float(np.sum(np.delete(s, keep.get(k, [])) ** 2)) for k, s in svals.items())
     new = []
-    for (Nq, j), idx in keep.items():
-        Nb = Nq if side == "L" else N - Nq
-        new.append((Nb, j, len(idx), (Nq, j), idx))
+    for (Nk, j), idx in keep.items():
+        new.append((Nk, j, len(idx), (Nk, j), idx))
     new.sort()
     sec = [(Nb, j, d) for (Nb, j, d, _, _) in new]
     A, rest = {}, {}
@@ -146,46 +177,86 @@ def isometry(psi, blocks, left, right, site_kind, N, D, side, with_rest=False):
     return sec, A, dropped
 
 
-def predict_moving_right(rest, right, RA, next_blocks, next_n):
+def _recouple(j1, j2, j3, J, j12, j23):
+    """<((j1 j2) j12, j3) J | (j1, (j2 j3) j23) J> (twos arguments): the 6j
+    recoupling of three spins, (-1)^(j1+j2+j3+J) sqrt((2j12+1)(2j23+1))
+    {j1 j2 j12; j3 J j23}; 1 when J = 0."""
+    if J == 0:
+        return 1.0 if (j12 == j3 and j23 == j1) else 0.0
+    sg = -1.0 if ((j1 + j2 + j3 + J) // 2) % 2 else 1.0
+    return sg * np.sqrt((j12 + 1) * (j23 + 1)) * sixj(j1, j2, j12, j3, J, j23)
+
+
+def predict_moving_right(rest, right, RA, next_blocks, next_n, left_next=None, twoS=0, site_kind=None):
     """Start vector of window i+1 after the left block grew at window i:
     rest = isometry(..., 'L', with_rest=True)[3]; right = the right sectors
     of window i; RA = the MPS tensor of that right block ({b: (rows
-    [(r', s3, r0, d)], G)}, rows stacked (r', s3))."""
+    [(r', s3, r0, d)], G)}, rows stacked (r', s3)); left_next = the grown
+    left block's sectors (needed for S > 0).  The kept wavefunction
+    [k x (s2 x b)_j2R]^S, b = [s3 x r']^Sb, is recoupled to
+    [(k x s2)_j' x (s3 x r')_Sb]^S."""
     out = np.zeros(next_n)
     bidx = sectors.block_index(next_blocks)
-    for qo, (rrows, C) in rest.items():
-        for (b, s2, c0, db) in rrows:
+    sites = synth.site_states(site_kind) if site_kind is not None else None
+    for qo, (rcols, C) in rest.items():
+        jk = left_next[qo][1] if left_next is not None else None
+        for (j2R, b, s2, c0, db) in rcols:
             Sb = right[b][1]
             rows_b, G = RA[b]
+            X = None
             for (rp, s3, r0, drp) in rows_b:
-                i = bidx[(qo, s2, s3, rp, Sb, Sb)]
-                sectors.block_view(out, next_blocks[i])[:] += C[:, c0:c0 + db] @ G[r0:r0 + drp, :].T
+                if twoS == 0:
+                    terms = [(Sb, 1.0)]
+                else:
+                    t2 = sites[s2][1]
+                    terms = [(jp, _recouple(jk, t2, Sb, twoS, jp, j2R))
+                             for jp in range(abs(jk - t2), jk + t2 + 1, 2) if triangle(jp, Sb, twoS)]
+                for (jp, w) in terms:
+                    if w == 0.0:
+                        continue
+                    i = bidx[(qo, s2, s3, rp, jp, Sb)]
+                    if X is None:
+                        X = C[:, c0:c0 + db]
+                    sectors.block_view(out, next_blocks[i])[:] += w * (X @ G[r0:r0 + drp, :].T)
     return out
 
 
-def predict_moving_left(rest, left, LA, next_blocks, next_n):
+def predict_moving_left(rest, left, LA, next_blocks, next_n, right_next=None, twoS=0, site_kind=None):
     """Start vector of window i-1 after the right block grew at window i:
     rest = isometry(..., 'R', with_rest=True)[3]; left = the left sectors of
     window i; LA = the MPS tensor of that left block ({a: (rows
-    [(a'', s0, r0, d)], G)})."""
+    [(a'', s0, r0, d)], G)}); right_next = the grown right block's sectors
+    (needed for S > 0).  [(a x s1)_jL1 x k]^S, a = [a'' x s0]^Sa, is
+    recoupled to [(a'' x s0)_Sa x (s1 x k)_j'']^S."""
     out = np.zeros(next_n)
     bidx = sectors.block_index(next_blocks)
+    sites = synth.site_states(site_kind) if site_kind is not None else None
     for qo, (lrows, C) in rest.items():
-        for (a, s1, c0, da) in lrows:
+        jk = right_next[qo][1] if right_next is not None else None
+        for (jL1, a, s1, c0, da) in lrows:
             Sa = left[a][1]
             rows_a, G = LA[a]
             for (app, s0, r0, dapp) in rows_a:
-                i = bidx[(app, s0, s1, qo, Sa, Sa)]
-                sectors.block_view(out, next_blocks[i])[:] += G[r0:r0 + dapp, :] @ C[c0:c0 + da, :]
+                if twoS == 0:
+                    terms = [(Sa, 1.0)]
+                else:
+                    t1 = sites[s1][1]
+                    terms = [(jpp, _recouple(Sa, t1, jk, twoS, jL1, jpp))
+                             for jpp in range(abs(t1 - jk), t1 + jk + 1, 2) if triangle(Sa, jpp, twoS)]
+                for (jpp, w) in terms:
+                    if w == 0.0:
+                        continue
+                    i = bidx[(app, s0, s1, qo, Sa, jpp)]
+                    sectors.block_view(out, next_blocks[i])[:] += w * (G[r0:r0 + dapp, :] @ C[c0:c0 + da, :])
     return out
 
 
-def window(strings, Lb, Rb, N):
+def window(strings, Lb, Rb, N, twoS=0):
     """The two-site problem between blocks Lb and Rb: (apply, diag, blocks,
     psi length, left sectors, right sectors)."""
     table, env, ls, rs = abinitio.problem_from_blocks(strings, Lb, Rb)
-    blocks, n = sectors.build_blocks(ls, rs, synth.SPATIAL_ORBITAL, N, 0)
-    tasks = heff.build_tasks(table, ls, rs, blocks, 0)
+    blocks, n = sectors.build_blocks(ls, rs, synth.SPATIAL_ORBITAL, N, twoS)
+    tasks = heff.build_tasks(table, ls, rs, blocks, twoS)
     apply = lambda v: heff.apply_heff(table, env, tasks, blocks, n, v)
     diag = heff.diag_heff(table, env, tasks, blocks, n)
     return apply, diag, blocks, n, ls, rs
@@ -204,7 +275,7 @@ class HeisenbergBlock:
         return HeisenbergBlock(cur, H, S, self.J)
 
 
-def heisenberg_window(Lb, Rb, N, J=1.0):
+def heisenberg_window(Lb, Rb, N, J=1.0, twoS=0):
     """The two-site problem of the spin-1/2 Heisenberg chain between blocks
     Lb and Rb: (apply, diag, blocks, psi length, left sectors, right
     sectors)."""
@@ -218,8 +289,8 @@ def heisenberg_window(Lb, Rb, N, J=1.0):
             env[(side, oid)] = {(qo, qi): vals.get((qo, qi), np.zeros((b.sectors[qo][2], b.sectors[qi][2])))
                                 for (qo, qi) in envmod.allowed_blocks(op, b.sectors)}
     ls, rs = Lb.sectors, Rb.sectors
-    blocks, n = sectors.build_blocks(ls, rs, synth.SPIN_HALF, N, 0)
-    tasks = heff.build_tasks(table, ls, rs, blocks, 0)
+    blocks, n = sectors.build_blocks(ls, rs, synth.SPIN_HALF, N, twoS)
+    tasks = heff.build_tasks(table, ls, rs, blocks, twoS)
     apply = lambda v: heff.apply_heff(table, env, tasks, blocks, n, v)
     diag = heff.diag_heff(table, env, tasks, blocks, n)
     return apply, diag, blocks, n, ls, rs
@@ -235,7 +306,8 @@ def _solve(win, seed, tol, x0=None):
 
 
 def sweep(cfg, D, n_half, tol=1e-9, h=None, eri=None, predict=False, stats=None, J=1.0):
-    """Energies of every two-site step of n_half half-sweeps (S = 0), with the
+    """Energies of every two-site step of n_half half-sweeps (target spin
+    cfg.twoS / 2), with the
     initial right blocks from cfg's seeded MPS; returns (energies, discarded
     weights).  The model follows cfg's site kind: the ab initio Hamiltonian
     of the integrals (h, eri; default: cfg's seeded ones) on orbital sites,
@@ -243,9 +315,8 @@ def sweep(cfg, D, n_half, tol=1e-9, h=None, eri=None, predict=False, stats=None,
     ``predict`` every window after the first starts from the wavefunction
     predicted from the previous one.  A list ``stats`` receives (Davidson
     iterations, Rayleigh quotient of the start vector) per step."""
-    assert cfg.twoS == 0
     kind = cfg.site_kind
-    L, N = cfg.L, cfg.N
+    L, N, twoS = cfg.L, cfg.N, cfg.twoS
     if kind == synth.SPATIAL_ORBITAL:
         if h is None:
             h, eri = synth.integrals(cfg.L, cfg.seed)
@@ -253,12 +324,12 @@ def sweep(cfg, D, n_half, tol=1e-9, h=None, eri=None, predict=False, stats=None,
         R = [abinitio.RightBlock(strings, L)]
         Lbs = [abinitio.LeftBlock(strings, L)] + [None] * (L - 2)
         grow = lambda b, sec, A, left: b.grown(sec, A)
-        make_window = lambda Lb, Rb: window(strings, Lb, Rb, N)
+        make_window = lambda Lb, Rb: window(strings, Lb, Rb, N, twoS)
     else:
         R = [HeisenbergBlock([(0, 0, 1)], J=J)]
         Lbs = [HeisenbergBlock([(0, 0, 1)], J=J)] + [None] * (L - 2)
         grow = lambda b, sec, A, left: b.grown(sec, A, left)
-        make_window = lambda Lb, Rb: heisenberg_window(Lb, Rb, N, J)
+        make_window = lambda Lb, Rb: heisenberg_window(Lb, Rb, N, J, twoS)
     chain = synth.bond_sector_chain(cfg, L - 2)
     # R[m]: right block of the last m sites; RA[m] / LA[m]: the MPS tensor
     # that grew R[m] from R[m-1] / Lbs[m] from Lbs[m-1]
@@ -283,19 +354,19 @@ def sweep(cfg, D, n_half, tol=1e-9, h=None, eri=None, predict=False, stats=None,
             energies.append(theta)
             guess = x   # at a turn the next window is this one
             if half % 2 == 0 and i < L - 2:
-                sec, A, w, rest = isometry(x, blocks, ls, rs, kind, N, D, "L", with_rest=True)
+                sec, A, w, rest = isometry(x, blocks, ls, rs, kind, N, D, "L", with_rest=True, twoS=twoS)
                 Lbs[i + 1] = grow(Lb, sec, A, True)
                 LA[i + 1] = A
                 discarded.append(w)
                 if predict:
-                    nb, nn = sectors.build_blocks(Lbs[i + 1].sectors, R[L - 3 - i].sectors, kind, N, 0)
-                    guess = predict_moving_right(rest, rs, RA[L - 2 - i], nb, nn)
+                    nb, nn = sectors.build_blocks(Lbs[i + 1].sectors, R[L - 3 - i].sectors, kind, N, twoS)
+                    guess = predict_moving_right(rest, rs, RA[L - 2 - i], nb, nn, sec, twoS, kind)
             elif half % 2 == 1 and i > 0:
-                sec, A, w, rest = isometry(x, blocks, ls, rs, kind, N, D, "R", with_rest=True)
+                sec, A, w, rest = isometry(x, blocks, ls, rs, kind, N, D, "R", with_rest=True, twoS=twoS)
                 R[L - 1 - i] = grow(Rb, sec, A, False)
                 RA[L - 1 - i] = A
                 discarded.append(w)
                 if predict:
-                    nb, nn = sectors.build_blocks(Lbs[i - 1].sectors, R[L - 1 - i].sectors, kind, N, 0)
-                    guess = predict_moving_left(rest, ls, LA[i], nb, nn)
+                    nb, nn = sectors.build_blocks(Lbs[i - 1].sectors, R[L - 1 - i].sectors, kind, N, twoS)
+                    guess = predict_moving_left(rest, ls, LA[i], nb, nn, sec, twoS, kind)
     return np.array(energies), np.array(discarded)

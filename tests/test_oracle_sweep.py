@@ -16,8 +16,13 @@
 * The spin-1/2 Heisenberg chain (L = 12, D = 32, four sweeps): every window
   from the second half-sweep on equals exact diagonalisation; with D = 4 the
   energies are variational.
+* Targets with S > 0 (S = 1/2, 1): exact sweeps equal full CI and exact
+  diagonalisation, the prediction (which recouples by a 6j) keeps the
+  truncated-state identities, and the S = 0 factor planted in its place
+  breaks them.
 """
 import numpy as np
+import pytest
 
 import synth
 from oracle import fci, sectors, sweep
@@ -77,73 +82,78 @@ def test_isometry_orthonormal_and_truncated():
 # the window it came from.  Both windows' H_eff are projections P^T H P of
 # the same Hamiltonian onto spaces that contain that state.
 
-def _from_bond_matrices(mats, blocks, n):
-    """Inverse of the bond-matrix view: {(N_L1, j): (left stacks, right
-    stacks, M)} back into the flat two-site vector."""
+def _from_bond_matrices(mats, blocks, n, side):
+    """Inverse of the bond-matrix view (``sweep._bond_matrices``'s layout)
+    back into the flat two-site vector."""
     out = np.zeros(n)
     bidx = sectors.block_index(blocks)
-    for (Nq, j), (lrows, rrows, M) in mats.items():
-        for (a, s1, r0, da) in lrows:
-            for (b, s2, c0, db) in rrows:
-                sectors.block_view(out, blocks[bidx[(a, s1, s2, b, j, j)]])[:] = M[r0:r0 + da, c0:c0 + db]
+    for (Nk, j), (rows, cols, M) in mats.items():
+        if side == "L":
+            for (a, s1, r0, da) in rows:
+                for (jo, b, s2, c0, db) in cols:
+                    sectors.block_view(out, blocks[bidx[(a, s1, s2, b, j, jo)]])[:] = M[r0:r0 + da, c0:c0 + db]
+        else:
+            for (jo, a, s1, r0, da) in rows:
+                for (b, s2, c0, db) in cols:
+                    sectors.block_view(out, blocks[bidx[(a, s1, s2, b, jo, j)]])[:] = M[r0:r0 + da, c0:c0 + db]
     return out
 
 
-def _truncated(psi, blocks, n, ls, rs, N, sec, A, rest, side):
-    mats = sweep._bond_matrices(psi, blocks, ls, rs, synth.SPATIAL_ORBITAL, N)
+def _truncated(psi, blocks, n, ls, rs, N, sec, A, rest, side, kind=synth.SPATIAL_ORBITAL, twoS=0):
+    mats = sweep._bond_matrices(psi, blocks, ls, rs, kind, N, twoS, side)
     kept = {}
     for qo, (Nb, j, d) in enumerate(sec):
-        key = (Nb, j) if side == "L" else (N - Nb, j)
-        lrows, rrows, M = mats[key]
+        rows, cols, M = mats[(Nb, j)]
         Q, C = A[qo][1], rest[qo][1]
-        kept[key] = (lrows, rrows, Q @ C if side == "L" else C @ Q.T)
-    for key, (lrows, rrows, M) in mats.items():
+        kept[(Nb, j)] = (rows, cols, Q @ C if side == "L" else C @ Q.T)
+    for key, (rows, cols, M) in mats.items():
         if key not in kept:
-            kept[key] = (lrows, rrows, np.zeros_like(M))
-    return _from_bond_matrices(kept, blocks, n)
+            kept[key] = (rows, cols, np.zeros_like(M))
+    return _from_bond_matrices(kept, blocks, n, side)
 
 
 def _rq(apply, v):
     return float(v @ apply(v) / (v @ v))
 
 
-def _prediction_chain(L, N, D, seed, plant=None):
+def _prediction_chain(L, N, D, seed, plant=None, twoS=0):
     """Walks windows 0 .. L-2 moving right and back moving left with seeded
     (unconverged) vectors, growing blocks with the truncated isometries;
     returns per transition (|guess|^2, 1 - w, RQ of the guess in the next
     window, RQ of the truncated state in its own window)."""
     from oracle import abinitio
     from oracle import env as envmod
-    cfg = synth.Config("pred", synth.SPATIAL_ORBITAL, L, N, 0, D, seed)
+    kind = synth.SPATIAL_ORBITAL
+    cfg = synth.Config("pred", kind, L, N, twoS, D, seed)
     h, eri = synth.integrals(L, seed)
     strings = abinitio.hamiltonian_strings(h, eri)
     chain = synth.bond_sector_chain(cfg, L - 2)
     R, RA = [abinitio.RightBlock(strings, L)], [None] * (L - 1)
     for k in range(1, L - 1):
-        RA[k] = envmod.mps_tensor(seed, envmod.SIDE_MPS_R, k, chain[k - 1], chain[k], synth.SPATIAL_ORBITAL)
+        RA[k] = envmod.mps_tensor(seed, envmod.SIDE_MPS_R, k, chain[k - 1], chain[k], kind)
         R.append(R[-1].grown(chain[k], RA[k]))
     Lbs, LA = [abinitio.LeftBlock(strings, L)] + [None] * (L - 2), [None] * (L - 1)
     out = []
     for i in range(0, L - 2):
-        apply, _, blocks, n, ls, rs = sweep.window(strings, Lbs[i], R[L - 2 - i], N)
+        apply, _, blocks, n, ls, rs = sweep.window(strings, Lbs[i], R[L - 2 - i], N, twoS)
         psi = synth.gaussian_psi(n, 50 + i)
-        sec, A, w, rest = sweep.isometry(psi, blocks, ls, rs, synth.SPATIAL_ORBITAL, N, D, "L", with_rest=True)
+        sec, A, w, rest = sweep.isometry(psi, blocks, ls, rs, kind, N, D, "L", with_rest=True, twoS=twoS)
         Lbs[i + 1] = Lbs[i].grown(sec, A)
         LA[i + 1] = A
-        apply2, _, nb, nn, _, _ = sweep.window(strings, Lbs[i + 1], R[L - 3 - i], N)
+        apply2, _, nb, nn, _, _ = sweep.window(strings, Lbs[i + 1], R[L - 3 - i], N, twoS)
         RAi = RA[L - 2 - i] if plant is None else plant(RA[L - 2 - i])
-        g = sweep.predict_moving_right(rest, rs, RAi, nb, nn)
-        t = _truncated(psi, blocks, n, ls, rs, N, sec, A, rest, "L")
+        g = sweep.predict_moving_right(rest, rs, RAi, nb, nn, sec, twoS, kind)
+        t = _truncated(psi, blocks, n, ls, rs, N, sec, A, rest, "L", kind, twoS)
         out.append((g @ g, 1.0 - w, _rq(apply2, g), _rq(apply, t)))
     for i in range(L - 2, 0, -1):
-        apply, _, blocks, n, ls, rs = sweep.window(strings, Lbs[i], R[L - 2 - i], N)
+        apply, _, blocks, n, ls, rs = sweep.window(strings, Lbs[i], R[L - 2 - i], N, twoS)
         psi = synth.gaussian_psi(n, 80 + i)
-        sec, A, w, rest = sweep.isometry(psi, blocks, ls, rs, synth.SPATIAL_ORBITAL, N, D, "R", with_rest=True)
+        sec, A, w, rest = sweep.isometry(psi, blocks, ls, rs, kind, N, D, "R", with_rest=True, twoS=twoS)
         R[L - 1 - i] = R[L - 2 - i].grown(sec, A)
         RA[L - 1 - i] = A
-        apply2, _, nb, nn, _, _ = sweep.window(strings, Lbs[i - 1], R[L - 1 - i], N)
-        g = sweep.predict_moving_left(rest, ls, LA[i], nb, nn)
-        t = _truncated(psi, blocks, n, ls, rs, N, sec, A, rest, "R")
+        apply2, _, nb, nn, _, _ = sweep.window(strings, Lbs[i - 1], R[L - 1 - i], N, twoS)
+        g = sweep.predict_moving_left(rest, ls, LA[i], nb, nn, sec, twoS, kind)
+        t = _truncated(psi, blocks, n, ls, rs, N, sec, A, rest, "R", kind, twoS)
         out.append((g @ g, 1.0 - w, _rq(apply2, g), _rq(apply, t)))
     return out
 
@@ -248,3 +258,42 @@ def test_heisenberg_truncated_sweep_is_variational():
     # the last sweep is within its truncation error of the ground state
     assert np.all(E[-(cfg.L - 1):] - E0 < 1e-4)
     assert abs(E[cfg.L - 2] - E[cfg.L - 1]) < 1e-9
+
+
+# ---------------------------------------------------------------- targets with S > 0
+@pytest.mark.parametrize("N,twoS", [(5, 1), (6, 2)])
+def test_prediction_for_spin_targets_is_the_truncated_state(N, twoS):
+    # at S > 0 the guess recouples [k x (s2 x b)_j2R]^S by a 6j; the
+    # identities of the truncated state still hold to rounding
+    res = _prediction_chain(6, N, 5, 1003, twoS=twoS)
+    assert max(1.0 - w for (_, w, _, _) in res) > 1e-3
+    for (g2, w, e_next, e_trunc) in res:
+        assert abs(g2 - w) <= 1e-12
+        assert abs(e_next - e_trunc) <= 1e-11 * abs(e_trunc)
+
+
+def test_prediction_without_the_recoupling_fails(monkeypatch):
+    # a planted mistake: the S = 0 factor (1) used for an S = 1 target
+    monkeypatch.setattr(sweep, "_recouple", lambda *a: 1.0)
+    res = _prediction_chain(6, 6, 5, 1003, twoS=2)
+    assert max(abs(e - t) / abs(t) for (_, _, e, t) in res) > 1e-3
+
+
+@pytest.mark.parametrize("N,twoS", [(5, 1), (6, 2)])
+def test_exact_sweep_for_spin_targets_equals_full_ci(N, twoS):
+    cfg = synth.Config("sws", synth.SPATIAL_ORBITAL, 6, N, twoS, 400, 1002)
+    st = []
+    E, w = sweep.sweep(cfg, 400, 2, predict=True, stats=st)
+    h, eri = synth.integrals(6, 1002)
+    assert np.abs(E - fci.spin_levels(h, eri, N, twoS)[0]).max() < 1e-9
+    assert np.all(np.abs(w) < 1e-20)
+    assert all(it == 1 for (it, _) in st[1:])
+
+
+def test_heisenberg_triplet_sweep_equals_exact_diagonalisation():
+    from oracle import ed
+    cfg = synth.Config("h10s1", synth.SPIN_HALF, 10, 10, 2, 32, 1001)
+    E, w = sweep.sweep(cfg, 32, 4, tol=1e-10, predict=True)
+    E0 = ed.heisenberg_levels(10, 2)[0]
+    assert E.min() >= E0 - 1e-10
+    assert np.abs(E[cfg.L - 1:] - E0).max() < 1e-9
