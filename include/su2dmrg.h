@@ -359,7 +359,7 @@ int su2_energy_check(su2_ctx* ctx, su2_dav* dav, int32_t prec, double* rq, doubl
 int su2_davidson_vector(su2_ctx* ctx, su2_dav* dav, double* x_dev);
 int su2_davidson_destroy(su2_dav* dav);
 
-/* Two-site sweep (Sec. II; total spin 0) of the ab initio model
+/* Two-site sweep (Sec. II; target spin S = opts->twoS / 2) of the ab initio model
  * (SU2_MODEL_AB_INITIO with its integrals) or of the spin-1/2 Heisenberg
  * chain (SU2_MODEL_HEISENBERG, coupling J; h and eri unused): at every
  * window (sites i, i+1) the environment is assembled from the blocks of
@@ -388,6 +388,7 @@ typedef struct {
   int32_t n_slices;      /* BF16 slices of the split path (0: 5)            */
   uint64_t guess_seed;   /* seed of the Davidson start vectors              */
   int32_t predict;       /* 1: start each window from the predicted vector  */
+  int32_t twoS;          /* twice the target spin S (0: singlet)           */
 } su2_sweep_opts;
 int su2_sweep_create(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond_chain* right_chain, int32_t N,
                      const su2_sweep_opts* opts, su2_sweep** out);

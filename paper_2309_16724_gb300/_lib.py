@@ -74,7 +74,7 @@ class EnvInfo(C.Structure):
 
 class SweepOpts(C.Structure):
     _fields_ = [("D", C.c_int32), ("prec", C.c_int32), ("tol", C.c_double), ("max_iter", C.c_int32),
-                ("n_slices", C.c_int32), ("guess_seed", C.c_uint64), ("predict", C.c_int32)]
+                ("n_slices", C.c_int32), ("guess_seed", C.c_uint64), ("predict", C.c_int32), ("twoS", C.c_int32)]
 
 
 class DavOpts(C.Structure):
@@ -450,15 +450,15 @@ class Davidson:
 
 
 class Sweep:
-    """su2_sweep_create / su2_sweep_run: the two-site sweep (S = 0) on the
-    GPU, of the ab initio model of the integrals (h, eri) or, with h = eri =
-    None, of the spin-1/2 Heisenberg chain of len(right_chain) + 1 sites with
-    coupling J; it starts at window 0 moving right with the right blocks of
+    """su2_sweep_create / su2_sweep_run: the two-site sweep (target spin
+    twoS / 2) on the GPU, of the ab initio model of the integrals (h, eri)
+    or, with h = eri = None, of the spin-1/2 Heisenberg chain of
+    len(right_chain) + 1 sites with coupling J; it starts at window 0 moving right with the right blocks of
     `right_chain` (bonds of 0 .. L-2 sites) grown by the seeded MPS tensors,
     or by the caller's (`mps_right`, the layout of su2_hamiltonian)."""
 
     def __init__(self, ctx: Context, h, eri, right_chain, N, D, prec=SU2_SPLIT_BF16, tol=1e-8, max_iter=400,
-                 n_slices=5, seed=0, guess_seed=1, mps_right=None, predict=False, J=1.0):
+                 n_slices=5, seed=0, guess_seed=1, mps_right=None, predict=False, J=1.0, twoS=0):
         self.ctx = ctx
         mr = _mps(mps_right)
         if h is None and eri is None:
@@ -476,7 +476,7 @@ class Sweep:
             H = Hamiltonian(SU2_MODEL_AB_INITIO, 0, L - 2, 1.0, seed, h.ctypes.data, eri.ctypes.data, None,
                             None if mr is None else mr.ctypes.data)
         rc_, keep = _chain(right_chain)
-        o = SweepOpts(D, prec, tol, max_iter, n_slices, guess_seed, 1 if predict else 0)
+        o = SweepOpts(D, prec, tol, max_iter, n_slices, guess_seed, 1 if predict else 0, twoS)
         hd = C.c_void_p()
         ctx.check(lib().su2_sweep_create(ctx.h, C.byref(H), C.byref(rc_), N, C.byref(o), C.byref(hd)))
         self.h = hd

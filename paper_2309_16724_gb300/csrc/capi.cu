@@ -1219,6 +1219,7 @@ int su2_sweep_create(su2_ctx* ctx, const su2_hamiltonian* H, const su2_bond_chai
   if (!heis && (H->model != SU2_MODEL_AB_INITIO || !H->h || !H->eri))
     return fail(ctx, SU2_EINVAL, "the sweep needs the ab initio model (with its integrals) or the Heisenberg chain");
   if (opts->D < 1 || N < 0) return fail(ctx, SU2_EINVAL, "D must be >= 1");
+  if (opts->twoS < 0) return fail(ctx, SU2_EINVAL, "the target spin must be >= 0");
   if (opts->prec != SU2_FP64 && opts->prec != SU2_SPLIT_BF16) return fail(ctx, SU2_EINVAL, "unknown precision");
   std::vector<std::vector<Sector>> rch;
   if (right_chain->n_bonds < 1 || !right_chain->bond_offset || !right_chain->sectors)
@@ -1302,7 +1303,7 @@ int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies
     su2_sectors S;
     S.site_kind = kind;
     S.N = sw->N;
-    S.twoS = 0;
+    S.twoS = sw->o.twoS;
     su2_env* env = new (std::nothrow) su2_env();
     if (!env) return fail(ctx, SU2_ENOMEM, "host allocation");
     env->ctx = ctx;
@@ -1319,14 +1320,14 @@ int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies
     } else {
       err = sweep_env(sw->w, i, env->table, env->L, env->R, S.left, S.right);
     }
-    if (err.empty()) build_blocks(S.left, S.right, kind, sw->N, 0, S.blocks, S.psi_len);
+    if (err.empty()) build_blocks(S.left, S.right, kind, sw->N, S.twoS, S.blocks, S.psi_len);
     if (err.empty() && S.psi_len == 0) err = "no two-site state with the target particle number";
     if (err.empty()) {
       env->psi_len = S.psi_len;
       env->blocks = S.blocks;
       env->lsec = S.left;
       env->rsec = S.right;
-      err = build_tasks(env->table, S.left, S.right, S.blocks, 0, env->L, env->R, env->tasks);
+      err = build_tasks(env->table, S.left, S.right, S.blocks, S.twoS, env->L, env->R, env->tasks);
     }
     if (!err.empty()) {
       cudaFree(env->L.dev_ready);
@@ -1391,7 +1392,7 @@ int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies
       std::vector<Sector> cur;
       std::vector<std::vector<double>> Q, rest;
       err = sweep_split(S.blocks, h.data(), S.left, S.right, sw->N, sw->o.D, sw->dir > 0, cur, Q, &w,
-                        sw->o.predict ? &rest : nullptr, kind);
+                        sw->o.predict ? &rest : nullptr, kind, S.twoS);
       if (err.empty() && sw->heis) {
         // the grown block on the host, then the next window's guess
         if (sw->dir > 0) {
@@ -1399,18 +1400,18 @@ int su2_sweep_run(su2_ctx* ctx, su2_sweep* sw, int32_t n_steps, double* energies
           sw->hLq[size_t(i + 1)] = Q;
           if (err.empty() && sw->o.predict)
             err = predict_guess(true, S.left, S.right, sw->hL[size_t(i + 1)].sec, sw->hR[size_t(L - 3 - i)].sec,
-                                sw->hRq[size_t(L - 2 - i)], sw->N, kind, cur, rest, sw->guess);
+                                sw->hRq[size_t(L - 2 - i)], sw->N, kind, cur, rest, sw->guess, S.twoS);
         } else {
           err = heis_grow(sw->hR[size_t(L - 2 - i)], cur, Q, false, sw->H.J, sw->hR[size_t(L - 1 - i)]);
           sw->hRq[size_t(L - 1 - i)] = Q;
           if (err.empty() && sw->o.predict)
             err = predict_guess(false, S.left, S.right, sw->hL[size_t(i - 1)].sec, sw->hR[size_t(L - 1 - i)].sec,
-                                sw->hLq[size_t(i)], sw->N, kind, cur, rest, sw->guess);
+                                sw->hLq[size_t(i)], sw->N, kind, cur, rest, sw->guess, S.twoS);
         }
       } else if (err.empty()) {
         err = sweep_grow(sw->w, i, sw->dir > 0, cur, Q);
         if (err.empty() && sw->o.predict)
-          err = sweep_predict(sw->w, i, sw->dir > 0, S.left, S.right, sw->N, cur, rest, sw->guess);
+          err = sweep_predict(sw->w, i, sw->dir > 0, S.left, S.right, sw->N, cur, rest, sw->guess, S.twoS);
       }
       if (!err.empty()) return fail(ctx, SU2_EINVAL, err);
     } else if (sw->o.predict) {

@@ -1436,50 +1436,56 @@ std::string sweep_env(SweepBlocks* w, int i, OpTable& table, SideOps& Lops, Side
 std::string sweep_split(const std::vector<Block>& blocks, const double* psi, const std::vector<Sector>& lsec,
                         const std::vector<Sector>& rsec, int N, int D, bool left, std::vector<Sector>& new_sec,
                         std::vector<std::vector<double>>& Q, double* discarded,
-                        std::vector<std::vector<double>>* rest, int site_kind) {
+                        std::vector<std::vector<double>>* rest, int site_kind, int twoS) {
   std::vector<int> sN, sS;
   site_states(site_kind, sN, sS);
   const int ns = int(sN.size());
   struct Stk {
-    int q, s, r0, d;
+    int q, s, r0, d, j;  // sector, site state, first row, rows; j: coupled spin of the half
   };
-  auto stacks = [&](const std::vector<Sector>& sec, int Nq, int j, int& tot) {
-    std::vector<Stk> v;
-    tot = 0;
+  // the stacks (sector, site state) of one half with coupled spin j,
+  // numbered on from tot
+  auto stacks = [&](const std::vector<Sector>& sec, int Nq, int j, int& tot, std::vector<Stk>& v) {
     for (int qp = 0; qp < int(sec.size()); ++qp)
       for (int si = 0; si < ns; ++si)
         if (sec[qp].N + sN[si] == Nq && triangle(sec[qp].twoS, sS[si], j)) {
-          v.push_back(Stk{qp, si, tot, sec[qp].dim});
+          v.push_back(Stk{qp, si, tot, sec[qp].dim, j});
           tot += sec[qp].dim;
         }
-    return v;
   };
-  // (a, s1, s2, b, j) -> block (S = 0: jL1 = j2R = j; one (a, s1) pair may
-  // couple to two values of j)
-  std::map<std::tuple<int, int, int, int, int>, int> bidx;
+  // the bond matrix of each sector (N_k, j) of the block that grows: moving
+  // right, rows (a, s1) of the left half with j_L1 = j and columns (s2, b) of
+  // every j_2R coupling with j to the target, j_2R ascending; moving left,
+  // columns (s2, b) with j_2R = j and rows over every j_L1.  The coupled
+  // states are orthonormal, so the singular values carry the multiplet weights.
+  std::map<std::array<int, 6>, int> bidx;
   std::map<std::pair<int, int>, int> keys;
   for (int i = 0; i < int(blocks.size()); ++i) {
     const Block& B = blocks[i];
-    if (B.jL1 != B.j2R) return "the sweep needs a total-spin-0 target";
-    bidx[{B.a, B.s1, B.s2, B.b, B.jL1}] = i;
-    keys[{lsec[B.a].N + sN[B.s1], B.jL1}] = 1;
+    bidx[{B.a, B.s1, B.s2, B.b, B.jL1, B.j2R}] = i;
+    if (left) keys[{lsec[B.a].N + sN[B.s1], B.jL1}] = 1;
+    else keys[{rsec[B.b].N + sN[B.s2], B.j2R}] = 1;
   }
   struct Sec {
-    int Nq, j;
+    int Nk, j;
     std::vector<double> U, sv, M;  // M: the bond matrix (nr x nc, column-major)
     int rows, nr, nc;
   };
   std::vector<Sec> all;
   double total = 0.0;
   for (const auto& kv : keys) {
-    const int Nq = kv.first.first, j = kv.first.second;
-    int nr = 0, nc = 0;
-    const auto ls = stacks(lsec, Nq, j, nr);
-    const auto rs = stacks(rsec, N - Nq, j, nc);
+    const int Nk = kv.first.first, j = kv.first.second;
+    int nown = 0, nother = 0;
+    std::vector<Stk> own, other;
+    stacks(left ? lsec : rsec, Nk, j, nown, own);
+    for (int jo = std::abs(j - twoS); jo <= j + twoS; jo += 2) stacks(left ? rsec : lsec, N - Nk, jo, nother, other);
+    const std::vector<Stk>& ls = left ? own : other;
+    const std::vector<Stk>& rs = left ? other : own;
+    const int nr = left ? nown : nother, nc = left ? nother : nown;
     std::vector<double> M(size_t(nr) * nc, 0.0);
     for (const Stk& x : ls)
       for (const Stk& y : rs) {
-        auto it = bidx.find({x.q, x.s, y.s, y.q, j});
+        auto it = bidx.find({x.q, x.s, y.s, y.q, x.j, y.j});
         if (it == bidx.end()) continue;
         const Block& B = blocks[it->second];
         for (int c = 0; c < B.cols; ++c)
@@ -1487,7 +1493,7 @@ std::string sweep_split(const std::vector<Block>& blocks, const double* psi, con
             M[size_t(x.r0 + r) + size_t(y.r0 + c) * nr] = psi[B.offset + r + int64_t(c) * B.rows];
       }
     Sec sc;
-    sc.Nq = Nq;
+    sc.Nk = Nk;
     sc.j = j;
     sc.nr = nr;
     sc.nc = nc;
@@ -1514,7 +1520,7 @@ std::string sweep_split(const std::vector<Block>& blocks, const double* psi, con
   // kept: their singular vectors are arbitrary
   std::vector<Cand> cand;
   for (int q = 0; q < int(all.size()); ++q) {
-    const int Nb = left ? all[q].Nq : N - all[q].Nq;
+    const int Nb = all[q].Nk;
     for (int x = 0; x < int(all[q].sv.size()); ++x) {
       const double w2 = all[q].sv[x] * all[q].sv[x];
       if (w2 > 1e-24 * total) cand.push_back(Cand{w2, Nb, all[q].j, q, x});
@@ -1539,7 +1545,7 @@ std::string sweep_split(const std::vector<Block>& blocks, const double* psi, con
   std::vector<std::pair<std::pair<int, int>, int>> order;  // ((N, 2S) of the new bond, sector)
   for (const auto& kv : nkeep) {
     const Sec& sc = all[size_t(kv.first)];
-    order.push_back({{left ? sc.Nq : N - sc.Nq, sc.j}, kv.first});
+    order.push_back({{sc.Nk, sc.j}, kv.first});
   }
   std::sort(order.begin(), order.end());
   new_sec.clear();
@@ -1607,18 +1613,19 @@ std::string sweep_grow(SweepBlocks* w, int i, bool left, const std::vector<Secto
   return "";
 }
 
-// Wavefunction prediction (S = 0).  Moving right from window i the kept
+// Wavefunction prediction.  Moving right from window i the kept
 // wavefunction is Q (Q^T M) per bond sector: Q became the grown left block,
-// and C = Q^T M, with columns stacked (right sector b, site s2), is expanded
-// over the right block's MPS tensor, b = [s3 x r'] with rows stacked (r', s3),
-// into the blocks (k, s2, s3, r', S_b, S_b) of window i+1.  Moving left,
-// C = M Q (rows (left sector a, site s1)) is expanded over the left block's
-// tensor, a = [a'' x s0], into the blocks (a'', s0, s1, k, S_a, S_a) of
-// window i-1.  The recoupling (j_k (s2 S_b)_j)_0 -> ((j_k s2)_(S_b) S_b)_0 of
-// total spin 0 has the factor (-1)^(j_k+s2+S_b) sqrt((2S_b+1)(2j_k+1)) times
-// the 6j {j_k s2 S_b; S_b 0 j_k}, which is 1; no operator changes places, so
-// no fermionic sign enters.  The guess is laid out in the next window's
-// block order (build_blocks of its sectors).
+// and C = Q^T M, with columns stacked (j_2R, right sector b, site s2), is
+// expanded over the right block's MPS tensor, b = [s3 x r'] with rows
+// stacked (r', s3), into the blocks (k, s2, s3, r', j', S_b) of window i+1.
+// Moving left, C = M Q (rows (j_L1, left sector a, site s1)) is expanded over
+// the left block's tensor, a = [a'' x s0], into the blocks
+// (a'', s0, s1, k, S_a, j'') of window i-1.  The spins are recoupled,
+// (j_k (s2 S_b)_j2R)_S -> ((j_k s2)_j' S_b)_S and ((S_a s1)_jL1 j_k)_S ->
+// (S_a (s1 j_k)_j'')_S, by the 6j factor of `recouple`, which is exactly 1
+// at S = 0 (one term, j' = S_b); no operator changes places, so no fermionic
+// sign enters.  The guess is laid out in the next window's block order
+// (build_blocks of its sectors).
 std::string sweep_right_state(SweepBlocks* w, std::vector<std::vector<Sector>>& chain,
                               std::vector<std::vector<std::vector<double>>>& tensors) {
   chain.clear();
@@ -1633,85 +1640,108 @@ std::string sweep_right_state(SweepBlocks* w, std::vector<std::vector<Sector>>& 
 
 std::string sweep_predict(SweepBlocks* w, int i, bool right, const std::vector<Sector>& lsec,
                           const std::vector<Sector>& rsec, int N, const std::vector<Sector>& cur,
-                          const std::vector<std::vector<double>>& rest, std::vector<double>& guess) {
+                          const std::vector<std::vector<double>>& rest, std::vector<double>& guess, int twoS) {
   const int L = w->L;
   const int nx = right ? i + 1 : i - 1;
   if (nx < 0 || nx > L - 2) return "no window to predict";
   return predict_guess(right, lsec, rsec, w->Lb[size_t(nx)].lay.sec, w->Rb[size_t(L - 2 - nx)].lay.sec,
-                       right ? w->Rq[size_t(L - 2 - i)] : w->Lq[size_t(i)], N, SU2_SITE_ORBITAL, cur, rest, guess);
+                       right ? w->Rq[size_t(L - 2 - i)] : w->Lq[size_t(i)], N, SU2_SITE_ORBITAL, cur, rest, guess,
+                       twoS);
 }
+
+namespace {
+// <((j1 j2) j12, j3) J | (j1, (j2 j3) j23) J> (twos): the recoupling of three
+// spins, (-1)^(j1+j2+j3+J) sqrt((2 j12+1)(2 j23+1)) {j1 j2 j12; j3 J j23}
+double recouple(int j1, int j2, int j3, int J, int j12, int j23) {
+  if (J == 0) return (j12 == j3 && j23 == j1) ? 1.0 : 0.0;
+  const double sg = (((j1 + j2 + j3 + J) / 2) % 2) ? -1.0 : 1.0;
+  return sg * std::sqrt(double(j12 + 1) * double(j23 + 1)) * sixj(j1, j2, j12, j3, J, j23);
+}
+}  // namespace
 
 std::string predict_guess(bool right, const std::vector<Sector>& lsec, const std::vector<Sector>& rsec,
                           const std::vector<Sector>& nl, const std::vector<Sector>& nr,
                           const std::vector<std::vector<double>>& T, int N, int site_kind,
                           const std::vector<Sector>& cur, const std::vector<std::vector<double>>& rest,
-                          std::vector<double>& guess) {
+                          std::vector<double>& guess, int twoS) {
   const std::vector<Sector>& tsec = right ? rsec : lsec;            // sectors the tensor produces
   const std::vector<Sector>& tprev = right ? nr : nl;                // its previous bond
   if (T.size() != tsec.size()) return "the MPS tensor of the adjacent block is not known";
   std::vector<Block> nb;
   int64_t nlen = 0;
-  std::string err = build_blocks(nl, nr, site_kind, N, 0, nb, nlen);
+  std::string err = build_blocks(nl, nr, site_kind, N, twoS, nb, nlen);
   if (!err.empty()) return err;
-  std::map<std::tuple<int, int, int, int, int>, int> bidx;
-  for (int x = 0; x < int(nb.size()); ++x) bidx[{nb[x].a, nb[x].s1, nb[x].s2, nb[x].b, nb[x].jL1}] = x;
+  std::map<std::array<int, 6>, int> bidx;
+  for (int x = 0; x < int(nb.size()); ++x) bidx[{nb[x].a, nb[x].s1, nb[x].s2, nb[x].b, nb[x].jL1, nb[x].j2R}] = x;
   std::vector<int> sN, sS;
   site_states(site_kind, sN, sS);
   struct Stk {
-    int q, s, r0, d;
+    int q, s, r0, d, j;
   };
-  auto stacks = [&](const std::vector<Sector>& sec, int Nq, int j, int& tot) {
-    std::vector<Stk> v;
-    tot = 0;
+  auto stacks = [&](const std::vector<Sector>& sec, int Nq, int j, int& tot, std::vector<Stk>& v) {
     for (int qp = 0; qp < int(sec.size()); ++qp)
       for (int si = 0; si < int(sN.size()); ++si)
         if (sec[qp].N + sN[si] == Nq && triangle(sec[qp].twoS, sS[si], j)) {
-          v.push_back(Stk{qp, si, tot, sec[qp].dim});
+          v.push_back(Stk{qp, si, tot, sec[qp].dim, j});
           tot += sec[qp].dim;
         }
-    return v;
   };
   guess.assign(size_t(nlen), 0.0);
   for (int qo = 0; qo < int(cur.size()); ++qo) {
-    const int j = cur[qo].twoS, d = cur[qo].dim;
-    const int Nq = right ? cur[qo].N : N - cur[qo].N;  // particles left of the bond between the two sites
+    const int jk = cur[qo].twoS, d = cur[qo].dim;
+    const int No = N - cur[qo].N;  // particles of the other half of window i
+    // right: C's columns (b, s2) of window i's right half, j_2R ascending over
+    // the spins that couple with j_k to S; left: C's rows (a, s1) likewise
     int tot = 0;
-    // right: C's columns (b, s2) over the right sectors of window i; left:
-    // C's rows (a, s1) over its left sectors
-    const auto st = right ? stacks(rsec, N - Nq, j, tot) : stacks(lsec, Nq, j, tot);
+    std::vector<Stk> st;
+    for (int jo = std::abs(jk - twoS); jo <= jk + twoS; jo += 2) stacks(right ? rsec : lsec, No, jo, tot, st);
     const std::vector<double>& C = rest[size_t(qo)];
     if (C.size() != size_t(tot) * d) return "prediction: the kept wavefunction does not match its stacks";
     for (const Stk& x : st) {
       const int S = tsec[size_t(x.q)].twoS, dq = tsec[size_t(x.q)].dim;
+      const int ts = sS[size_t(x.s)];  // spin of the site between the kept half and the adjacent block
       int trows = 0;
-      const auto tst = stacks(tprev, tsec[size_t(x.q)].N, S, trows);
+      std::vector<Stk> tst;
+      stacks(tprev, tsec[size_t(x.q)].N, S, trows, tst);
       const std::vector<double>& G = T[size_t(x.q)];
       if (G.size() != size_t(trows) * dq) return "prediction: an MPS tensor does not match its stacks";
-      for (const Stk& y : tst) {
-        // right: block (qo, s2 = x.s, s3 = y.s, r' = y.q); left: (a'' = y.q, s0 = y.s, s1 = x.s, qo)
-        const auto it = right ? bidx.find({qo, x.s, y.s, y.q, S}) : bidx.find({y.q, y.s, x.s, qo, S});
-        if (it == bidx.end()) return "prediction: a block of the next window is missing";
-        const Block& B = nb[size_t(it->second)];
-        double* out = guess.data() + B.offset;
-        if (right) {
-          // out (d x dr') += C[:, x.r0 : x.r0 + db] G[y.r0 : y.r0 + dr', :]^T
-          for (int c = 0; c < B.cols; ++c)
-            for (int m = 0; m < dq; ++m) {
-              const double g = G[size_t(y.r0 + c) + size_t(m) * trows];
-              if (g == 0.0) continue;
-              const double* cc = &C[size_t(x.r0 + m) * d];
-              for (int r = 0; r < B.rows; ++r) out[r + int64_t(c) * B.rows] += cc[r] * g;
-            }
-        } else {
-          // out (da'' x d) += G[y.r0 : y.r0 + da'', :] C[x.r0 : x.r0 + da, :]
-          for (int c = 0; c < B.cols; ++c)
-            for (int m = 0; m < dq; ++m) {
-              const double cv = C[size_t(x.r0 + m) + size_t(c) * tot];
-              if (cv == 0.0) continue;
-              for (int r = 0; r < B.rows; ++r) out[r + int64_t(c) * B.rows] += G[size_t(y.r0 + r) + size_t(m) * trows] * cv;
-            }
-        }
+      // the new coupled spin of the site with the kept half, and its weight:
+      // right: (j_k (s2 S_b)_j2R)_S -> ((j_k s2)_j' S_b)_S; left: ((S_a s1)_jL1
+      // j_k)_S -> (S_a (s1 j_k)_j'')_S
+      std::vector<std::pair<int, double>> terms;
+      for (int jn = std::abs(jk - ts); jn <= jk + ts; jn += 2) {
+        if (!triangle(jn, S, twoS)) continue;
+        const double wgt = right ? recouple(jk, ts, S, twoS, jn, x.j) : recouple(S, ts, jk, twoS, x.j, jn);
+        if (wgt != 0.0) terms.push_back({jn, wgt});
       }
+      for (const Stk& y : tst)
+        for (const auto& tw : terms) {
+          // right: block (qo, s2 = x.s, s3 = y.s, r' = y.q, j', S_b); left: (a'' = y.q, s0 = y.s, s1 = x.s, qo, S_a, j'')
+          const auto it = right ? bidx.find({qo, x.s, y.s, y.q, tw.first, S})
+                                : bidx.find({y.q, y.s, x.s, qo, S, tw.first});
+          if (it == bidx.end()) return "prediction: a block of the next window is missing";
+          const Block& B = nb[size_t(it->second)];
+          double* out = guess.data() + B.offset;
+          const double wgt = tw.second;
+          if (right) {
+            // out (d x dr') += wgt C[:, x.r0 : x.r0 + db] G[y.r0 : y.r0 + dr', :]^T
+            for (int c = 0; c < B.cols; ++c)
+              for (int m = 0; m < dq; ++m) {
+                const double g = wgt * G[size_t(y.r0 + c) + size_t(m) * trows];
+                if (g == 0.0) continue;
+                const double* cc = &C[size_t(x.r0 + m) * d];
+                for (int r = 0; r < B.rows; ++r) out[r + int64_t(c) * B.rows] += cc[r] * g;
+              }
+          } else {
+            // out (da'' x d) += wgt G[y.r0 : y.r0 + da'', :] C[x.r0 : x.r0 + da, :]
+            for (int c = 0; c < B.cols; ++c)
+              for (int m = 0; m < dq; ++m) {
+                const double cv = wgt * C[size_t(x.r0 + m) + size_t(c) * tot];
+                if (cv == 0.0) continue;
+                for (int r = 0; r < B.rows; ++r) out[r + int64_t(c) * B.rows] += G[size_t(y.r0 + r) + size_t(m) * trows] * cv;
+              }
+          }
+        }
     }
   }
   return "";

@@ -146,7 +146,8 @@ std::string sweep_env(SweepBlocks* w, int i, OpTable& table, SideOps& L, SideOps
 std::string sweep_split(const std::vector<Block>& blocks, const double* psi, const std::vector<Sector>& lsec,
                         const std::vector<Sector>& rsec, int N, int D, bool left, std::vector<Sector>& new_sec,
                         std::vector<std::vector<double>>& Q, double* discarded,
-                        std::vector<std::vector<double>>* rest = nullptr, int site_kind = SU2_SITE_ORBITAL);
+                        std::vector<std::vector<double>>* rest = nullptr, int site_kind = SU2_SITE_ORBITAL,
+                        int twoS = 0);
 std::string sweep_grow(SweepBlocks* w, int i, bool left, const std::vector<Sector>& cur,
                        const std::vector<std::vector<double>>& Q);
 // the bonds of the right blocks (0 .. L-2 orbitals) and the MPS tensors
@@ -157,7 +158,7 @@ std::string sweep_right_state(SweepBlocks* w, std::vector<std::vector<Sector>>& 
 // from window i's kept wavefunction (`rest` of sweep_split, after sweep_grow)
 std::string sweep_predict(SweepBlocks* w, int i, bool right, const std::vector<Sector>& lsec,
                           const std::vector<Sector>& rsec, int N, const std::vector<Sector>& cur,
-                          const std::vector<std::vector<double>>& rest, std::vector<double>& guess);
+                          const std::vector<std::vector<double>>& rest, std::vector<double>& guess, int twoS = 0);
 // the same from explicit data: the next window's bond sectors (nl, nr) and
 // the MPS tensor T of the block adjacent to window i on the side the sweep
 // moves to (its right block moving right, its left block moving left)
@@ -165,7 +166,7 @@ std::string predict_guess(bool right, const std::vector<Sector>& lsec, const std
                           const std::vector<Sector>& nl, const std::vector<Sector>& nr,
                           const std::vector<std::vector<double>>& T, int N, int site_kind,
                           const std::vector<Sector>& cur, const std::vector<std::vector<double>>& rest,
-                          std::vector<double>& guess);
+                          std::vector<double>& guess, int twoS = 0);
 
 // counter-based generator (SplitMix64, Steele/Lea/Flood 2014)
 uint64_t splitmix(uint64_t x);

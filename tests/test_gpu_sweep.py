@@ -190,3 +190,52 @@ def test_sweep_checkpoint_resumes(ctx, model):
     assert ctx.status() == 0
     assert np.abs(ea - eb).max() < 1e-8, (ea, eb)
     assert np.allclose(wa, wb, rtol=1e-5, atol=1e-12)
+
+
+@pytest.mark.parametrize("N,twoS", [(5, 1), (6, 2)])
+def test_spin_target_sweep_equals_full_ci(ctx, N, twoS):
+    """Targets with S > 0 (bond matrices over every j_2R, prediction
+    recoupled by a 6j), bonds that keep every multiplet: every window equals
+    the lowest spin-S level of full CI, after the first window in one or
+    two iterations."""
+    import paper_2309_16724_gb300 as P
+    cfg = synth.Config("sws", synth.SPATIAL_ORBITAL, 6, N, twoS, 400, 1002)
+    h, eri = synth.integrals(6, 1002)
+    chain = synth.bond_sector_chain(cfg, cfg.L - 2)
+    sw = P.Sweep(ctx, h, eri, chain, N, 400, prec=0, tol=1e-10, seed=cfg.seed, predict=True, twoS=twoS)
+    e, w, it, e0 = sw.run(2 * (cfg.L - 1), stats=True)
+    sw.close()
+    assert ctx.status() == 0
+    assert np.abs(e - fci.spin_levels(h, eri, N, twoS)[0]).max() < 1e-9
+    assert it[1:].max() <= 2, it
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-8)])
+def test_spin_target_truncated_sweep_matches_oracle(ctx, prec, tol):
+    import paper_2309_16724_gb300 as P
+    cfg = synth.Config("sw7s1", synth.SPATIAL_ORBITAL, 7, 6, 2, 6, 1002)
+    h, eri = synth.integrals(cfg.L, cfg.seed)
+    chain = synth.bond_sector_chain(cfg, cfg.L - 2)
+    sw = P.Sweep(ctx, h, eri, chain, cfg.N, 6, prec=prec, tol=1e-10, seed=cfg.seed, predict=True, twoS=2)
+    e, w, it, e0 = sw.run(2 * (cfg.L - 1), stats=True)
+    sw.close()
+    assert ctx.status() == 0
+    so = []
+    eo, wo = osweep.sweep(cfg, 6, 2, tol=1e-10, predict=True, stats=so)
+    assert np.abs(e - eo).max() < tol, (e, eo)
+    rq = np.array([x[1] for x in so])
+    assert np.abs(e0[1:] - rq[1:]).max() < 1e-7, (e0, rq)
+
+
+def test_heisenberg_triplet_sweep_equals_exact_diagonalisation(ctx):
+    import paper_2309_16724_gb300 as P
+    from oracle import ed
+    cfg = synth.Config("h10s1", synth.SPIN_HALF, 10, 10, 2, 32, 1001)
+    chain = synth.bond_sector_chain(cfg, cfg.L - 2)
+    sw = P.Sweep(ctx, None, None, chain, cfg.N, 32, prec=1, tol=1e-10, seed=cfg.seed, predict=True, twoS=2)
+    e, w = sw.run(4 * (cfg.L - 1))
+    sw.close()
+    assert ctx.status() == 0
+    E0 = ed.heisenberg_levels(10, 2)[0]
+    assert e.min() >= E0 - 1e-9
+    assert np.abs(e[cfg.L - 1:] - E0).max() < 1e-9
