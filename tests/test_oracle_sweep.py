@@ -38,9 +38,23 @@ def test_exact_sweep_equals_full_ci_at_every_step():
     assert np.all(np.abs(w) < 1e-20)
 
 
+_SW7 = synth.Config("sw7", synth.SPATIAL_ORBITAL, 7, 6, 0, 6, 1002)
+_SW7_RUNS = {}
+
+
+def _sw7(predict):
+    """Two half-sweeps of the seven-orbital chain at D = 6 (run once per
+    flag and shared by the tests): (energies, discarded weights, stats)."""
+    if predict not in _SW7_RUNS:
+        st = []
+        E, w = sweep.sweep(_SW7, 6, 2, predict=predict, stats=st)
+        _SW7_RUNS[predict] = (E, w, st)
+    return _SW7_RUNS[predict]
+
+
 def test_truncated_sweep_is_variational():
-    cfg = synth.Config("sw7", synth.SPATIAL_ORBITAL, 7, 6, 0, 6, 1002)
-    E, w = sweep.sweep(cfg, 6, 2)
+    cfg = _SW7
+    E, w, _ = _sw7(False)
     h, eri = synth.integrals(7, 1002)
     e0 = fci.spin_levels(h, eri, 6, 0)[0]
     assert np.all(E >= e0 - 1e-10)
@@ -218,10 +232,9 @@ def test_predicted_sweep_same_energies_fewer_iterations():
     assert st[0][0] > 10 and all(it == 1 for (it, _) in st[1:])
     # truncated bonds: the same energies and discarded weights as the sweep
     # from seeded start vectors, in fewer iterations
-    cfg = synth.Config("sw7", synth.SPATIAL_ORBITAL, 7, 6, 0, 6, 1002)
-    s0, s1 = [], []
-    E0, w0 = sweep.sweep(cfg, 6, 2, stats=s0)
-    E1, w1 = sweep.sweep(cfg, 6, 2, predict=True, stats=s1)
+    cfg = _SW7
+    E0, w0, s0 = _sw7(False)
+    E1, w1, s1 = _sw7(True)
     assert np.abs(E1 - E0).max() < 1e-8
     assert np.abs(w1 - w0).max() < 1e-8
     assert sum(s[0] for s in s1) < sum(s[0] for s in s0)
