@@ -180,3 +180,13 @@ def test_shard_options(hctx):
         assert len(prow) > 0
         got += [key(x) for x in prow]
     assert sorted(got) == want
+
+
+def test_sweep_needs_a_device_context(hctx):
+    """su2_sweep_create on a host-only context returns SU2_EINVAL with its
+    reason (the sweep's Davidson runs on the GPU; there is no host path)."""
+    cfg = synth.CONFIGS["heis12"]
+    chain = synth.bond_sector_chain(cfg, cfg.L - 2)
+    with pytest.raises(L.Su2Error) as ei:
+        L.Sweep(hctx, None, None, chain, cfg.N, cfg.D)
+    assert ei.value.code == L.SU2_EINVAL and "device context" in str(ei.value)
